@@ -1,0 +1,297 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: hand-derived
+golden bytes, a library FFT, closed forms of the PFB for tones, invariants
+(shift, Parseval, linearity) and the exact quantiser definition.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2303_09886_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dtft(w, f):
+    """W(f) = sum_u w[u] exp(-2 pi i f u), a library-free closed-form helper."""
+    u = np.arange(w.size)
+    return np.sum(w * np.exp(-2j * np.pi * f * u))
+
+
+# ----------------------------------------------------------------- unpack
+
+def test_unpack_golden():
+    with open(os.path.join(GOLDEN, "unpack10_msb.txt")) as fh:
+        lines = [l for l in fh if l.strip() and not l.startswith("#")]
+    assert len(lines) == 3
+    for line in lines:
+        hexpart, vals = line.split(";")
+        b = np.array([int(x, 16) for x in hexpart.split()], np.uint8)
+        expect = np.array([int(v) for v in vals.split()], np.int32)
+        got = O.unpack10(b, expect.size)
+        np.testing.assert_array_equal(got, expect)
+
+
+def test_unpack_pack_roundtrip_all_values_all_offsets():
+    # every 10-bit value at every one of the 4 positions of a 5-byte group
+    vals = np.arange(-512, 512, dtype=np.int32)
+    for shift in range(4):
+        s = np.roll(np.tile(vals, 4), shift)
+        got = O.unpack10(synth.pack10(s), s.size)
+        np.testing.assert_array_equal(got, s)
+
+
+def test_pack10_known_bytes():
+    # the generator's packer against the same hand-derived bytes
+    np.testing.assert_array_equal(synth.pack10(np.array([-512, -1, 0, 511])),
+                                  np.array([0x80, 0x3F, 0xF0, 0x01, 0xFF], np.uint8))
+
+
+# -------------------------------------------------------------------- DFT
+
+@pytest.mark.parametrize("N", [1, 2, 4, 8, 16, 64, 256])
+def test_fft_matches_naive_dft(N):
+    g = np.random.default_rng(N)
+    x = g.standard_normal(N) + 1j * g.standard_normal(N)
+    a, b = O.fft(x), O.dft_naive(x)
+    assert np.max(np.abs(a - b)) <= 1e-12 * max(1.0, np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("N", [32, 1024, 16384, 65536])
+def test_fft_matches_library(N):
+    g = np.random.default_rng(N)
+    x = g.standard_normal(N) + 1j * g.standard_normal(N)
+    a, b = O.fft(x), np.fft.fft(x)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+def test_dft_sign_and_closed_forms():
+    N = 16
+    delta1 = np.zeros(N, complex)
+    delta1[1] = 1.0
+    k = np.arange(N)
+    # a delayed impulse transforms to exp(-2 pi i k / N): fixes the sign (R5)
+    np.testing.assert_allclose(O.dft_naive(delta1), np.exp(-2j * np.pi * k / N), atol=1e-13)
+    np.testing.assert_allclose(O.fft(delta1), np.exp(-2j * np.pi * k / N), atol=1e-13)
+    const = np.ones(N, complex)
+    expect = np.zeros(N, complex)
+    expect[0] = N
+    np.testing.assert_allclose(O.fft(const), expect, atol=1e-12)
+
+
+def test_parseval_real_input():
+    N = 2048
+    g = np.random.default_rng(7).standard_normal(N)
+    X = O.fft(g.astype(complex))
+    lhs = np.sum(g * g)
+    rhs = (abs(X[0]) ** 2 + abs(X[N // 2]) ** 2 + 2 * np.sum(np.abs(X[1:N // 2]) ** 2)) / N
+    assert abs(lhs - rhs) <= 1e-10 * lhs
+
+
+# ---------------------------------------------------------------- weights
+
+@pytest.mark.parametrize("N,T", [(64, 4), (2048, 16), (16384, 16)])
+def test_default_weights_shape(N, T):
+    w = O.pfb_weights(N, T)
+    assert w.size == N * T
+    assert np.max(np.abs(w - w[::-1])) < 1e-15          # linear phase
+    assert abs(np.sum(w * w) - 1.0) < 1e-12               # R3 normalisation
+    W0 = abs(_dtft(w, 0.0))
+    # sinc cut-off at half a channel: adjacent channels cross near -6 dB
+    half = 20 * np.log10(abs(_dtft(w, 0.5 / N)) / W0)
+    assert -6.5 < half < -5.5
+    # stopband at the next channel centre
+    assert 20 * np.log10(abs(_dtft(w, 1.0 / N)) / W0) < (-40 if T < 8 else -75)
+
+
+# ----------------------------------------------------- delay model (R4)
+
+@pytest.mark.parametrize("d,c,delta", [(7.3, 7, 0.3), (7.5, 8, -0.5), (-0.2, 0, -0.2),
+                                       (-0.5, 0, -0.5), (-0.7, -1, 0.3), (0.0, 0, 0.0)])
+def test_delay_split(d, c, delta):
+    cc, dd, ph = O.DelayModel.constant(delay=d, phase=0.25).eval(12345)
+    assert cc == c and abs(dd - delta) < 1e-12 and ph == 0.25
+
+
+def test_delay_rate_and_segments():
+    m = O.DelayModel([(-(2 ** 62), 0, 1.0, 1e-3, 0.0, 0.01), (5000, 5000, 100.0, 0.0, 1.0, 0.0)])
+    c, dl, ph = m.eval(1000)            # d = 1 + 1e-3 * 1000 = 2
+    assert c == 2 and abs(dl) < 1e-12 and abs(ph - 10.0) < 1e-12
+    c, dl, ph = m.eval(5000)            # second segment
+    assert c == 100 and dl == 0.0 and ph == 1.0
+
+
+# ------------------------------------------------ FIR + DFT composition
+
+def test_pfb_closed_form_composition():
+    """Eq. 1 followed by the DFT equals one sum over the whole window:
+    X[k] = sum_{u < N T} w[u] s[t0 - c + u] exp(-2 pi i k u / N)."""
+    N, T = 64, 4
+    n = N // 2
+    g = np.random.default_rng(3)
+    s = g.integers(-512, 512, size=4096).astype(np.int32)
+    w = g.standard_normal(N * T)           # arbitrary weights: checks the index map
+    c = 5
+    m = 20
+    pre, _, co = O.channelize(s, 0, N, T, w, O.DelayModel.constant(delay=c), np.ones(n), m, 1)
+    assert co[0] == c
+    u = np.arange(N * T)
+    win = s[N * m - c + u].astype(np.float64)
+    k = np.arange(n)[:, None]
+    X = np.sum(w * win * np.exp(-2j * np.pi * ((k * u) % N) / N), axis=1)
+    np.testing.assert_allclose(pre[0], X, rtol=0, atol=1e-9 * np.max(np.abs(X)))
+
+
+def test_fir_missing_samples_are_zero():
+    N, T = 16, 2
+    s = np.arange(1, 33, dtype=np.int32)       # samples at absolute 100..131
+    w = np.ones(N * T)
+    g = O.fir(s, 100, N, T, w, t0=96, c=0)     # window [96, 128)
+    # t covers [96,112) and [112,128): sums of in-range samples only
+    expect = np.array([(s[t - 4] if t >= 4 else 0) + s[t + 12] for t in range(N)], float)
+    np.testing.assert_array_equal(g, expect)
+
+
+# --------------------------------------------------------- tone responses
+
+def _tone(N, total, f, A, psi, start=0):
+    i = np.arange(start, start + total, dtype=np.float64)
+    return A * np.cos(2 * np.pi * f * i + psi)
+
+
+def test_bin_centred_tone_lands_in_one_channel():
+    """Channel response is the Fourier transform of the weights (Sec. 5.2):
+    a bin-centred tone gives (A/2) W(0) in its channel plus one image term."""
+    N, T, k0, A = 256, 8, 19, 1000.0
+    n = N // 2
+    w = O.pfb_weights(N, T)
+    s = np.rint(_tone(N, N * 64, k0 / N, A, 0.4)).astype(np.int32)
+    # the closed form holds for the unrounded tone; the oracle sees the rounded
+    # one, which differs by at most half a unit per sample
+    s_exact = _tone(N, N * 64, k0 / N, A, 0.4)
+    m = 10
+    pre, _, _ = O.channelize(s, 0, N, T, w, O.DelayModel.constant(), np.ones(n), m, 1)
+    P = np.abs(pre[0]) ** 2
+    assert P[k0] / P.sum() > 0.999
+    # closed form on the exact tone (quantisation of the tone adds white noise)
+    t0 = N * m
+    u = np.arange(N * T)
+    X_exact = np.sum(w * s_exact[t0 + u] * np.exp(-2j * np.pi * k0 * u / N))
+    W0 = _dtft(w, 0.0)
+    Wimg = _dtft(w, 2 * k0 / N)
+    theta = 2 * np.pi * k0 * t0 / N + 0.4
+    main = 0.5 * A * W0 * np.exp(1j * theta)
+    assert abs(X_exact - main) <= 0.5 * A * abs(Wimg) * (1 + 1e-9) + 1e-9
+    # rounding the tone to integers moves the channel by at most the
+    # rounding noise bound sum |w| * 0.5
+    assert abs(pre[0][k0] - X_exact) <= 0.5 * np.sum(np.abs(w))
+    # every other channel: below the stopband given by W at >= 1 channel
+    others = np.delete(P, k0) / P[k0]
+    assert 10 * np.log10(others.max()) < -60
+
+
+def test_sub_channel_tone_response_matches_weight_transform():
+    """Sec. 5.2: the channel response follows |W(f - k/N)| (sub-channel sweep)."""
+    N, T, A = 128, 8, 1.0e4
+    n = N // 2
+    w = O.pfb_weights(N, T)
+    k0 = 23
+    for frac in (0.0, 0.2, 0.5, 0.8):
+        f = (k0 + frac) / N
+        s = np.rint(_tone(N, N * 40, f, A, 1.1)).astype(np.int32)
+        pre, _, _ = O.channelize(s, 0, N, T, w, O.DelayModel.constant(), np.ones(n), 12, 1)
+        for k in (k0 - 1, k0, k0 + 1, k0 + 2):
+            expect = 0.5 * A * abs(_dtft(w, f - k / N))
+            bound = 0.5 * A * abs(_dtft(w, f + k / N)) + 0.5 * np.sum(np.abs(w))
+            assert abs(abs(pre[0][k]) - expect) <= bound
+
+
+# ----------------------------------------------------------- delays
+
+def test_integer_delay_is_a_sample_shift():
+    N, T = 64, 4
+    n = N // 2
+    g = np.random.default_rng(11)
+    s = g.integers(-512, 512, size=8192).astype(np.int32)
+    w = O.pfb_weights(N, T)
+    c = 5
+    shifted = np.concatenate([np.zeros(c, np.int32), s[:-c]])   # s'[i] = s[i - c]
+    a, _, _ = O.channelize(s, 0, N, T, w, O.DelayModel.constant(delay=c), np.ones(n), 3, 20)
+    b, _, _ = O.channelize(shifted, 0, N, T, w, O.DelayModel.constant(), np.ones(n), 3, 20)
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("d", [0.3, 0.7, 1.0, 7.3, 12.49])
+def test_fine_and_coarse_delay_compose(d):
+    """A total delay d (split into coarse c and fine delta, R4/R6) delays a
+    bin-centred tone: Y_d[k0] = Y_0[k0] exp(-2 pi i k0 d / N), up to the
+    image term."""
+    N, T, k0, A = 256, 8, 37, 3000.0
+    n = N // 2
+    w = O.pfb_weights(N, T)
+    s = _tone(N, N * 64, k0 / N, A, 0.2)
+    si = np.rint(s * 1000).astype(np.int64)   # keep the tone almost exact
+    assert np.abs(si).max() < 2 ** 31
+    si = si.astype(np.int32)
+    y0, _, _ = O.channelize(si, 0, N, T, w, O.DelayModel.constant(), np.ones(n), 20, 1)
+    yd, _, _ = O.channelize(si, 0, N, T, w, O.DelayModel.constant(delay=d), np.ones(n), 20, 1)
+    img = 0.5 * A * 1000 * abs(_dtft(w, 2 * k0 / N))
+    noise = 0.5 * np.sum(np.abs(w))
+    expect = y0[0][k0] * np.exp(-2j * np.pi * k0 * d / N)
+    assert abs(yd[0][k0] - expect) <= 2 * (img + noise) + 1e-6 * abs(expect)
+
+
+def test_phase_and_gain():
+    N, T = 64, 4
+    n = N // 2
+    g = np.random.default_rng(5)
+    s = g.integers(-512, 512, size=4096).astype(np.int32)
+    w = O.pfb_weights(N, T)
+    base, _, _ = O.channelize(s, 0, N, T, w, O.DelayModel.constant(delay=2.3), np.ones(n), 4, 8)
+    ph, _, _ = O.channelize(s, 0, N, T, w, O.DelayModel.constant(delay=2.3, phase=0.1), np.ones(n), 4, 8)
+    np.testing.assert_allclose(ph, base * np.exp(0.1j), rtol=1e-12, atol=1e-9)
+    two, _, _ = O.channelize(s, 0, N, T, w, O.DelayModel.constant(delay=2.3), 2 * np.ones(n), 4, 8)
+    np.testing.assert_array_equal(two, 2 * base)
+    G = np.exp(1j * np.linspace(0, 3, n))
+    rot, _, _ = O.channelize(s, 0, N, T, w, O.DelayModel.constant(delay=2.3), G, 4, 8)
+    np.testing.assert_allclose(rot, base * G, rtol=1e-12, atol=1e-9)
+
+
+# ----------------------------------------------------------- quantiser
+
+@pytest.mark.parametrize("x,q", [(0.0, 0), (0.49999999, 0), (0.5, 1), (-0.5, -1), (1.5, 2),
+                                 (2.5, 3), (-2.5, -3), (126.4, 126), (126.5, 127), (127.5, 127),
+                                 (-127.5, -127), (-128.0, -127), (1e6, 127), (-1e6, -127)])
+def test_quantiser_half_away_and_saturate(x, q):
+    assert O.quantise(x) == q
+
+
+def test_saturating_tone_never_minus_128():
+    N, T, k0 = 2048, 16, 192      # tone in channel 192 of 1024, as in Sec. 3.5.1
+    n = N // 2
+    w = O.pfb_weights(N, T)
+    s = np.clip(np.rint(_tone(N, N * 24, k0 / N, 100.0, 0.3)), -512, 511).astype(np.int32)
+    pre, q, _ = O.channelize(s, 0, N, T, w, O.DelayModel.constant(), np.ones(n), 2, 4)
+    assert np.abs(pre[:, k0]).max() > 1000          # far beyond full scale
+    assert q.min() >= -127 and q.max() <= 127
+    tone = q[:, k0, :]
+    assert np.all(np.abs(tone).max(axis=1) == 127)
+
+
+# ----------------------------------------------------------- corner turn
+
+def test_corner_turn_golden():
+    with open(os.path.join(GOLDEN, "corner_turn_small.txt")) as fh:
+        lines = [l for l in fh if l.strip() and not l.startswith("#")]
+    hdr = dict(kv.split("=") for kv in lines[0].split())
+    M, n, S = int(hdr["M"]), int(hdr["n"]), int(hdr["S"])
+    expect = np.array([int(v) for v in lines[1].split()], np.int8)
+    q0 = np.empty((M, n, 2), np.int8)
+    for m in range(M):
+        for k in range(n):
+            q0[m, k] = (10 * m + 2 * k + 1, 10 * m + 2 * k + 2)
+    out = O.corner_turn(q0, -q0, S)
+    np.testing.assert_array_equal(out, expect)
