@@ -1,0 +1,181 @@
+/*
+ * fengine.h -- C ABI of libfengine, a GB300 (sm_103a) F-engine channelizer.
+ *
+ * The library implements the data-parallel hot path of the F-engine in
+ * B. Merry, "Efficient channelization on a Graphics Processing Unit"
+ * (arXiv:2303.09886), Sec. 2.1: unpack 10-bit samples, coarse delay, PFB FIR
+ * (Eq. 1), real-to-complex FFT, fine delay and bandpass gain, requantisation
+ * to 8-bit Gaussian integers and the channel-major corner turn (Sec. 2.2,
+ * Sec. 3.6), for the two polarisations of each antenna (Sec. 2.1, last
+ * paragraph).
+ *
+ * Conventions shared by every entry point:
+ *  - N = 2 n is the FFT length for n channels; spectrum m has timestamp
+ *    t0 = N m (critically sampled PFB, consecutive spectra N samples apart).
+ *  - Packed samples: sample i of a chunk occupies bits [10 i, 10 i + 10) of
+ *    the byte stream, most significant bit first, two's complement
+ *    (Sec. 2.2 fixes 10 bits per sample without padding; the bit order is
+ *    this library's documented choice). A chunk of L samples is 5 L / 4 bytes.
+ *  - Pointers named d_* are DEVICE pointers (cudaMalloc / PyTorch CUDA
+ *    tensors); all other pointers are host pointers. The caller owns every
+ *    buffer it passes; the plan owns its own state (weights, history tails,
+ *    delay models, gains, twiddles, scratch) and frees it in
+ *    fengine_plan_destroy.
+ *  - cuda_stream arguments are cudaStream_t handles passed as void*; NULL is
+ *    the legacy default stream. Work is enqueued asynchronously; a device
+ *    fault surfaces as FENGINE_ECUDA from a later call.
+ *  - Errors are reported only through fengine_status; nothing aborts, traps
+ *    the device or throws across the ABI. fengine_last_error() returns a
+ *    thread-local message for the last failure on the calling thread.
+ */
+#ifndef FENGINE_H
+#define FENGINE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FENGINE_ABI_VERSION 1
+#define FENGINE_MAX_DELAY_SEGMENTS 16
+
+typedef enum {
+    FENGINE_OK = 0,
+    FENGINE_EINVAL = 1,       /* invalid argument or configuration */
+    FENGINE_ENOMEM = 2,       /* device or host allocation failed */
+    FENGINE_ECUDA = 3,        /* CUDA runtime error (see fengine_last_error) */
+    FENGINE_ESEQ = 4,         /* chunk timestamp not contiguous with the stream */
+    FENGINE_EBUSY = 5,        /* no free slot / over the memory budget */
+    FENGINE_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
+    FENGINE_EUNSUPPORTED = 7, /* valid request this build does not implement */
+    FENGINE_EDELAY = 8        /* a coarse delay of this call leaves [0, max_delay] */
+} fengine_status;
+
+typedef enum {
+    FENGINE_FP32 = 0,    /* FP32 FIR and FFT on CUDA cores */
+    FENGINE_TC_FP16 = 1, /* reduced-precision form (FP16 operands, FP32 accumulation) */
+    FENGINE_TC_BF16 = 2  /* reduced-precision form (BF16 operands, FP32 accumulation) */
+} fengine_precision;
+
+/* Plan configuration (Sec. 2.1: channels and taps; Sec. 3.1: chunks;
+ * Sec. 3.3: coarse delay range; Sec. 2.2: 256 spectra per output heap). */
+typedef struct {
+    int32_t n_antennas;        /* >= 1 */
+    int32_t n_pols;            /* must be 2 (dual-polarisation F-engine) */
+    int32_t n_channels;        /* n: power of two, 8 <= n <= 32768 */
+    int32_t n_taps;            /* T: one of 1, 2, 4, 8, 16, 32 */
+    int64_t chunk_samples;     /* L per polarisation per call: a positive multiple of 2n */
+    int32_t spectra_per_heap;  /* S: 1 <= S <= L/2n; 0 selects min(256, L/2n) */
+    int32_t precision;         /* fengine_precision */
+    int64_t max_delay_samples; /* D >= 0: every coarse delay must lie in [0, D] */
+    const float *weights;      /* host, 2n*T prototype w[t + 2n j] (Eq. 1's w_{t,j});
+                                  NULL = built-in Hann-windowed sinc, sum w^2 = 1 */
+} fengine_config;
+
+typedef struct fengine_plan_s *fengine_plan_t;
+
+/* Read-only facts about a plan. */
+typedef struct {
+    int32_t n_channels, n_taps, n_antennas, spectra_per_heap;
+    int32_t fft_n1, fft_n2;       /* four-step split N = n1 * n2 used on the device */
+    int64_t spectra_per_chunk;    /* M = L / 2n: spectra every call emits per stream */
+    int64_t history_samples;      /* H = 2n (T - 1) + D rounded up to a multiple of 4 */
+    int64_t latency_spectra;      /* T - 1: first spectrum of a call = first_sample/2n - (T-1) */
+    int64_t out_bytes;            /* bytes of d_out per call: n_antennas * M * n * 4 */
+    size_t device_bytes;          /* device memory the plan holds */
+    size_t scratch_bytes;         /* part of device_bytes used as per-call scratch */
+} fengine_info;
+
+const char *fengine_strerror(fengine_status status);
+const char *fengine_last_error(void);
+int32_t fengine_abi_version(void);
+
+/* Built-in prototype filter (Sec. 5.2: Hann-windowed sinc), evaluated in FP64
+ * and rounded to FP32: for u in [0, M), M = 2n T,
+ *   w[u] = sin^2(pi (u + 1/2) / M) sinc((u + 1/2 - M/2) / 2n),
+ * scaled so that sum w^2 = 1. out: host array of 2n*T floats. */
+fengine_status fengine_default_weights(int32_t n_channels, int32_t n_taps, float *out);
+
+/* The requantiser of one Gaussian-integer component that the kernels apply
+ * (Sec. 2.1 step 6, Sec. 3.6): saturate to [-127, 127] and round half away
+ * from zero, here evaluated on the host from the same source. */
+int32_t fengine_quantise(float x);
+
+/* Create a plan on the current CUDA device (use the plan only while that
+ * device is current). Copies cfg->weights. Allocates all
+ * device state up front (history tails zeroed: samples before a stream's first
+ * chunk read as zero). Delays start at 0, phases at 0, gains at 1. */
+fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *out);
+fengine_status fengine_plan_destroy(fengine_plan_t plan);
+fengine_status fengine_get_info(fengine_plan_t plan, fengine_info *info);
+
+/* Delay and phase model of one (antenna, pol) stream (Sec. 2.1 steps 2 and 4,
+ * Sec. 3.3). From spectrum timestamp t0 >= t_apply on:
+ *   d(t0)   = delay + delay_rate * (t0 - t_ref)      samples
+ *   phi(t0) = phase + phase_rate * (t0 - t_ref)      radians
+ * The spectrum uses coarse delay c = floor(d + 1/2) (window start t0 - c,
+ * Eq. 1) and fine delay delta = d - c, applied as the channel rotation
+ * exp(i (phi - 2 pi delta k / 2n)). Up to FENGINE_MAX_DELAY_SEGMENTS models
+ * per stream are kept, ordered by t_apply; a new model with the same t_apply
+ * replaces the old one. Takes effect from the next fengine_process_chunk.
+ * Returns FENGINE_EINVAL for a bad index or non-finite parameter. */
+fengine_status fengine_set_delay(fengine_plan_t plan, int32_t ant, int32_t pol,
+                                 int64_t t_apply, int64_t t_ref, double delay,
+                                 double delay_rate, double phase, double phase_rate);
+
+/* Per-channel complex bandpass gains of one stream (Sec. 2.1 step 5). host
+ * array of n complex values as interleaved (re, im) floats. Takes effect from
+ * the next fengine_process_chunk. */
+fengine_status fengine_set_gains(fengine_plan_t plan, int32_t ant, int32_t pol,
+                                 const float *gains_re_im);
+
+/* Forget the stream history: the next call may start at any first_sample,
+ * and samples before it read as zero. */
+fengine_status fengine_reset(fengine_plan_t plan);
+
+/* Channelize one chunk of every stream (Sec. 2.1 steps 1-6).
+ *   d_packed       device, [antenna][pol][5L/4] bytes: samples
+ *                  [first_sample, first_sample + L) of each stream.
+ *   first_sample   multiple of 2n; after the first call (or a reset) it must
+ *                  equal the previous first_sample + L, else FENGINE_ESEQ.
+ *   d_out          device, n_antennas * M * n * 4 bytes: for each antenna the
+ *                  M = L/2n spectra m = first_sample/2n - (T-1) + q,
+ *                  q in [0, M), as heaps of S spectra (the last heap of a call
+ *                  may hold fewer, S_h = min(S, M - h S)); heap h is the
+ *                  array [k][s][pol][re, im] of int8 with q = h S + s
+ *                  (channel-major within the heap, Sec. 2.2 / Sec. 3.6).
+ *                  Values are round-half-away-from-zero, saturated to
+ *                  [-127, 127].
+ *   d_prequant     optional (NULL to skip) device FP32 [antenna][pol][M][n][re, im]:
+ *                  the spectra after fine delay and gain, before quantisation.
+ *   d_window_tap   optional (NULL to skip) device int32 [antenna][pol][M][2n]:
+ *                  the unpacked, coarse-delayed samples s[2n m - c_m + t],
+ *                  t in [0, 2n), that the first FIR tap of spectrum m uses.
+ *   first_spectrum optional host out: the m of q = 0.
+ * Every spectrum's window [2n m - c_m, 2n m - c_m + 2n T) lies in the data
+ * this call and the plan's history hold, for every c_m in [0, D]; a delay
+ * model that puts c_m outside [0, D] for a spectrum of this call is refused
+ * with FENGINE_EDELAY before anything is enqueued. Asynchronous on
+ * cuda_stream; the input may be reused once the stream passes this call. */
+fengine_status fengine_process_chunk(fengine_plan_t plan, void *cuda_stream,
+                                     const uint8_t *d_packed, int64_t first_sample,
+                                     int8_t *d_out, float *d_prequant,
+                                     int32_t *d_window_tap, int64_t *first_spectrum);
+
+/* Per-stage device timing, a profiling aid. While enabled, every
+ * fengine_process_chunk records CUDA events on its stream between its
+ * kernels. fengine_stage_times waits for those events, writes the summed
+ * milliseconds per stage to ms[0..3] = {delay table, phase 1 (unpack + FIR +
+ * first FFT stage), phase 2 (second FFT stage + delay/gain + requantise +
+ * corner turn), history tail update}, the number of timed calls to *calls,
+ * and starts a new accumulation. Disabled by default. */
+fengine_status fengine_set_profiling(fengine_plan_t plan, int32_t enable);
+fengine_status fengine_stage_times(fengine_plan_t plan, float *ms, int32_t *calls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FENGINE_H */

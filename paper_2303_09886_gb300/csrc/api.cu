@@ -1,0 +1,513 @@
+// Host side of libfengine: plan state, argument checking and the launch
+// sequence of one fengine_process_chunk call. See include/fengine.h for the
+// contract of every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fengine.h"
+#include "fe_device.cuh"
+#include "fe_internal.cuh"
+
+using fe::DelaySeg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fengine_status fail(fengine_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+fengine_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return FENGINE_ECUDA;
+}
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Same arithmetic as the device delay table (no contraction: the build
+// passes -ffp-contract=off to the host compiler), so c agrees exactly.
+long long coarse_delay(const DelaySeg &s, long long t0) {
+    const double dt = (double)(t0 - s.t_ref);
+    volatile double prod = s.rate * dt;
+    const double d = s.d0 + prod;
+    return (long long)std::floor(d + 0.5);
+}
+
+}  // namespace
+
+struct fengine_plan_s {
+    int device = 0;
+    int n_ant = 0, n_streams = 0, n = 0, N = 0, T = 0, S = 0, M = 0, N1 = 0, N2 = 0, W = 0, C = 0, R2 = 0;
+    int precision = 0;
+    long long L = 0, D = 0, H = 0, chunk_bytes = 0, hist_bytes = 0;
+    // device state
+    float *d_w = nullptr;
+    float2 *d_tw1 = nullptr, *d_tw2 = nullptr, *d_gains = nullptr, *d_ftab = nullptr, *d_A = nullptr;
+    uint8_t *d_hist[2] = {nullptr, nullptr};
+    int cur = 0;
+    DelaySeg *d_seg = nullptr;
+    int *d_nseg = nullptr, *d_ctab = nullptr, *d_err = nullptr;
+    size_t device_bytes = 0, scratch_bytes = 0;
+    // host mirrors, pinned staging
+    std::vector<std::vector<DelaySeg>> segs;
+    std::vector<float2> gains;
+    bool delay_dirty = true, gains_dirty = true;
+    DelaySeg *h_seg = nullptr;
+    int *h_nseg = nullptr;
+    float2 *h_gains = nullptr;
+    cudaEvent_t staged = nullptr;
+    bool staged_pending = false;
+    bool started = false;
+    long long next_sample = 0;
+    // optional per-stage timing: 5 events per timed call
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_events;
+    size_t prof_used = 0;
+};
+
+namespace {
+
+template <typename P>
+cudaError_t dalloc(fengine_plan_s *pl, P **ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e == cudaSuccess) pl->device_bytes += bytes;
+    return e;
+}
+
+void release(fengine_plan_s *pl) {
+    if (!pl) return;
+    cudaFree(pl->d_w);
+    cudaFree(pl->d_tw1);
+    cudaFree(pl->d_tw2);
+    cudaFree(pl->d_gains);
+    cudaFree(pl->d_ftab);
+    cudaFree(pl->d_A);
+    cudaFree(pl->d_hist[0]);
+    cudaFree(pl->d_hist[1]);
+    cudaFree(pl->d_seg);
+    cudaFree(pl->d_nseg);
+    cudaFree(pl->d_ctab);
+    cudaFree(pl->d_err);
+    cudaFreeHost(pl->h_seg);
+    cudaFreeHost(pl->h_nseg);
+    cudaFreeHost(pl->h_gains);
+    if (pl->staged) cudaEventDestroy(pl->staged);
+    for (cudaEvent_t ev : pl->prof_events) cudaEventDestroy(ev);
+    delete pl;
+}
+
+void default_weights_fp64(int N, int T, std::vector<double> &w) {
+    const long long Mw = (long long)N * T;
+    w.resize(Mw);
+    double ss = 0.0;
+    for (long long u = 0; u < Mw; u++) {
+        const double x = ((double)u + 0.5 - (double)Mw / 2.0) / (double)N;
+        const double sinc = x == 0.0 ? 1.0 : std::sin(M_PI * x) / (M_PI * x);
+        const double h = std::sin(M_PI * ((double)u + 0.5) / (double)Mw);
+        w[u] = h * h * sinc;
+        ss += w[u] * w[u];
+    }
+    const double sc = 1.0 / std::sqrt(ss);
+    for (auto &v : w) v *= sc;
+}
+
+// exp(-2 pi i a / b) with a reduced exactly modulo b first.
+float2 unit_root(long long a, long long b) {
+    const long long r = ((a % b) + b) % b;
+    const double ang = -2.0 * M_PI * (double)r / (double)b;
+    return make_float2((float)std::cos(ang), (float)std::sin(ang));
+}
+
+// Next profiling event (created on first use, reused across accumulations).
+cudaEvent_t prof_event(fengine_plan_s *pl) {
+    if (pl->prof_used == pl->prof_events.size()) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+        pl->prof_events.push_back(ev);
+    }
+    return pl->prof_events[pl->prof_used++];
+}
+
+void prof_mark(fengine_plan_s *pl, cudaEvent_t *slot, cudaStream_t st) {
+    if (!pl->profiling) return;
+    *slot = prof_event(pl);
+    if (*slot) cudaEventRecord(*slot, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fengine_strerror(fengine_status st) {
+    switch (st) {
+        case FENGINE_OK: return "ok";
+        case FENGINE_EINVAL: return "invalid argument";
+        case FENGINE_ENOMEM: return "out of memory";
+        case FENGINE_ECUDA: return "CUDA error";
+        case FENGINE_ESEQ: return "chunk timestamp not contiguous with the stream";
+        case FENGINE_EBUSY: return "busy: no slot or over budget";
+        case FENGINE_ETIMEOUT: return "device wait timed out";
+        case FENGINE_EUNSUPPORTED: return "unsupported in this build";
+        case FENGINE_EDELAY: return "coarse delay outside [0, max_delay_samples]";
+    }
+    return "unknown status";
+}
+
+const char *fengine_last_error(void) { return g_last_error.c_str(); }
+
+int32_t fengine_abi_version(void) { return FENGINE_ABI_VERSION; }
+
+int32_t fengine_quantise(float x) { return fe::quant8(x); }
+
+fengine_status fengine_default_weights(int32_t n_channels, int32_t n_taps, float *out) {
+    if (!out || !is_pow2(n_channels) || n_taps < 1 || n_taps > 1024)
+        return fail(FENGINE_EINVAL, "fengine_default_weights: bad arguments");
+    std::vector<double> w;
+    default_weights_fp64(2 * n_channels, n_taps, w);
+    for (size_t i = 0; i < w.size(); i++) out[i] = (float)w[i];
+    return FENGINE_OK;
+}
+
+fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *out) {
+    if (!cfg || !out) return fail(FENGINE_EINVAL, "fengine_plan_create: null argument");
+    *out = nullptr;
+    const int n = cfg->n_channels, T = cfg->n_taps;
+    if (cfg->n_antennas < 1) return fail(FENGINE_EINVAL, "n_antennas must be >= 1");
+    if (cfg->n_pols != 2) return fail(FENGINE_EINVAL, "n_pols must be 2");
+    if (!is_pow2(n) || n < 8 || n > 32768) return fail(FENGINE_EINVAL, "n_channels must be a power of two in [8, 32768]");
+    if (!(T == 1 || T == 2 || T == 4 || T == 8 || T == 16 || T == 32))
+        return fail(FENGINE_EINVAL, "n_taps must be one of 1, 2, 4, 8, 16, 32");
+    const long long N = 2LL * n;
+    if (cfg->chunk_samples <= 0 || cfg->chunk_samples % N)
+        return fail(FENGINE_EINVAL, "chunk_samples must be a positive multiple of 2 n_channels");
+    const long long M = cfg->chunk_samples / N;
+    if (M > (1LL << 30)) return fail(FENGINE_EINVAL, "chunk too long");
+    if (cfg->max_delay_samples < 0 || cfg->max_delay_samples > (1LL << 30))
+        return fail(FENGINE_EINVAL, "max_delay_samples out of range");
+    int S = cfg->spectra_per_heap;
+    if (S == 0) S = (int)(M < 256 ? M : 256);
+    if (S < 1 || S > M) return fail(FENGINE_EINVAL, "spectra_per_heap must be in [1, L/2n]");
+    if (cfg->precision != FENGINE_FP32)
+        return fail(FENGINE_EUNSUPPORTED, "only FENGINE_FP32 is implemented in this build");
+
+    fengine_plan_s *pl = new (std::nothrow) fengine_plan_s();
+    if (!pl) return fail(FENGINE_ENOMEM, "host allocation");
+    cudaGetDevice(&pl->device);
+    pl->n_ant = cfg->n_antennas;
+    pl->n_streams = 2 * cfg->n_antennas;
+    pl->n = n;
+    pl->N = (int)N;
+    pl->T = T;
+    pl->S = S;
+    pl->M = (int)M;
+    pl->L = cfg->chunk_samples;
+    pl->D = cfg->max_delay_samples;
+    pl->precision = cfg->precision;
+    pl->N1 = (int)(N / 1024 > 8 ? N / 1024 : 8);
+    pl->N2 = (int)(N / pl->N1);
+    pl->W = fe::phase1_W(pl->N1, pl->N2);
+    pl->C = pl->N1 * pl->W;
+    pl->R2 = fe::phase2_R2(pl->N2);
+    long long H = N * (T - 1) + pl->D;
+    H = (H + 3) / 4 * 4;
+    pl->H = H;
+    pl->hist_bytes = H / 4 * 5;
+    pl->chunk_bytes = pl->L / 4 * 5;
+
+    const int ns = pl->n_streams;
+    cudaError_t e = cudaSuccess;
+    const size_t a_bytes = (size_t)ns * M * (pl->N1 / 2 + 1) * pl->N2 * sizeof(float2);
+    if ((e = dalloc(pl, &pl->d_w, sizeof(float) * N * T)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_tw1, sizeof(float2) * (pl->N1 / 2 + 1) * pl->N2)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_tw2, sizeof(float2) * pl->N2)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_gains, sizeof(float2) * ns * n)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_ftab, sizeof(float2) * ns * M)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_ctab, sizeof(int) * ns * M)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_A, a_bytes)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_hist[0], (size_t)pl->hist_bytes * ns + 16)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_hist[1], (size_t)pl->hist_bytes * ns + 16)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_seg, sizeof(DelaySeg) * fe::kMaxSeg * ns)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_nseg, sizeof(int) * ns)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_err, sizeof(int))) != cudaSuccess) {
+        release(pl);
+        g_last_error = std::string("device allocation: ") + cudaGetErrorString(e);
+        return FENGINE_ENOMEM;
+    }
+    pl->scratch_bytes = a_bytes + sizeof(float2) * ns * M + sizeof(int) * ns * M;
+    if ((e = cudaMallocHost((void **)&pl->h_seg, sizeof(DelaySeg) * fe::kMaxSeg * ns)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&pl->h_nseg, sizeof(int) * ns)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&pl->h_gains, sizeof(float2) * ns * n)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&pl->staged, cudaEventDisableTiming)) != cudaSuccess) {
+        release(pl);
+        g_last_error = std::string("pinned allocation: ") + cudaGetErrorString(e);
+        return FENGINE_ENOMEM;
+    }
+
+    // weights (Eq. 1's w_{t,j} = w[t + N j])
+    std::vector<float> w((size_t)N * T);
+    if (cfg->weights) {
+        std::memcpy(w.data(), cfg->weights, sizeof(float) * N * T);
+    } else {
+        std::vector<double> wd;
+        default_weights_fp64((int)N, T, wd);
+        for (size_t i = 0; i < wd.size(); i++) w[i] = (float)wd[i];
+    }
+    for (float v : w)
+        if (!std::isfinite(v)) {
+            release(pl);
+            return fail(FENGINE_EINVAL, "weights must be finite");
+        }
+    // twiddles, evaluated in FP64 with exact integer phase reduction
+    std::vector<float2> tw1((size_t)(pl->N1 / 2 + 1) * pl->N2), tw2(pl->N2);
+    for (int k1 = 0; k1 <= pl->N1 / 2; k1++)
+        for (int t2 = 0; t2 < pl->N2; t2++) tw1[(size_t)k1 * pl->N2 + t2] = unit_root((long long)k1 * t2, N);
+    for (int q = 0; q < pl->N2; q++) tw2[q] = unit_root(q, pl->N2);
+    pl->segs.assign(ns, std::vector<DelaySeg>{DelaySeg{-(1LL << 62), 0, 0.0, 0.0, 0.0, 0.0}});
+    pl->gains.assign((size_t)ns * n, make_float2(1.0f, 0.0f));
+
+    if ((e = cudaMemcpy(pl->d_w, w.data(), sizeof(float) * N * T, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(pl->d_tw1, tw1.data(), sizeof(float2) * tw1.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(pl->d_tw2, tw2.data(), sizeof(float2) * tw2.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(pl->d_hist[0], 0, (size_t)pl->hist_bytes * ns + 16)) != cudaSuccess ||
+        (e = cudaMemset(pl->d_hist[1], 0, (size_t)pl->hist_bytes * ns + 16)) != cudaSuccess ||
+        (e = cudaMemset(pl->d_err, 0, sizeof(int))) != cudaSuccess) {
+        release(pl);
+        return cuda_fail(e, "plan upload");
+    }
+    *out = pl;
+    return FENGINE_OK;
+}
+
+fengine_status fengine_plan_destroy(fengine_plan_t pl) {
+    if (!pl) return fail(FENGINE_EINVAL, "null plan");
+    if (pl->staged_pending) cudaEventSynchronize(pl->staged);
+    release(pl);
+    return FENGINE_OK;
+}
+
+fengine_status fengine_get_info(fengine_plan_t pl, fengine_info *info) {
+    if (!pl || !info) return fail(FENGINE_EINVAL, "null argument");
+    info->n_channels = pl->n;
+    info->n_taps = pl->T;
+    info->n_antennas = pl->n_ant;
+    info->spectra_per_heap = pl->S;
+    info->fft_n1 = pl->N1;
+    info->fft_n2 = pl->N2;
+    info->spectra_per_chunk = pl->M;
+    info->history_samples = pl->H;
+    info->latency_spectra = pl->T - 1;
+    info->out_bytes = (long long)pl->n_ant * pl->M * pl->n * 4;
+    info->device_bytes = pl->device_bytes;
+    info->scratch_bytes = pl->scratch_bytes;
+    return FENGINE_OK;
+}
+
+fengine_status fengine_set_delay(fengine_plan_t pl, int32_t ant, int32_t pol, int64_t t_apply,
+                                 int64_t t_ref, double delay, double delay_rate, double phase,
+                                 double phase_rate) {
+    if (!pl) return fail(FENGINE_EINVAL, "null plan");
+    if (ant < 0 || ant >= pl->n_ant || pol < 0 || pol > 1) return fail(FENGINE_EINVAL, "bad stream index");
+    if (!std::isfinite(delay) || !std::isfinite(delay_rate) || !std::isfinite(phase) || !std::isfinite(phase_rate))
+        return fail(FENGINE_EINVAL, "delay model must be finite");
+    auto &v = pl->segs[ant * 2 + pol];
+    const DelaySeg s{(long long)t_apply, (long long)t_ref, delay, delay_rate, phase, phase_rate};
+    size_t i = 0;
+    while (i < v.size() && v[i].t_apply < t_apply) i++;
+    if (i < v.size() && v[i].t_apply == t_apply) {
+        v[i] = s;
+    } else {
+        if ((int)v.size() >= fe::kMaxSeg) return fail(FENGINE_EINVAL, "too many pending delay models");
+        v.insert(v.begin() + i, s);
+    }
+    pl->delay_dirty = true;
+    return FENGINE_OK;
+}
+
+fengine_status fengine_set_gains(fengine_plan_t pl, int32_t ant, int32_t pol, const float *g) {
+    if (!pl || !g) return fail(FENGINE_EINVAL, "null argument");
+    if (ant < 0 || ant >= pl->n_ant || pol < 0 || pol > 1) return fail(FENGINE_EINVAL, "bad stream index");
+    for (int k = 0; k < 2 * pl->n; k++)
+        if (!std::isfinite(g[k])) return fail(FENGINE_EINVAL, "gains must be finite");
+    float2 *dst = pl->gains.data() + (size_t)(ant * 2 + pol) * pl->n;
+    for (int k = 0; k < pl->n; k++) dst[k] = make_float2(g[2 * k], g[2 * k + 1]);
+    pl->gains_dirty = true;
+    return FENGINE_OK;
+}
+
+fengine_status fengine_reset(fengine_plan_t pl) {
+    if (!pl) return fail(FENGINE_EINVAL, "null plan");
+    cudaError_t e;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "reset sync");
+    const size_t hb = (size_t)pl->hist_bytes * pl->n_streams + 16;
+    if ((e = cudaMemset(pl->d_hist[0], 0, hb)) != cudaSuccess ||
+        (e = cudaMemset(pl->d_hist[1], 0, hb)) != cudaSuccess)
+        return cuda_fail(e, "reset history");
+    pl->started = false;
+    return FENGINE_OK;
+}
+
+fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const uint8_t *d_packed,
+                                     int64_t first_sample, int8_t *d_out, float *d_prequant,
+                                     int32_t *d_window_tap, int64_t *first_spectrum) {
+    if (!pl || !d_packed || !d_out) return fail(FENGINE_EINVAL, "null argument");
+    if (first_sample % pl->N) return fail(FENGINE_EINVAL, "first_sample must be a multiple of 2 n_channels");
+    if (pl->started && first_sample != pl->next_sample)
+        return fail(FENGINE_ESEQ, "expected first_sample " + std::to_string(pl->next_sample));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const long long m0 = first_sample / pl->N - (pl->T - 1);
+    const long long t_first = (long long)pl->N * m0, t_last = (long long)pl->N * (m0 + pl->M - 1);
+
+    // Drop delay models that no spectrum from this call on can use, then
+    // check that every coarse delay of this call lies in [0, D]. A segment is
+    // linear, so its extreme delays over a spectrum range are at the ends.
+    for (int s = 0; s < pl->n_streams; s++) {
+        auto &v = pl->segs[s];
+        while (v.size() > 1 && v[1].t_apply <= t_first) {
+            v.erase(v.begin());
+            pl->delay_dirty = true;
+        }
+        for (size_t i = 0; i < v.size(); i++) {
+            long long lo = i == 0 ? t_first : (v[i].t_apply > t_first ? v[i].t_apply : t_first);
+            long long hi = i + 1 < v.size() ? v[i + 1].t_apply - 1 : t_last;
+            if (hi > t_last) hi = t_last;
+            // round lo up to a spectrum timestamp
+            lo = (lo + pl->N - 1) / pl->N * pl->N;
+            if (lo < t_first) lo = t_first;
+            if (lo > hi) continue;
+            hi = hi / pl->N * pl->N;
+            if (hi < lo) continue;
+            const long long c0 = coarse_delay(v[i], lo), c1 = coarse_delay(v[i], hi);
+            if (c0 < 0 || c1 < 0 || c0 > pl->D || c1 > pl->D)
+                return fail(FENGINE_EDELAY, "stream " + std::to_string(s) + ": coarse delay " +
+                                                std::to_string(c0 < 0 || c0 > pl->D ? c0 : c1) +
+                                                " outside [0, " + std::to_string(pl->D) + "]");
+        }
+    }
+
+    cudaError_t e;
+    if (pl->delay_dirty || pl->gains_dirty) {
+        if (pl->staged_pending) {
+            if ((e = cudaEventSynchronize(pl->staged)) != cudaSuccess) return cuda_fail(e, "staging wait");
+            pl->staged_pending = false;
+        }
+        if (pl->delay_dirty) {
+            for (int s = 0; s < pl->n_streams; s++) {
+                pl->h_nseg[s] = (int)pl->segs[s].size();
+                for (size_t i = 0; i < pl->segs[s].size(); i++) pl->h_seg[(size_t)s * fe::kMaxSeg + i] = pl->segs[s][i];
+            }
+            if ((e = cudaMemcpyAsync(pl->d_seg, pl->h_seg, sizeof(DelaySeg) * fe::kMaxSeg * pl->n_streams,
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(pl->d_nseg, pl->h_nseg, sizeof(int) * pl->n_streams,
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "delay upload");
+        }
+        if (pl->gains_dirty) {
+            std::memcpy(pl->h_gains, pl->gains.data(), sizeof(float2) * pl->gains.size());
+            if ((e = cudaMemcpyAsync(pl->d_gains, pl->h_gains, sizeof(float2) * pl->gains.size(),
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "gain upload");
+        }
+        if ((e = cudaEventRecord(pl->staged, st)) != cudaSuccess) return cuda_fail(e, "staging event");
+        pl->staged_pending = true;
+        pl->delay_dirty = pl->gains_dirty = false;
+    }
+
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    prof_mark(pl, &ev[0], st);
+    fe::DelayTableParams dp{};
+    dp.seg = pl->d_seg;
+    dp.nseg = pl->d_nseg;
+    dp.n_streams = pl->n_streams;
+    dp.N = pl->N;
+    dp.m0 = m0;
+    dp.M = pl->M;
+    dp.max_delay = (int)pl->D;
+    dp.ctab = pl->d_ctab;
+    dp.ftab = pl->d_ftab;
+    dp.err = pl->d_err;
+    if ((e = fe::launch_delay_table(dp, st)) != cudaSuccess) return cuda_fail(e, "delay table launch");
+    prof_mark(pl, &ev[1], st);
+
+    fe::Phase1Params p1{};
+    p1.chunk = d_packed;
+    p1.hist = pl->d_hist[pl->cur];
+    p1.chunk_bytes = pl->chunk_bytes;
+    p1.hist_bytes = pl->hist_bytes;
+    p1.H = pl->H;
+    p1.L = pl->L;
+    p1.N = pl->N;
+    p1.N2 = pl->N2;
+    p1.W = pl->W;
+    p1.C = pl->C;
+    p1.M = pl->M;
+    p1.m0 = m0;
+    p1.t_in = first_sample;
+    p1.w = pl->d_w;
+    p1.tw1 = pl->d_tw1;
+    p1.ctab = pl->d_ctab;
+    p1.A = pl->d_A;
+    p1.window_tap = d_window_tap;
+    if ((e = fe::launch_phase1(pl->T, pl->N1, p1, pl->n_streams, st)) != cudaSuccess)
+        return cuda_fail(e, "phase-1 launch");
+    prof_mark(pl, &ev[2], st);
+
+    fe::Phase2Params p2{};
+    p2.A = pl->d_A;
+    p2.tw2 = pl->d_tw2;
+    p2.gains = pl->d_gains;
+    p2.ftab = pl->d_ftab;
+    p2.N = pl->N;
+    p2.N1 = pl->N1;
+    p2.M = pl->M;
+    p2.S = pl->S;
+    p2.R2 = pl->R2;
+    p2.out = d_out;
+    p2.prequant = reinterpret_cast<float2 *>(d_prequant);
+    if ((e = fe::launch_phase2(pl->N2, p2, pl->n_ant, st)) != cudaSuccess)
+        return cuda_fail(e, "phase-2 launch");
+    prof_mark(pl, &ev[3], st);
+
+    if ((e = fe::launch_tail_update(pl->d_hist[pl->cur], d_packed, pl->d_hist[1 - pl->cur], pl->hist_bytes,
+                                    pl->chunk_bytes, pl->n_streams, st)) != cudaSuccess)
+        return cuda_fail(e, "tail launch");
+    prof_mark(pl, &ev[4], st);
+    pl->cur = 1 - pl->cur;
+    pl->started = true;
+    pl->next_sample = first_sample + pl->L;
+    if (first_spectrum) *first_spectrum = m0;
+    return FENGINE_OK;
+}
+
+fengine_status fengine_set_profiling(fengine_plan_t pl, int32_t enable) {
+    if (!pl) return fail(FENGINE_EINVAL, "null plan");
+    pl->profiling = enable != 0;
+    return FENGINE_OK;
+}
+
+fengine_status fengine_stage_times(fengine_plan_t pl, float *ms, int32_t *calls) {
+    if (!pl || !ms || !calls) return fail(FENGINE_EINVAL, "null argument");
+    for (int i = 0; i < 4; i++) ms[i] = 0.0f;
+    const size_t n_calls = pl->prof_used / 5;
+    for (size_t c = 0; c < n_calls; c++) {
+        cudaEvent_t *ev = pl->prof_events.data() + 5 * c;
+        cudaError_t e = cudaEventSynchronize(ev[4]);
+        if (e != cudaSuccess) return cuda_fail(e, "stage timing");
+        for (int i = 0; i < 4; i++) {
+            float t = 0.0f;
+            if ((e = cudaEventElapsedTime(&t, ev[i], ev[i + 1])) != cudaSuccess) return cuda_fail(e, "stage timing");
+            ms[i] += t;
+        }
+    }
+    *calls = (int32_t)n_calls;
+    pl->prof_used = 0;
+    return FENGINE_OK;
+}
+
+}  // extern "C"

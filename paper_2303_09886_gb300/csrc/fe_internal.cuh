@@ -1,0 +1,91 @@
+// Internal declarations shared by the libfengine translation units.
+//
+// Device data path of one fengine_process_chunk call (Sec. 2.1 steps 1-6):
+//   k_delay_table   FP64 delay/phase model per spectrum -> coarse c, fine delta, phase
+//   k_phase1<T,N1>  unpack + coarse delay + PFB FIR (Eq. 1) + first FFT stage
+//                   (real N1-point DFT over t1, twiddle by exp(-2 pi i k1 t2 / N))
+//   k_phase2<N2>    N2-point FFT over t2 + fine-delay rotation + gain +
+//                   requantise + channel-major corner turn
+//   k_tail_update   keep the last H packed samples of every stream
+// with the four-step split t = N2 t1 + t2, k = k1 + N1 k2 of the 2n-point
+// real DFT (the exp(-2 pi i k1 t2 / N) cross term is the twiddle).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fe {
+
+constexpr int kMaxSeg = 16;   // FENGINE_MAX_DELAY_SEGMENTS
+
+// One linear delay/phase segment of a stream, applied from t_apply on.
+struct DelaySeg {
+    long long t_apply, t_ref;
+    double d0, rate, phi0, phi_rate;
+};
+
+// Per-stream delay models, device resident: seg[stream * kMaxSeg + i].
+struct DelayTableParams {
+    const DelaySeg *seg;
+    const int *nseg;          // [stream]
+    int n_streams;
+    int N;                    // FFT length 2n
+    long long m0;             // first spectrum of the call
+    int M;                    // spectra per call
+    int max_delay;            // coarse delays clamp into [0, max_delay]
+    int *ctab;                // out [stream][M] coarse delay
+    float2 *ftab;             // out [stream][M] (fine delay delta, phase reduced to [-pi, pi))
+    int *err;                 // set to 1 if a coarse delay had to be clamped
+};
+
+struct Phase1Params {
+    const uint8_t *chunk;     // [stream][chunk_bytes]
+    const uint8_t *hist;      // [stream][hist_bytes], samples [t_in - H, t_in)
+    long long chunk_bytes, hist_bytes;
+    long long H;              // history samples (multiple of 4)
+    long long L;              // chunk samples
+    int N, N2, W, C;          // FFT length, second-stage size, t2 per CTA, columns per CTA
+    int M;                    // spectra per call
+    long long m0;             // first spectrum of the call
+    long long t_in;           // first sample of the chunk
+    const float *w;           // [N*T] prototype, w[t + N j]
+    const float2 *tw1;        // [(N1/2+1)][N2] exp(-2 pi i k1 t2 / N)
+    const int *ctab;          // [stream][M]
+    float2 *A;                // out [stream][M][N1/2+1][N2]
+    int *window_tap;          // optional out [stream][M][N]
+};
+
+struct Phase2Params {
+    const float2 *A;          // [stream][M][N1/2+1][N2]
+    const float2 *tw2;        // [N2] exp(-2 pi i q / N2)
+    const float2 *gains;      // [stream][n]
+    const float2 *ftab;       // [stream][M]
+    int N, N1, M, S, R2;      // FFT length, first-stage size, spectra/call, spectra/heap, spectra/CTA
+    int8_t *out;              // [ant][heap][n][S_h][pol][2]
+    float2 *prequant;         // optional [stream][M][n]
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_delay_table(const DelayTableParams &p, cudaStream_t s);
+cudaError_t launch_tail_update(const uint8_t *hist_in, const uint8_t *chunk, uint8_t *hist_out,
+                               long long hist_bytes, long long chunk_bytes, int n_streams,
+                               cudaStream_t s);
+cudaError_t launch_phase1(int T, int N1, const Phase1Params &p, int n_streams, cudaStream_t s);
+cudaError_t launch_phase2(int N2, const Phase2Params &p, int n_ant, cudaStream_t s);
+
+// Tile shapes (host and device agree through these).
+constexpr int kP1Rows = 32;   // spectra per phase-1 CTA
+inline int phase1_W(int N1, int N2) {
+    int w = (N1 >= 64) ? 8 : 32;
+    return w < N2 ? w : N2;
+}
+inline int phase2_R2(int N2) {
+    int r = 8192 / N2;          // 2 pols * R2 * N2 * 8 B <= 128 KiB of shared memory
+    if (r > 32) r = 32;
+    if (r < 1) r = 1;
+    return r;
+}
+size_t phase1_smem_bytes(int T, int C);
+size_t phase2_smem_bytes(int N2, int R2);
+
+}  // namespace fe

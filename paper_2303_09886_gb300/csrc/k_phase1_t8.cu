@@ -1,0 +1,7 @@
+// Phase-1 kernels for T = 8 taps (one translation unit per tap count so the
+// instantiations compile in parallel).
+#include "k_phase1.cuh"
+
+namespace fe {
+template cudaError_t launch_phase1_n1<8>(int, const Phase1Params &, int, cudaStream_t);
+}  // namespace fe

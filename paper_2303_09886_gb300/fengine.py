@@ -1,0 +1,202 @@
+"""Thin Python binding of libfengine (include/fengine.h).
+
+Argument marshalling only: every step of the channelizer runs in the CUDA
+kernels behind the C ABI. PyTorch supplies device memory and streams; tensors
+are passed to the library as raw device pointers. If the shared library is
+missing or fails to load, every entry point raises -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfengine.so")
+
+FP32, TC_FP16, TC_BF16 = 0, 1, 2
+STATUS = {0: "FENGINE_OK", 1: "FENGINE_EINVAL", 2: "FENGINE_ENOMEM", 3: "FENGINE_ECUDA",
+          4: "FENGINE_ESEQ", 5: "FENGINE_EBUSY", 6: "FENGINE_ETIMEOUT",
+          7: "FENGINE_EUNSUPPORTED", 8: "FENGINE_EDELAY"}
+
+# every symbol include/fengine.h declares
+EXPORTS = ("fengine_strerror", "fengine_last_error", "fengine_abi_version", "fengine_quantise",
+           "fengine_default_weights", "fengine_plan_create", "fengine_plan_destroy",
+           "fengine_get_info", "fengine_set_delay", "fengine_set_gains", "fengine_reset",
+           "fengine_process_chunk", "fengine_set_profiling", "fengine_stage_times")
+
+
+class FEngineError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("n_antennas", ctypes.c_int32), ("n_pols", ctypes.c_int32),
+                ("n_channels", ctypes.c_int32), ("n_taps", ctypes.c_int32),
+                ("chunk_samples", ctypes.c_int64), ("spectra_per_heap", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_delay_samples", ctypes.c_int64),
+                ("weights", ctypes.POINTER(ctypes.c_float))]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_channels", ctypes.c_int32), ("n_taps", ctypes.c_int32),
+                ("n_antennas", ctypes.c_int32), ("spectra_per_heap", ctypes.c_int32),
+                ("fft_n1", ctypes.c_int32), ("fft_n2", ctypes.c_int32),
+                ("spectra_per_chunk", ctypes.c_int64), ("history_samples", ctypes.c_int64),
+                ("latency_spectra", ctypes.c_int64), ("out_bytes", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfengine.so (built by paper_2303_09886_gb300.build). Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FEngineError(-1, f"{path} is missing: run paper_2303_09886_gb300.build.build() "
+                               "(the CUDA extension is required; there is no fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.fengine_strerror.argtypes = [ctypes.c_int]
+    lib.fengine_strerror.restype = ctypes.c_char_p
+    lib.fengine_last_error.argtypes = []
+    lib.fengine_last_error.restype = ctypes.c_char_p
+    lib.fengine_abi_version.argtypes = []
+    lib.fengine_abi_version.restype = i32
+    lib.fengine_quantise.argtypes = [ctypes.c_float]
+    lib.fengine_quantise.restype = i32
+    lib.fengine_default_weights.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_float)]
+    lib.fengine_plan_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    lib.fengine_plan_destroy.argtypes = [vp]
+    lib.fengine_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.fengine_set_delay.argtypes = [vp, i32, i32, i64, i64, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double]
+    lib.fengine_set_gains.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_float)]
+    lib.fengine_reset.argtypes = [vp]
+    lib.fengine_process_chunk.argtypes = [vp, vp, vp, i64, vp, vp, vp, ctypes.POINTER(i64)]
+    for name in ("fengine_default_weights", "fengine_plan_create", "fengine_plan_destroy",
+                 "fengine_get_info", "fengine_set_delay", "fengine_set_gains", "fengine_reset",
+                 "fengine_process_chunk", "fengine_set_profiling", "fengine_stage_times"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        lib = load()
+        raise FEngineError(status, lib.fengine_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def quantise(x: float) -> int:
+    """The kernels' requantiser evaluated on the host (same source)."""
+    return int(load().fengine_quantise(float(x)))
+
+
+def default_weights(n_channels: int, n_taps: int) -> np.ndarray:
+    out = np.empty(2 * n_channels * n_taps, np.float32)
+    _check(load().fengine_default_weights(n_channels, n_taps,
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+class Plan:
+    """One F-engine plan: n_antennas dual-pol streams on the current CUDA device."""
+
+    def __init__(self, n_antennas: int, n_channels: int, n_taps: int, chunk_samples: int,
+                 spectra_per_heap: int = 0, max_delay_samples: int = 0, weights=None,
+                 precision: int = FP32):
+        lib = load()
+        self._w = None
+        if weights is not None:
+            self._w = np.ascontiguousarray(weights, dtype=np.float32)
+            if self._w.size != 2 * n_channels * n_taps:
+                raise ValueError("weights must have 2 * n_channels * n_taps entries")
+        cfg = Config(n_antennas, 2, n_channels, n_taps, chunk_samples, spectra_per_heap, precision,
+                     max_delay_samples,
+                     self._w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if self._w is not None else None)
+        h = ctypes.c_void_p()
+        _check(lib.fengine_plan_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.info = Info()
+        _check(lib.fengine_get_info(self._h, ctypes.byref(self.info)))
+        self.n_antennas, self.n_channels, self.n_taps = n_antennas, n_channels, n_taps
+        self.chunk_samples = chunk_samples
+        self.N = 2 * n_channels
+        self.M = int(self.info.spectra_per_chunk)
+        self.S = int(self.info.spectra_per_heap)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().fengine_plan_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_delay(self, ant: int, pol: int, delay: float, rate: float = 0.0, phase: float = 0.0,
+                  phase_rate: float = 0.0, t_apply: int = -(2 ** 62), t_ref: int = 0):
+        _check(load().fengine_set_delay(self._h, ant, pol, t_apply, t_ref, delay, rate, phase,
+                                        phase_rate))
+
+    def set_gains(self, ant: int, pol: int, gains):
+        g = np.ascontiguousarray(np.broadcast_to(np.asarray(gains, np.complex64), (self.n_channels,)))
+        gi = g.view(np.float32)
+        _check(load().fengine_set_gains(self._h, ant, pol, gi.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def reset(self):
+        _check(load().fengine_reset(self._h))
+
+    STAGES = ("delay_table", "phase1", "phase2", "tail")
+
+    def set_profiling(self, enable: bool = True):
+        _check(load().fengine_set_profiling(self._h, 1 if enable else 0))
+
+    def stage_times(self):
+        """Summed device milliseconds per stage since the last call, and the call count."""
+        ms = (ctypes.c_float * 4)()
+        calls = ctypes.c_int32()
+        _check(load().fengine_stage_times(self._h, ms, ctypes.byref(calls)))
+        return dict(zip(self.STAGES, list(ms))), calls.value
+
+    def process(self, packed, first_sample: int, out, prequant=None, window_tap=None, stream=None):
+        """Enqueue one chunk. packed: uint8 CUDA tensor [ant, pol, 5L/4]; out: int8
+        CUDA tensor of info.out_bytes. Returns the first spectrum index."""
+        import torch
+        if packed.dtype != torch.uint8 or out.dtype != torch.int8:
+            raise TypeError("packed must be uint8 and out int8")
+        if packed.numel() != self.n_antennas * 2 * self.chunk_samples * 5 // 4:
+            raise ValueError("packed has the wrong size")
+        if out.numel() != self.info.out_bytes:
+            raise ValueError("out has the wrong size")
+        if prequant is not None and prequant.numel() != self.n_antennas * 2 * self.M * self.n_channels * 2:
+            raise ValueError("prequant has the wrong size")
+        if window_tap is not None and window_tap.numel() != self.n_antennas * 2 * self.M * self.N:
+            raise ValueError("window_tap has the wrong size")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        fs = ctypes.c_int64()
+        _check(load().fengine_process_chunk(self._h, ctypes.c_void_p(s.cuda_stream), _ptr(packed),
+                                            first_sample, _ptr(out), _ptr(prequant), _ptr(window_tap),
+                                            ctypes.byref(fs)))
+        return fs.value

@@ -1,0 +1,93 @@
+"""Host-side checks of the C ABI (no GPU): the library builds and loads,
+exports every symbol include/fengine.h declares, and its host-only entry
+points agree with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2303_09886_gb300 import build, fengine
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return fengine.load()
+
+
+def _declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "fengine.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fengine_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_symbols()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(fengine.EXPORTS) == declared
+
+
+def test_abi_version_and_strerror(lib):
+    assert lib.fengine_abi_version() == 1
+    for st in range(9):
+        assert lib.fengine_strerror(st)
+    assert b"unknown" in lib.fengine_strerror(99)
+
+
+@pytest.mark.parametrize("n,T", [(8, 2), (1024, 16), (8192, 16), (32768, 4)])
+def test_default_weights_match_oracle(lib, n, T):
+    w32 = fengine.default_weights(n, T)
+    w64 = O.pfb_weights(2 * n, T)
+    assert np.max(np.abs(w32.astype(np.float64) - w64)) <= 2.0 ** -24 * np.max(np.abs(w64))
+
+
+def test_quantiser_matches_oracle_on_every_tie_and_neighbour(lib):
+    """The kernels' FP32 quantiser (same source, run on the host) against the
+    oracle's round-half-away-and-saturate: every half-integer in [-130, 130],
+    its float neighbours, and a dense random sample."""
+    xs = []
+    for k in range(-260, 261):
+        h = np.float32(k / 2.0)
+        v = h
+        for _ in range(4):
+            xs.append(v)
+            v = np.nextafter(v, np.float32(np.inf), dtype=np.float32)
+        v = h
+        for _ in range(4):
+            v = np.nextafter(v, np.float32(-np.inf), dtype=np.float32)
+            xs.append(v)
+    xs += list(np.random.default_rng(1).uniform(-140, 140, 20000).astype(np.float32))
+    xs += [np.float32(v) for v in (0.0, -0.0, 1e-30, -1e-30, 0.49999997, -0.49999997, 1e30, -1e30)]
+    for x in xs:
+        assert fengine.quantise(float(x)) == O.quantise(float(x)), x
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(n_pols=3), 1), (dict(n_channels=1000), 1), (dict(n_taps=3), 1),
+    (dict(chunk_samples=1000), 1), (dict(spectra_per_heap=10 ** 6), 1),
+    (dict(max_delay_samples=-1), 1), (dict(n_antennas=0), 1)])
+def test_plan_config_validation_before_any_device_call(lib, kw, status):
+    cfg = dict(n_antennas=1, n_pols=2, n_channels=1024, n_taps=16, chunk_samples=2048 * 8,
+               spectra_per_heap=0, precision=0, max_delay_samples=0, weights=None)
+    cfg.update(kw)
+    c = fengine.Config(**cfg)
+    h = ctypes.c_void_p()
+    assert lib.fengine_plan_create(ctypes.byref(c), ctypes.byref(h)) == status
+    assert not h.value
+    assert lib.fengine_last_error()
+
+
+def test_binding_refuses_without_library(tmp_path):
+    with pytest.raises(fengine.FEngineError):
+        fengine._lib, saved = None, fengine._lib
+        try:
+            fengine.load(str(tmp_path / "missing.so"))
+        finally:
+            fengine._lib = saved
