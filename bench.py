@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 F-engine hot path.
+
+One step = one fengine_process_chunk call: every stage of the hot path over
+one chunk of every stream of the workload (default: 4 antennas x 2 pols x
+2^25 samples/pol, 8192 channels, 16 taps). Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 2] [--impl fengine|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+comparison arm): each step is a bounded sample of the same workload.
+Under torchrun every rank runs an independent replica (no collective on the
+data path: the streams are independent), timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "input Gsample/s per GB300 (8K-ch, 16-tap), TC/batched vs FP32 plain; % HBM roofline"
+UNIT = "Gsample/s"
+
+# DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by the hash of the kernel sources it was
+# taken on; reported as null once the sources change.
+NCU_TRAFFIC = {}
+
+
+def _src_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2303_09886_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the loop runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+
+    def summary(self, t0: float, t1: float):
+        rows = [r for ts, r in self.rows if t0 - 0.15 <= ts <= t1 + 0.15 and len(r) >= 9]
+        if not rows:
+            rows = [r for ts, r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, wl):
+    """Comparison arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+
+    cores = os.cpu_count() or 1
+    # bounded sample of the workload: antenna 0, both pols, one full chunk
+    n_spec = wl.chunk_samples // wl.N
+    T = wl.n_taps
+    w = O.pfb_weights(wl.N, T)
+    dl = {(a, p): (d, r, ph, pr) for a, p, d, r, ph, pr in wl.delays()}
+    g = wl.gains()
+    from paper_2303_09886_gb300 import synth
+    pk = [synth.pack10(wl.samples(0, p, wl.chunk_samples)) for p in range(2)]
+    n_out = n_spec - T + 1          # spectra whose windows lie inside the chunk
+
+    def step():
+        q = []
+        for p in range(2):
+            s = O.unpack10(pk[p], wl.chunk_samples)
+            d, r, ph, pr = dl[(0, p)]
+            gains = np.ones(wl.n_channels) if g is None else g[0, p]
+            _, qq, _ = O.channelize(s, 0, wl.N, T, w, O.DelayModel.constant(d, ph, r, pr), gains,
+                                    0, n_out)
+            q.append(qq)
+        O.corner_turn(q[0], q[1], min(256, n_out))
+        return 2 * n_out * wl.N
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    samples = 0
+    for _ in range(args.steps):
+        samples += step()
+    dt = time.perf_counter() - t0
+    value = samples / dt / 1e9
+    sample_desc = (f"antenna 0 of {wl.n_antennas}, both pols, spectra 0..{n_out - 1} of one "
+                   f"{wl.chunk_samples}-sample chunk per step (unpack + FIR + FFT + delay/gain + "
+                   f"quantise + corner turn, FP64)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.description, "name": wl.name},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(wl, budget_s: float = 15.0):
+    """The oracle as it stands on the host cores, on a bounded sample: antenna 0,
+    pol 0, as many whole 64-spectrum blocks of the chunk as fit the budget."""
+    from oracle import oracle as O
+    from paper_2303_09886_gb300 import synth
+
+    T, N = wl.n_taps, wl.N
+    w = O.pfb_weights(N, T)
+    d, r, ph, pr = [x[2:] for x in wl.delays() if x[0] == 0 and x[1] == 0][0]
+    g = wl.gains()
+    gains = np.ones(wl.n_channels) if g is None else g[0, 0]
+    blk = 64
+    n_spec = wl.chunk_samples // N
+    s_all = wl.samples(0, 0, wl.chunk_samples)
+    samples = 0
+    t0 = time.perf_counter()
+    q0 = 0
+    while q0 + blk - 1 + T <= n_spec and time.perf_counter() - t0 < budget_s:
+        lo = max(0, N * q0 - wl.max_delay)
+        lo -= lo % 4
+        hi = N * (q0 + blk - 1 + T)
+        s = O.unpack10(synth.pack10(s_all[lo:hi]), hi - lo)
+        O.channelize(s, lo, N, T, w, O.DelayModel.constant(d, ph, r, pr), gains, q0, blk)
+        samples += blk * N
+        q0 += blk
+    dt = time.perf_counter() - t0
+    return {"value": samples / dt / 1e9, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"antenna 0 pol 0, {samples // N} spectra ({samples} samples) of one chunk of "
+                      f"{wl.name}: unpack + FIR + FFT + delay/gain + quantise, FP64, OpenMP over spectra"}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--impl", default="fengine", choices=["fengine", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--antennas", type=int, default=0, help="override the workload's antenna count")
+    ap.add_argument("--chunk-samples", type=int, default=0, help="override the chunk length")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)
+
+    from paper_2303_09886_gb300.workloads import WORKLOADS
+    wl = WORKLOADS[args.workload]
+    if args.antennas or args.chunk_samples:
+        import dataclasses
+        wl = dataclasses.replace(wl, n_antennas=args.antennas or wl.n_antennas,
+                                 chunk_samples=args.chunk_samples or wl.chunk_samples)
+        wl.description += f" [scaled: {wl.n_antennas} ant, {wl.chunk_samples} samples/pol]"
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2303_09886_gb300 import build as fe_build
+    from paper_2303_09886_gb300 import fengine
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fe_build.build() if rank == 0 else None
+    if ws > 1:
+        dist.barrier()
+    fengine.load()
+
+    plan = fengine.Plan(wl.n_antennas, wl.n_channels, wl.n_taps, wl.chunk_samples,
+                        spectra_per_heap=wl.spectra_per_heap, max_delay_samples=wl.max_delay)
+    for a, p, d, r, ph, pr in wl.delays():
+        plan.set_delay(a, p, d, r, ph, pr)
+    g = wl.gains()
+    if g is not None:
+        for a in range(wl.n_antennas):
+            for p in range(2):
+                plan.set_gains(a, p, g[a, p])
+    h_in = torch.from_numpy(wl.packed_chunk()).pin_memory()
+    d_in = h_in.cuda()
+    d_out = torch.empty(plan.info.out_bytes, dtype=torch.int8, device="cuda")
+    stream = torch.cuda.current_stream()
+    L = wl.chunk_samples
+    t_next = [0]
+
+    def step():
+        plan.process(d_in, t_next[0], d_out, stream=stream)
+        t_next[0] += L
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.warmup):
+        step()
+    plan.set_profiling(True)
+    plan.stage_times()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    if ws > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    stage_ms, calls = plan.stage_times()
+    plan.set_profiling(False)
+    ms_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * wl.samples_per_step * args.steps / (ms_max / 1e3) / 1e9
+
+    # end to end through the public API with host buffers: H2D of the packed
+    # chunk from pinned memory, the call, D2H of the 8-bit output, every step
+    e2e = None
+    if not args.no_e2e:
+        h_out = torch.empty(plan.info.out_bytes, dtype=torch.int8).pin_memory()
+        for _ in range(2):
+            d_in.copy_(h_in, non_blocking=True)
+            step()
+            h_out.copy_(d_out, non_blocking=True)
+        torch.cuda.synchronize()
+        k2 = max(3, min(args.steps, 20))
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(k2):
+            d_in.copy_(h_in, non_blocking=True)
+            step()
+            h_out.copy_(d_out, non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        ems = e2.elapsed_time(e3)
+        if ws > 1:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": ws * wl.samples_per_step * k2 / (ems / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_in.numel()), "d2h_bytes_per_step": int(h_out.numel()),
+               "steps": k2}
+    clocks.stop()
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (algorithmic bytes per launch / mean launch time)
+    N1 = plan.info.fft_n1
+    inter = (N1 // 2 + 1) / N1 * 8.0          # bytes of FP32 intermediate per input sample
+    spl = wl.samples_per_step
+    bytes_per_sample = {"phase1": 1.25 + inter, "phase2": inter + 1.0}
+    dom = max(("phase1", "phase2"), key=lambda k: stage_ms[k])
+    launch_ms = stage_ms[dom] / max(calls, 1)
+    peak, peak_kind = _peaks()
+    achieved = bytes_per_sample[dom] * spl / (launch_ms / 1e3) / 1e9
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("src") == _src_hash() else None
+    step_ms = ms_max / args.steps
+    path_alg = 2.25 * spl / (step_ms / 1e3) / 1e9
+    path_all = (2.25 + 2 * inter) * spl / (step_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.description, "name": wl.name, "n_antennas": wl.n_antennas,
+                   "n_channels": wl.n_channels, "n_taps": wl.n_taps, "chunk_samples": wl.chunk_samples,
+                   "precision": "fp32", "parallelism": f"replicas x{ws}",
+                   "l2": f"inputs larger than L2: {h_in.numel() >> 20} MiB packed in + "
+                         f"{plan.info.out_bytes >> 20} MiB out per step"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_sample": bytes_per_sample[dom],
+                     "launch_ms": launch_ms},
+        "path": {"stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()},
+                 "algorithmic_GBps": path_alg, "frac_algorithmic": path_alg / peak,
+                 "with_intermediates_GBps": path_all, "frac_with_intermediates": path_all / peak,
+                 "bytes_per_sample": {"algorithmic": 2.25, "with_intermediates": 2.25 + 2 * inter}},
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks.summary(w0, w1),
+    }
+    if not args.no_cpu and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

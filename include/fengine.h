@@ -64,7 +64,7 @@ typedef enum {
 typedef struct {
     int32_t n_antennas;        /* >= 1 */
     int32_t n_pols;            /* must be 2 (dual-polarisation F-engine) */
-    int32_t n_channels;        /* n: power of two, 8 <= n <= 32768 */
+    int32_t n_channels;        /* n: power of two, 16 <= n <= 32768 */
     int32_t n_taps;            /* T: one of 1, 2, 4, 8, 16, 32 */
     int64_t chunk_samples;     /* L per polarisation per call: a positive multiple of 2n */
     int32_t spectra_per_heap;  /* S: 1 <= S <= L/2n; 0 selects min(256, L/2n) */

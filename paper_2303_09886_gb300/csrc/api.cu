@@ -181,7 +181,7 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     const int n = cfg->n_channels, T = cfg->n_taps;
     if (cfg->n_antennas < 1) return fail(FENGINE_EINVAL, "n_antennas must be >= 1");
     if (cfg->n_pols != 2) return fail(FENGINE_EINVAL, "n_pols must be 2");
-    if (!is_pow2(n) || n < 8 || n > 32768) return fail(FENGINE_EINVAL, "n_channels must be a power of two in [8, 32768]");
+    if (!is_pow2(n) || n < 16 || n > 32768) return fail(FENGINE_EINVAL, "n_channels must be a power of two in [16, 32768]");
     if (!(T == 1 || T == 2 || T == 4 || T == 8 || T == 16 || T == 32))
         return fail(FENGINE_EINVAL, "n_taps must be one of 1, 2, 4, 8, 16, 32");
     const long long N = 2LL * n;

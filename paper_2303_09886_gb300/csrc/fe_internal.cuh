@@ -85,7 +85,6 @@ inline int phase2_R2(int N2) {
     if (r < 1) r = 1;
     return r;
 }
-size_t phase1_smem_bytes(int T, int C);
 size_t phase2_smem_bytes(int N2, int R2);
 
 }  // namespace fe

@@ -8,7 +8,6 @@ namespace fe {
 template <int T>
 cudaError_t launch_phase1_n1(int N1, const Phase1Params &p, int n_streams, cudaStream_t s);
 
-size_t phase1_smem_bytes(int T, int C) { return (size_t)(kP1Rows + T - 1) * C * sizeof(float); }
 
 cudaError_t launch_phase1(int T, int N1, const Phase1Params &p, int n_streams, cudaStream_t s) {
     switch (T) {

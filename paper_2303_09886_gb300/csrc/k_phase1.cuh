@@ -9,98 +9,147 @@
 //
 // One CTA owns a tile of kP1Rows consecutive spectra x C = N1 * W columns
 // {N2 t1 + t2 : t1 < N1, t2 in [t2_0, t2_0 + W)} of one (antenna, pol)
-// stream. It
-//   1. unpacks the (kP1Rows + T - 1) rows of delayed samples the tile needs
-//      into shared memory as FP32 (exact for 10-bit integers), one run of
-//      constant coarse delay at a time (Sec. 3.3: each PFB window uses one
-//      consistent delay);
+// stream. For each run of spectra with one coarse delay (Sec. 3.3: each PFB
+// window uses one consistent delay) it
+//   1. unpacks the (rows + T - 1) x N1 row segments of delayed samples into
+//      shared memory as FP32 (exact for 10-bit integers): every thread decodes
+//      whole 5-byte groups of 4 samples aligned to the packed stream, so each
+//      segment of W samples is stored with its 0-3 sample misalignment;
 //   2. runs the T-tap FIR down each column with the weights and a sliding
 //      window of T samples in registers (one shared-memory load and T FMAs
 //      per output), writing g in place;
-//   3. for each (spectrum, t2) does the real N1-point DFT over t1 in
-//      registers (an N1/2-point complex FFT of even/odd pairs plus the
-//      split), multiplies by the twiddle and stores B to the intermediate.
+// and finally, for each (spectrum, t2), does the real N1-point DFT over t1
+// in registers (an N1/2-point complex FFT of even/odd pairs plus the split),
+// multiplies by the twiddle and stores B to the intermediate.
 #pragma once
 #include "fe_device.cuh"
 #include "fe_internal.cuh"
 
 namespace fe {
 
-template <int T, int N1>
-__global__ void __launch_bounds__(512) k_phase1(const Phase1Params p) {
-    constexpr int R = kP1Rows;
-    constexpr int H1 = N1 / 2;
-    extern __shared__ float xs[];              // [(R + T - 1)][C]
-    __shared__ int c_sm[R];
-    __shared__ float2 tw_sm[33];               // exp(-2 pi i q / 64)
+constexpr int kP1Threads = 256;
 
-    const int C = p.C, W = p.W, N = p.N, N2 = p.N2;
+template <int T, int N1, int W>
+struct P1Shape {
+    static constexpr int R = kP1Rows;
+    static constexpr int NG = (W + 3) / 4 + 1;   // 4-sample groups per row segment
+    static constexpr int SW = 4 * NG;            // shared-memory floats per row segment
+    static constexpr int ROW = N1 * SW;          // floats per tile row
+    static constexpr int C = N1 * W;             // FIR columns per tile
+    static constexpr int ROWS = R + T - 1;
+};
+
+// 4 samples of the 5-byte group starting at packed byte b (MSB first,
+// 10-bit two's complement), as exact floats.
+__device__ __forceinline__ float4 unpack_group(const uint8_t *__restrict__ p, long long b) {
+    const unsigned b0 = __ldg(p + b), b1 = __ldg(p + b + 1), b2 = __ldg(p + b + 2),
+                   b3 = __ldg(p + b + 3), b4 = __ldg(p + b + 4);
+    const unsigned hi = (b0 << 24) | (b1 << 16) | (b2 << 8) | b3;   // bits 0..31 of the group
+    const unsigned u0 = hi >> 22;
+    const unsigned u1 = (hi >> 12) & 0x3FFu;
+    const unsigned u2 = (hi >> 2) & 0x3FFu;
+    const unsigned u3 = ((hi & 0x3u) << 8) | b4;
+    // two's complement 10-bit: v = (u ^ 512) - 512
+    return make_float4((float)((int)(u0 ^ 0x200u) - 512), (float)((int)(u1 ^ 0x200u) - 512),
+                       (float)((int)(u2 ^ 0x200u) - 512), (float)((int)(u3 ^ 0x200u) - 512));
+}
+
+template <int T, int N1, int W>
+__global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) {
+    using S = P1Shape<T, N1, W>;
+    constexpr int R = S::R, H1 = N1 / 2;
+    extern __shared__ float xs[];              // [ROWS][N1][SW]
+    __shared__ int c_sm[R];
+    __shared__ int off_sm[R];                  // segment misalignment of each row's run
+    __shared__ float2 tw_sm[33];               // exp(-2 pi i q / 64)
+    __shared__ float2 tw1_sm[(H1 + 1) * W];    // exp(-2 pi i k1 t2 / N) for this tile's t2
+
+    const int N = p.N, N2 = p.N2;
     const int stream = blockIdx.z;
     const int t2_0 = blockIdx.x * W;
     const int q0 = blockIdx.y * R;
     const int Rv = min(R, p.M - q0);
     const uint8_t *chunk = p.chunk + (long long)stream * p.chunk_bytes;
     const uint8_t *hist = p.hist + (long long)stream * p.hist_bytes;
-    const long long base = p.t_in - p.H;       // absolute index of history sample 0
+    const long long HL = p.H + p.L;
+    // rel index (from the first history sample) of tile row 0, column t = 0, before the delay
+    const long long rel_base = (long long)N * (p.m0 + q0) - (p.t_in - p.H) + t2_0;
 
-    for (int i = threadIdx.x; i < Rv; i += blockDim.x) c_sm[i] = p.ctab[(long long)stream * p.M + q0 + i];
-    for (int i = threadIdx.x; i < 33; i += blockDim.x) {
+    for (int i = threadIdx.x; i < Rv; i += kP1Threads) c_sm[i] = p.ctab[(long long)stream * p.M + q0 + i];
+    for (int i = threadIdx.x; i < 33; i += kP1Threads) {
         float s, c;
         sincospif(-(float)i / 32.0f, &s, &c);
         tw_sm[i] = make_float2(c, s);
     }
+    for (int i = threadIdx.x; i < (H1 + 1) * W; i += kP1Threads) {
+        const int k = i / W, w = i % W;
+        tw1_sm[i] = __ldg(p.tw1 + (long long)k * N2 + t2_0 + w);
+    }
     __syncthreads();
 
+    int off = 0;   // misalignment (0..3) of every segment of the current run
     int ra = 0;
     while (ra < Rv) {
         const int cd = c_sm[ra];
         int rb = ra + 1;
         while (rb < Rv && c_sm[rb] == cd) rb++;
-        // 1. delayed samples for rows [ra, rb + T - 1)
+        const long long rel0 = rel_base - cd;  // rel of (row 0, t1 0, w 0) at this delay
+        off = (int)(rel0 & 3);
+        // 1. unpack rows [ra, rb + T - 1), whole aligned groups
         const int rows = rb + T - 1 - ra;
-        for (int e = threadIdx.x; e < rows * C; e += blockDim.x) {
-            const int row = ra + e / C, col = e % C;
-            const int t = N2 * (col / W) + t2_0 + (col % W);
-            const long long i = (long long)N * (p.m0 + q0 + row) - cd + t;
-            const long long rel = i - base;
-            const int v = rel < p.H ? fetch10(hist, rel) : fetch10(chunk, rel - p.H);
-            xs[row * C + col] = (float)v;
-            if (p.window_tap && row < rb)
-                p.window_tap[((long long)stream * p.M + q0 + row) * N + t] = v;
+        for (int e = threadIdx.x; e < rows * N1 * S::NG; e += kP1Threads) {
+            const int gi = e % S::NG;
+            const int seg = e / S::NG;
+            const int t1 = seg % N1, row = ra + seg / N1;
+            const long long g = ((rel0 + (long long)N * row + (long long)N2 * t1) & ~3LL) + 4 * gi;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < HL) v = g < p.H ? unpack_group(hist, (g >> 2) * 5) : unpack_group(chunk, ((g - p.H) >> 2) * 5);
+            *reinterpret_cast<float4 *>(xs + row * S::ROW + t1 * S::SW + 4 * gi) = v;
         }
         __syncthreads();
+        if (p.window_tap) {
+            for (int e = threadIdx.x; e < (rb - ra) * S::C; e += kP1Threads) {
+                const int row = ra + e / S::C, col = e % S::C;
+                const int t1 = col / W, w = col % W;
+                p.window_tap[((long long)stream * p.M + q0 + row) * N + N2 * t1 + t2_0 + w] =
+                    (int)xs[row * S::ROW + t1 * S::SW + off + w];
+            }
+            __syncthreads();   // the FIR below overwrites these slots in place
+        }
         // 2. FIR down each column, g written over the row it starts at
-        for (int col = threadIdx.x; col < C; col += blockDim.x) {
-            const int t = N2 * (col / W) + t2_0 + (col % W);
+        for (int col = threadIdx.x; col < S::C; col += kP1Threads) {
+            const int t1 = col / W, w = col % W;
+            const int t = N2 * t1 + t2_0 + w;
+            float *x = xs + t1 * S::SW + off + w;
             float wr[T], win[T];
 #pragma unroll
             for (int j = 0; j < T; j++) wr[j] = __ldg(p.w + t + (long long)N * j);
 #pragma unroll
             for (int row = 0; row < R + T - 1; row++) {
-                if (row >= ra && row < rb + T - 1) win[row % T] = xs[row * C + col];
+                if (row >= ra && row < rb + T - 1) win[row % T] = x[row * S::ROW];
                 const int r = row - (T - 1);
                 if (r >= ra && r < rb) {
                     float acc = 0.0f;
 #pragma unroll
                     for (int j = 0; j < T; j++) acc = fmaf(wr[j], win[(r + j) % T], acc);
-                    xs[r * C + col] = acc;
+                    x[r * S::ROW] = acc;
                 }
             }
         }
+        for (int r = ra + (int)threadIdx.x; r < rb; r += kP1Threads) off_sm[r] = off;
         __syncthreads();
         ra = rb;
     }
 
     // 3. real N1-point DFT over t1, twiddle, store B[k1][t2]
-    for (int pi = threadIdx.x; pi < Rv * W; pi += blockDim.x) {
+    for (int pi = threadIdx.x; pi < Rv * W; pi += kP1Threads) {
         const int r = pi / W, w = pi % W;
-        const float *g = xs + r * C + w;
+        const float *g = xs + r * S::ROW + off_sm[r] + w;
         float2 z[H1];
 #pragma unroll
-        for (int q = 0; q < H1; q++) z[q] = make_float2(g[(2 * q) * W], g[(2 * q + 1) * W]);
+        for (int q = 0; q < H1; q++) z[q] = make_float2(g[(2 * q) * S::SW], g[(2 * q + 1) * S::SW]);
         fft_reg<H1>(z, tw_sm);
-        const int t2 = t2_0 + w;
-        float2 *out = p.A + ((long long)stream * p.M + q0 + r) * (H1 + 1) * N2 + t2;
+        float2 *out = p.A + ((long long)stream * p.M + q0 + r) * (H1 + 1) * N2 + t2_0 + w;
 #pragma unroll
         for (int k = 0; k <= H1; k++) {
             const float2 zk = z[k % H1], zm = z[(H1 - k) % H1];
@@ -108,30 +157,34 @@ __global__ void __launch_bounds__(512) k_phase1(const Phase1Params p) {
             const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
             const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
             const float2 a = cadd(E, cmul(tw_sm[k * (64 / N1)], O));
-            out[(long long)k * N2] = cmul(a, __ldg(p.tw1 + (long long)k * N2 + t2));
+            out[(long long)k * N2] = cmul(a, tw1_sm[k * W + w]);
         }
     }
 }
 
-template <int T, int N1>
-cudaError_t launch_phase1_t(const Phase1Params &p, int n_streams, cudaStream_t s) {
-    const int threads = p.C < 512 ? p.C : 512;
-    const size_t smem = phase1_smem_bytes(T, p.C);
-    cudaError_t e = cudaFuncSetAttribute(k_phase1<T, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int T, int N1, int W>
+cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t s) {
+    using S = P1Shape<T, N1, W>;
+    if (p.W != W || p.N2 % W) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)S::ROWS * S::ROW * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_phase1<T, N1, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(p.N2 / p.W, (p.M + kP1Rows - 1) / kP1Rows, n_streams);
-    k_phase1<T, N1><<<grid, threads, smem, s>>>(p);
+    dim3 grid(p.N2 / W, (p.M + kP1Rows - 1) / kP1Rows, n_streams);
+    k_phase1<T, N1, W><<<grid, kP1Threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <int T>
 cudaError_t launch_phase1_n1(int N1, const Phase1Params &p, int n_streams, cudaStream_t s) {
-    switch (N1) {
-        case 8: return launch_phase1_t<T, 8>(p, n_streams, s);
-        case 16: return launch_phase1_t<T, 16>(p, n_streams, s);
-        case 32: return launch_phase1_t<T, 32>(p, n_streams, s);
-        case 64: return launch_phase1_t<T, 64>(p, n_streams, s);
+    switch (N1 * 1000 + p.W) {
+        case 8032: return launch_phase1_tw<T, 8, 32>(p, n_streams, s);
+        case 16032: return launch_phase1_tw<T, 16, 32>(p, n_streams, s);
+        case 32032: return launch_phase1_tw<T, 32, 32>(p, n_streams, s);
+        case 64008: return launch_phase1_tw<T, 64, 8>(p, n_streams, s);
+        case 8016: return launch_phase1_tw<T, 8, 16>(p, n_streams, s);
+        case 8008: return launch_phase1_tw<T, 8, 8>(p, n_streams, s);
+        case 8004: return launch_phase1_tw<T, 8, 4>(p, n_streams, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -11,6 +11,17 @@
 // class N1 - k1. Classes k1 = 0 and k1 = N1/2 map onto themselves, so their
 // CTAs keep only the lower half. Every channel in [0, n) is written once.
 //
+// FFT: in-place decimation in frequency, radix 16 while possible, then one
+// radix-2/4/8 stage; each thread holds 16 points in registers per stage. The
+// result is left in digit-reversed order and read back through the index map
+// in the epilogue. Shared memory rows are padded by one complex per 16 so
+// that every stage and the epilogue are free of bank conflicts.
+//
+// Rotation: exp(i phi) exp(-2 pi i delta k / N) for k = k1 + N1 k2 is the
+// product of a per-(spectrum, pol) table over the high bits of k2 (with the
+// exp(i phi) and k1 factors folded in) and one over the low 5 bits, built
+// with sincospif at the start of the CTA.
+//
 // The CTA writes, for each of its channels, R2 consecutive spectra x 2 pols
 // x (re, im) = 4 R2 contiguous bytes of one heap row.
 #include "fe_device.cuh"
@@ -18,141 +29,234 @@
 
 namespace fe {
 
-template <int RP>
-__device__ __forceinline__ void dft_small(float2 (&v)[RP]);
+namespace {
 
-template <>
-__device__ __forceinline__ void dft_small<2>(float2 (&v)[2]) {
-    const float2 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+constexpr int kP2Threads = 512;
+
+// exp(-2 pi i q / 16), q = 0..15, as compile-time constants.
+__device__ __forceinline__ float2 w16(int q) {
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+    constexpr float re[16] = {1.f, c1, h, s1, 0.f, -s1, -h, -c1, -1.f, -c1, -h, -s1, 0.f, s1, h, c1};
+    constexpr float im[16] = {0.f, -s1, -h, -c1, -1.f, -c1, -h, -s1, 0.f, s1, h, c1, 1.f, c1, h, s1};
+    return make_float2(re[q], im[q]);
 }
 
-template <>
-__device__ __forceinline__ void dft_small<4>(float2 (&v)[4]) {
-    const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    const float2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
-    const float2 mi_t3 = make_float2(t3.y, -t3.x);   // -i * t3
-    v[0] = cadd(t0, t2);
-    v[2] = csub(t0, t2);
-    v[1] = cadd(t1, mi_t3);
-    v[3] = csub(t1, mi_t3);
-}
-
-// One radix-RP Stockham pass (self-sorting, decimation in time) over nseq
-// sequences of length N2 stored at rows of stride LD. Ns is the length of
-// the sub-transforms already done. Butterfly j reads x[j + r N2/RP],
-// multiplies by exp(-2 pi i r (j mod Ns) / (Ns RP)), takes an RP-point DFT
-// and writes y[(j / Ns) Ns RP + (j mod Ns) + r Ns]. In place: every thread
-// holds its butterflies in registers across a barrier.
-template <int RP, int K>
-__device__ __forceinline__ void stockham_pass(float2 *buf, int LD, int N2, int Ns, int nseq,
-                                              const float2 *__restrict__ tw2) {
-    const int B = N2 / RP;
-    const int slots = (int)blockDim.x * K;
-    const int spr = slots / B > 0 ? slots / B : 1;
-    const int twstride = N2 / (Ns * RP);
-    for (int s0 = 0; s0 < nseq; s0 += spr) {
-        float2 v[K][RP];
-        int dst[K];
-        bool act[K];
+// In-register R-point DFT (R = 2, 4, 8, 16), natural order in and out,
+// radix-2 decimation in time with compile-time twiddles.
+template <int R>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
 #pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int b = threadIdx.x + kk * blockDim.x;
-            const int sq = s0 + b / B, j = b % B;
-            act[kk] = (b < spr * B) && (sq < nseq);
-            dst[kk] = 0;
-            if (act[kk]) {
-                const float2 *x = buf + sq * LD;
-                const int k = j % Ns;
+    for (int i = 0; i < R; i++) {
+        const int j = bitrev<R>(i);
+        if (i < j) {
+            float2 t = v[i];
+            v[i] = v[j];
+            v[j] = t;
+        }
+    }
 #pragma unroll
-                for (int r = 0; r < RP; r++) {
-                    float2 a = x[j + r * B];
-                    if (r > 0) a = cmul(a, __ldg(tw2 + r * k * twstride));
-                    v[kk][r] = a;
-                }
-                dft_small<RP>(v[kk]);
-                dst[kk] = sq * LD + (j / Ns) * Ns * RP + k;
+    for (int len = 2; len <= R; len <<= 1) {
+#pragma unroll
+        for (int i = 0; i < R; i += len) {
+#pragma unroll
+            for (int j = 0; j < len / 2; j++) {
+                const float2 w = w16(j * (16 / len));
+                float2 b = v[i + j + len / 2];
+                if (j != 0) b = cmul(b, w);
+                const float2 a = v[i + j];
+                v[i + j] = cadd(a, b);
+                v[i + j + len / 2] = csub(a, b);
             }
         }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            if (act[kk]) {
-#pragma unroll
-                for (int r = 0; r < RP; r++) buf[dst[kk] + r * Ns] = v[kk][r];
-            }
-        }
-        __syncthreads();
     }
 }
 
-template <int N2>
-__global__ void __launch_bounds__(256) k_phase2(const Phase2Params p) {
-    extern __shared__ float2 buf[];            // [2 R2][N2 + 1]
-    constexpr int LD = N2 + 1;
-    const int k1 = blockIdx.x, ant = blockIdx.z;
-    const int R2 = p.R2, q0 = blockIdx.y * R2;
-    const int M = p.M, Rv = min(R2, M - q0);
-    const int N1 = p.N1, H1 = N1 / 2, N = p.N, n = N / 2, S = p.S;
-    const int nseq = 2 * Rv;
+// padded shared-memory index of element e of a sequence
+__device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
 
-    for (int e = threadIdx.x; e < nseq * N2; e += blockDim.x) {
+template <int N2>
+struct P2Shape {
+    static constexpr int P = N2 < 16 ? N2 : 16;                   // points per thread per stage
+    static constexpr int TPS = N2 / P;                            // threads per sequence
+    static constexpr int R2 = (8192 / N2) > 32 ? 32 : (8192 / N2); // spectra per CTA
+    static constexpr int LD = N2 + N2 / 16 + 1;                   // padded row stride
+    static constexpr int LO = N2 < 32 ? N2 : 32;                  // rotation low table size
+    static constexpr int HI = N2 / LO;                            // rotation high table size
+};
+
+// One DIF stage of radix R over spans of length Lspan (R divides Lspan).
+// Butterfly (block b, j): v[r] = x[b Lspan + j + r Lspan/R]; V = DFT_R(v);
+// x[b Lspan + j + k Lspan/R] = V[k] exp(-2 pi i j k / Lspan).
+template <int N2, int R, int Lspan>
+__device__ __forceinline__ void dif_stage(float2 *buf, int nseq, const float2 *tw) {
+    using S = P2Shape<N2>;
+    constexpr int PER = S::P / R;                 // butterflies per thread (16 points total)
+    constexpr int sub = Lspan / R;
+    constexpr int seq_per_round = kP2Threads / S::TPS;
+    constexpr int tws = N2 / Lspan;               // twiddle table stride
+    for (int s0 = 0; s0 < nseq; s0 += seq_per_round) {
+        const int sq = s0 + (int)threadIdx.x / S::TPS;
+        const int tl = (int)threadIdx.x % S::TPS;
+        if (sq < nseq) {
+            float2 *x = buf + sq * S::LD;
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                const int bf = tl + u * S::TPS;   // butterfly index in [0, per_seq)
+                const int blk = bf / sub, j = bf - blk * sub;
+                const int base = blk * Lspan + j;
+                float2 v[R];
+#pragma unroll
+                for (int r = 0; r < R; r++) v[r] = x[pad(base + r * sub)];
+                dft_reg<R>(v);
+                if constexpr (Lspan != R) {
+#pragma unroll
+                    for (int k = 1; k < R; k++) v[k] = cmul(v[k], tw[j * k * tws]);
+                }
+#pragma unroll
+                for (int r = 0; r < R; r++) x[pad(base + r * sub)] = v[r];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// All DIF stages: radix 16 while the span allows, then the remaining radix.
+template <int N2, int Lspan>
+__device__ __forceinline__ void dif_all(float2 *buf, int nseq, const float2 *tw) {
+    if constexpr (Lspan >= 16) {
+        dif_stage<N2, 16, Lspan>(buf, nseq, tw);
+        dif_all<N2, Lspan / 16>(buf, nseq, tw);
+    } else if constexpr (Lspan > 1) {
+        dif_stage<N2, Lspan, Lspan>(buf, nseq, tw);
+    }
+}
+
+// Position of F[k2] after the DIF stages (digit reversal of k2 in the radix
+// sequence 16, 16, ..., R_last).
+template <int N2>
+__device__ __forceinline__ int dif_pos(int k2) {
+    int p = 0, L = N2, k = k2;
+#pragma unroll
+    for (int s = 0; s < 12; s++) {
+        if (L <= 1) break;
+        const int R = L >= 16 ? 16 : L;
+        L /= R;
+        p += (k % R) * L;
+        k /= R;
+    }
+    return p;
+}
+
+}  // namespace
+
+template <int N2>
+__global__ void __launch_bounds__(kP2Threads) k_phase2(const Phase2Params p) {
+    using S = P2Shape<N2>;
+    constexpr int R2 = S::R2, LD = S::LD;
+    extern __shared__ float2 sm[];
+    float2 *buf = sm;                                  // [2 R2][LD]
+    float2 *tw = buf + 2 * R2 * LD;                    // [N2] exp(-2 pi i q / N2)
+    float2 *thi = tw + N2;                             // [2 R2][HI]
+    float2 *tlo = thi + 2 * R2 * S::HI;                // [2 R2][LO]
+    float2 *qup = tlo + 2 * R2 * S::LO;                // [2 R2] upper-class factor
+    long long *rowoff = reinterpret_cast<long long *>(qup + 2 * R2);   // [R2] heap row byte offset
+    int *rowstride = reinterpret_cast<int *>(rowoff + R2);             // [R2] bytes per channel row
+
+    const int k1 = blockIdx.x, ant = blockIdx.z;
+    const int q0 = blockIdx.y * R2;
+    const int M = p.M, Rv = min(R2, M - q0);
+    const int N1 = p.N1, H1 = N1 / 2, N = p.N, n = N / 2, S_ = p.S;
+
+    // stage B[k1][.] rows in (sequence = pol * R2 + r), padded
+    for (int e = threadIdx.x; e < 2 * R2 * N2; e += kP2Threads) {
         const int sq = e / N2, t2 = e % N2;
-        const int pol = sq / Rv, r = sq - pol * Rv;
-        buf[sq * LD + t2] =
-            p.A[(((long long)(ant * 2 + pol) * M + q0 + r) * (H1 + 1) + k1) * N2 + t2];
+        const int pol = sq / R2, r = sq % R2;
+        if (r < Rv)
+            buf[sq * LD + pad(t2)] =
+                p.A[(((long long)(ant * 2 + pol) * M + q0 + r) * (H1 + 1) + k1) * N2 + t2];
+    }
+    for (int e = threadIdx.x; e < N2; e += kP2Threads) tw[e] = __ldg(p.tw2 + e);
+    // rotation tables: angle/pi = phi/pi - 2 delta k / N, k = k1 + N1 (LO a + b)
+    const float inv = 2.0f / (float)N;
+    for (int e = threadIdx.x; e < 2 * R2 * (S::HI + S::LO + 1); e += kP2Threads) {
+        const int sq = e % (2 * R2), which = e / (2 * R2);
+        const int pol = sq / R2, r = sq % R2;
+        if (r >= Rv) continue;
+        const float2 f = p.ftab[(long long)(ant * 2 + pol) * M + q0 + r];   // (delta, phi / pi)
+        float sn, cs;
+        if (which < S::HI) {
+            const float kk = (float)(k1 + N1 * S::LO * which);
+            sincospif(f.y - f.x * kk * inv, &sn, &cs);
+            thi[sq * S::HI + which] = make_float2(cs, sn);
+        } else if (which < S::HI + S::LO) {
+            const int b = which - S::HI;
+            sincospif(-f.x * (float)(N1 * b) * inv, &sn, &cs);
+            tlo[sq * S::LO + b] = make_float2(cs, sn);
+        } else {
+            // upper class: Y = G exp(2 i phi - 2 pi i delta) conj(Z)
+            sincospif(2.0f * f.y - 2.0f * f.x, &sn, &cs);
+            qup[sq] = make_float2(cs, sn);
+        }
+    }
+    if ((int)threadIdx.x < Rv) {
+        const int q = q0 + threadIdx.x;
+        const int h = q / S_, s = q - h * S_;
+        const int Sh = min(S_, M - h * S_);
+        rowoff[threadIdx.x] = (long long)h * S_ * n * 4 + s * 4;
+        rowstride[threadIdx.x] = Sh * 4;
     }
     __syncthreads();
 
-    int Ns = 1;
-    while (Ns * 4 <= N2) {
-        stockham_pass<4, 4>(buf, LD, N2, Ns, nseq, p.tw2);
-        Ns *= 4;
-    }
-    if (Ns < N2) stockham_pass<2, 4>(buf, LD, N2, Ns, nseq, p.tw2);
+    // in-place DIF FFT over the 2 Rv sequences
+    dif_all<N2, N2>(buf, 2 * R2, tw);
 
+    // epilogue: rotate, gain, quantise, corner turn
     const bool upper = (k1 != 0 && k1 != H1);
     const int nslot = upper ? N2 : N2 / 2;
-    const float inv_n2 = 2.0f / (float)N;        // 2 / N, exact
-    for (int e = threadIdx.x; e < nslot * Rv; e += blockDim.x) {
-        const int r = e % Rv, k2 = e / Rv;
+    int8_t *out_ant = p.out + (long long)ant * M * n * 4;
+    const float2 *g0 = p.gains + (long long)(ant * 2) * n;
+    const float2 *g1 = g0 + n;
+    for (int e = threadIdx.x; e < nslot * R2; e += kP2Threads) {
+        const int r = e % R2, k2 = e / R2;
+        if (r >= Rv) continue;
         const bool up = k2 >= N2 / 2;
-        const int k = up ? N - (k1 + N1 * k2) : k1 + N1 * k2;
-        const int q = q0 + r;
+        const int kc = k1 + N1 * k2;                    // this slot's DFT index
+        const int k = up ? N - kc : kc;                 // channel written
+        const int a = k2 / S::LO, b = k2 % S::LO;
+        const int pos = pad(dif_pos<N2>(k2));
         unsigned packed = 0;
 #pragma unroll
         for (int pol = 0; pol < 2; pol++) {
-            float2 F = buf[(pol * Rv + r) * LD + k2];
-            if (up) F.y = -F.y;
-            const int st = ant * 2 + pol;
-            const float2 f = p.ftab[(long long)st * M + q];    // (delta, phi / pi)
-            float sn, cs;
-            sincospif(f.y - f.x * (float)k * inv_n2, &sn, &cs);
-            const float2 g = __ldg(p.gains + (long long)st * n + k);
-            const float2 y = cmul(cmul(g, make_float2(cs, sn)), F);
-            if (p.prequant) p.prequant[((long long)st * M + q) * n + k] = y;
+            const int sq = pol * R2 + r;
+            const float2 F = buf[sq * LD + pos];
+            const float2 z = cmul(cmul(thi[sq * S::HI + a], tlo[sq * S::LO + b]), F);
+            const float2 g = __ldg((pol ? g1 : g0) + k);
+            const float2 y = up ? cmul(cmul(g, qup[sq]), cconj(z)) : cmul(g, z);
+            if (p.prequant) p.prequant[((long long)(ant * 2 + pol) * M + q0 + r) * n + k] = y;
             const unsigned qr = (unsigned)quant8(y.x) & 0xFFu, qi = (unsigned)quant8(y.y) & 0xFFu;
             packed |= (qr | (qi << 8)) << (16 * pol);
         }
-        const int h = q / S, s = q - h * S;
-        const int Sh = min(S, M - h * S);
-        const long long off = (long long)ant * M * n * 4 + (long long)h * S * n * 4 +
-                              (long long)k * Sh * 4 + (long long)s * 4;
-        *reinterpret_cast<unsigned *>(p.out + off) = packed;
+        *reinterpret_cast<unsigned *>(out_ant + rowoff[r] + (long long)k * rowstride[r]) = packed;
     }
 }
 
-size_t phase2_smem_bytes(int N2, int R2) { return (size_t)2 * R2 * (N2 + 1) * sizeof(float2); }
+size_t phase2_smem_bytes(int N2, int R2) {
+    const int LD = N2 + N2 / 16 + 1;
+    const int LO = N2 < 32 ? N2 : 32, HI = N2 / LO;
+    return sizeof(float2) * ((size_t)2 * R2 * LD + N2 + 2 * R2 * (HI + LO + 1)) +
+           (sizeof(long long) + sizeof(int)) * R2;
+}
 
 template <int N2>
 static cudaError_t launch_p2(const Phase2Params &p, int n_ant, cudaStream_t s) {
-    const size_t smem = phase2_smem_bytes(N2, p.R2);
+    const int R2 = P2Shape<N2>::R2;
+    if (p.R2 != R2) return cudaErrorInvalidValue;
+    const size_t smem = phase2_smem_bytes(N2, R2);
     cudaError_t e = cudaFuncSetAttribute(k_phase2<N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(p.N1 / 2 + 1, (p.M + p.R2 - 1) / p.R2, n_ant);
-    k_phase2<N2><<<grid, 256, smem, s>>>(p);
+    dim3 grid(p.N1 / 2 + 1, (p.M + R2 - 1) / R2, n_ant);
+    k_phase2<N2><<<grid, kP2Threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -41,7 +41,7 @@ def test_abi_version_and_strerror(lib):
     assert b"unknown" in lib.fengine_strerror(99)
 
 
-@pytest.mark.parametrize("n,T", [(8, 2), (1024, 16), (8192, 16), (32768, 4)])
+@pytest.mark.parametrize("n,T", [(16, 2), (1024, 16), (8192, 16), (32768, 4)])
 def test_default_weights_match_oracle(lib, n, T):
     w32 = fengine.default_weights(n, T)
     w64 = O.pfb_weights(2 * n, T)

@@ -67,7 +67,7 @@ def test_other_fft_splits(n, T, M):
         _report(f"n={n} T={T}", compare_call(s, c, M2, S, n, T, delays, None))
 
 
-@pytest.mark.parametrize("n,T", [(8, 2), (16, 1), (64, 32), (128, 4)])
+@pytest.mark.parametrize("n,T", [(16, 2), (16, 1), (32, 8), (64, 32), (128, 4)])
 def test_tiny_transforms(n, T):
     L = 2 * n * 70
     s = streams(synth.SEED_BASE + 4, 2, 2 * L, 50.0)
