@@ -329,9 +329,12 @@ def main(argv=None):
     spl = wl.samples_per_step
     bytes_per_sample = {"phase1": 1.25 + inter, "phase2": inter + 1.0}
     dom = max(("phase1", "phase2"), key=lambda k: stage_ms[k])
-    launch_ms = stage_ms[dom] / max(calls, 1)
+    slabs = max(int(plan.info.slabs_per_chunk), 1)
+    kernel_ms_per_step = stage_ms[dom] / max(calls, 1)       # all slab launches of one step
+    launch_ms = kernel_ms_per_step / slabs                   # one launch = one slab
     peak, peak_kind = _peaks()
-    achieved = bytes_per_sample[dom] * spl / (launch_ms / 1e3) / 1e9
+    # algorithmic bytes of one launch (its slab's samples) / its mean duration
+    achieved = bytes_per_sample[dom] * (spl / slabs) / (launch_ms / 1e3) / 1e9
     tr = NCU_TRAFFIC.get(dom)
     traffic = tr["bytes_per_launch"] if tr and tr.get("src") == _src_hash() else None
     step_ms = ms_max / args.steps
@@ -349,13 +352,14 @@ def main(argv=None):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_sample": bytes_per_sample[dom],
-                     "launch_ms": launch_ms},
+                     "launch_ms": launch_ms, "launches_per_step": slabs,
+                     "slab_spectra": int(plan.info.slab_spectra)},
         "path": {"stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()},
                  "algorithmic_GBps": path_alg, "frac_algorithmic": path_alg / peak,
                  "with_intermediates_GBps": path_all, "frac_with_intermediates": path_all / peak,
                  "bytes_per_sample": {"algorithmic": 2.25, "with_intermediates": 2.25 + 2 * inter}},
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": (2 + 2 * slabs) * args.steps,
         "clocks": clocks.summary(w0, w1),
     }
     if not args.no_cpu and ws == 1:

@@ -81,11 +81,13 @@ typedef struct {
     int32_t n_channels, n_taps, n_antennas, spectra_per_heap;
     int32_t fft_n1, fft_n2;       /* four-step split N = n1 * n2 used on the device */
     int64_t spectra_per_chunk;    /* M = L / 2n: spectra every call emits per stream */
-    int64_t history_samples;      /* H = 2n (T - 1) + D rounded up to a multiple of 4 */
+    int64_t history_samples;      /* H = 2n (T - 1) + D rounded up to a multiple of 16 */
     int64_t latency_spectra;      /* T - 1: first spectrum of a call = first_sample/2n - (T-1) */
     int64_t out_bytes;            /* bytes of d_out per call: n_antennas * M * n * 4 */
     size_t device_bytes;          /* device memory the plan holds */
     size_t scratch_bytes;         /* part of device_bytes used as per-call scratch */
+    int32_t slab_spectra;         /* spectra per slab of the L2-resident two-phase pipeline */
+    int32_t slabs_per_chunk;      /* slabs (phase-1 + phase-2 launch pairs) per call */
 } fengine_info;
 
 const char *fengine_strerror(fengine_status status);
@@ -136,7 +138,7 @@ fengine_status fengine_set_gains(fengine_plan_t plan, int32_t ant, int32_t pol,
 fengine_status fengine_reset(fengine_plan_t plan);
 
 /* Channelize one chunk of every stream (Sec. 2.1 steps 1-6).
- *   d_packed       device, [antenna][pol][5L/4] bytes: samples
+ *   d_packed       device, 4-byte aligned (as is d_out), [antenna][pol][5L/4] bytes: samples
  *                  [first_sample, first_sample + L) of each stream.
  *   first_sample   multiple of 2n; after the first call (or a reset) it must
  *                  equal the previous first_sample + L, else FENGINE_ESEQ.
@@ -163,6 +165,86 @@ fengine_status fengine_process_chunk(fengine_plan_t plan, void *cuda_stream,
                                      const uint8_t *d_packed, int64_t first_sample,
                                      int8_t *d_out, float *d_prequant,
                                      int32_t *d_window_tap, int64_t *first_spectrum);
+
+/* ---- batching: many independent plans per call (uneven streams with
+ * different channel counts, tap counts and chunk lengths; engines are
+ * independent, Sec. 2.1 last paragraph) ---- */
+typedef struct fengine_batch_s *fengine_batch_t;
+
+/* One member of a batch call: the arguments fengine_process_chunk takes. */
+typedef struct {
+    fengine_plan_t plan;
+    const uint8_t *d_packed;
+    int64_t first_sample;
+    int8_t *d_out;
+} fengine_chunk_desc;
+
+/* A batch owns n_pool (1..64) internal CUDA streams. */
+fengine_status fengine_batch_create(int32_t n_pool, fengine_batch_t *out);
+fengine_status fengine_batch_destroy(fengine_batch_t batch);
+
+/* Process one chunk of each of n distinct plans as one call on cuda_stream:
+ * every member computes exactly what fengine_process_chunk computes for it
+ * (Sec. 2.1 steps 1-6), with the members spread over the pool's streams,
+ * largest work first onto the least-loaded stream, forked from and joined
+ * back into cuda_stream (so the call can be captured into a CUDA graph).
+ * first_spectra (host, n entries, may be NULL) receives each member's first
+ * spectrum. FENGINE_EINVAL for a repeated or invalid plan; a member that
+ * fails validation stops the call with its status, members enqueued before
+ * it still run and are joined. */
+fengine_status fengine_batch_process(fengine_batch_t batch, void *cuda_stream,
+                                     const fengine_chunk_desc *chunks, int32_t n,
+                                     int64_t *first_spectra);
+
+/* ---- streaming service: continuous batching of chunk requests (Sec. 3.1:
+ * host-to-device copies, computation and device-to-host copies of many
+ * chunks overlap) ---- */
+typedef struct fengine_service_s *fengine_service_t;
+
+typedef struct {
+    int32_t n_streams;          /* CUDA streams requests are spread over (1..64) */
+    int64_t hbm_budget_bytes;   /* device memory in-flight chunk buffers may hold */
+} fengine_service_config;
+
+typedef struct {
+    int64_t admitted, completed, deferred, failed, queued;
+    int64_t bytes_in_use, peak_bytes;
+    double latency_p50_us, latency_p99_us, latency_max_us;   /* submit -> output on host */
+} fengine_service_stats;
+
+/* Start the service on the current device: a dispatcher thread admits queued
+ * requests in arrival order once their input and output buffers fit in the
+ * budget next to the requests in flight; each plan keeps one CUDA stream, so
+ * a plan's chunks run in order while different plans overlap on the device.
+ * While a plan is used through a service, call its delay and gain setters
+ * only through the service (they are applied in order with its chunks). */
+fengine_status fengine_service_create(const fengine_service_config *cfg, fengine_service_t *out);
+
+/* Queue one chunk of `plan` from HOST memory: h_packed holds the plan's
+ * [antenna][pol][5L/4] bytes (pinned memory lets the copy run
+ * asynchronously), h_out receives info.out_bytes of 8-bit output. Both must
+ * stay valid until fengine_service_wait returns for the ticket. The result
+ * equals fengine_process_chunk's for the same chunk. */
+fengine_status fengine_service_submit(fengine_service_t svc, fengine_plan_t plan, const uint8_t *h_packed,
+                                      int64_t first_sample, int8_t *h_out, int64_t *ticket);
+
+/* fengine_set_delay / fengine_set_gains, applied in order with the plan's
+ * queued chunks. */
+fengine_status fengine_service_set_delay(fengine_service_t svc, fengine_plan_t plan, int32_t ant, int32_t pol,
+                                         int64_t t_apply, int64_t t_ref, double delay, double delay_rate,
+                                         double phase, double phase_rate);
+fengine_status fengine_service_set_gains(fengine_service_t svc, fengine_plan_t plan, int32_t ant, int32_t pol,
+                                         const float *gains_re_im);
+
+/* Wait up to timeout_ms (-1: no limit) for a chunk request; returns its
+ * status (FENGINE_ETIMEOUT if still running; FENGINE_EBUSY if it can never
+ * fit the budget) and its latency from submit to output in host memory. A
+ * ticket can be waited for once. */
+fengine_status fengine_service_wait(fengine_service_t svc, int64_t ticket, int32_t timeout_ms, double *latency_us);
+fengine_status fengine_service_get_stats(fengine_service_t svc, fengine_service_stats *out);
+
+/* Finish every queued request, then stop. */
+fengine_status fengine_service_destroy(fengine_service_t svc);
 
 /* Per-stage device timing, a profiling aid. While enabled, every
  * fengine_process_chunk records CUDA events on its stream between its

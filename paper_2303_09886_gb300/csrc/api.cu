@@ -66,10 +66,17 @@ struct fengine_plan_s {
     bool staged_pending = false;
     bool started = false;
     long long next_sample = 0;
-    // optional per-stage timing: 5 events per timed call
+    // slab pipeline: phase 1 of slab s+1 overlaps phase 2 of slab s on two
+    // internal streams; the intermediate of a slab stays in L2
+    int SL = 0, n_slabs = 0;
+    cudaStream_t sp[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_p1[2] = {nullptr, nullptr}, ev_p2[2] = {nullptr, nullptr};
+    // optional per-stage timing: (stage, start, end) event records
     bool profiling = false;
     std::vector<cudaEvent_t> prof_events;
     size_t prof_used = 0;
+    std::vector<int> prof_stage;
+    int prof_calls = 0;
 };
 
 namespace {
@@ -100,6 +107,12 @@ void release(fengine_plan_s *pl) {
     cudaFreeHost(pl->h_gains);
     if (pl->staged) cudaEventDestroy(pl->staged);
     for (cudaEvent_t ev : pl->prof_events) cudaEventDestroy(ev);
+    for (int i = 0; i < 2; i++) {
+        if (pl->ev_p1[i]) cudaEventDestroy(pl->ev_p1[i]);
+        if (pl->ev_p2[i]) cudaEventDestroy(pl->ev_p2[i]);
+        if (pl->sp[i]) cudaStreamDestroy(pl->sp[i]);
+    }
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
     delete pl;
 }
 
@@ -135,10 +148,19 @@ cudaEvent_t prof_event(fengine_plan_s *pl) {
     return pl->prof_events[pl->prof_used++];
 }
 
-void prof_mark(fengine_plan_s *pl, cudaEvent_t *slot, cudaStream_t st) {
+// Profiling: an event pair around one launch of `stage` on stream st.
+void prof_begin(fengine_plan_s *pl, int stage, cudaStream_t st) {
     if (!pl->profiling) return;
-    *slot = prof_event(pl);
-    if (*slot) cudaEventRecord(*slot, st);
+    cudaEvent_t ev = prof_event(pl);
+    if (!ev) return;
+    pl->prof_stage.push_back(stage);
+    cudaEventRecord(ev, st);
+}
+
+void prof_end(fengine_plan_s *pl, cudaStream_t st) {
+    if (!pl->profiling || pl->prof_used == 0 || pl->prof_used % 2 == 0) return;
+    cudaEvent_t ev = prof_event(pl);
+    if (ev) cudaEventRecord(ev, st);
 }
 
 }  // namespace
@@ -216,14 +238,26 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     pl->C = pl->N1 * pl->W;
     pl->R2 = fe::phase2_R2(pl->N2);
     long long H = N * (T - 1) + pl->D;
-    H = (H + 3) / 4 * 4;
+    H = (H + 15) / 16 * 16;     // whole 5-byte groups, and 4-byte aligned rows of packed history
     pl->H = H;
     pl->hist_bytes = H / 4 * 5;
     pl->chunk_bytes = pl->L / 4 * 5;
 
     const int ns = pl->n_streams;
     cudaError_t e = cudaSuccess;
-    const size_t a_bytes = (size_t)ns * M * (pl->N1 / 2 + 1) * pl->N2 * sizeof(float2);
+    // Slab of spectra whose FP32 intermediate (all streams) is about 40 MiB:
+    // the slab being written and the one being read fit in the 126 MiB L2
+    // next to the streaming input and output. A multiple of 32 spectra (both
+    // phases' tiles).
+    const size_t per_spec = (size_t)ns * (pl->N1 / 2 + 1) * pl->N2 * sizeof(float2);
+    long long SL = (long long)((40u << 20) / per_spec) / 32 * 32;
+    if (SL < 32) SL = 32;
+    const long long M32 = (M + 31) / 32 * 32;
+    if (SL > M32) SL = M32;
+    pl->SL = (int)SL;
+    pl->n_slabs = (int)((M + SL - 1) / SL);
+    const int nbuf = pl->n_slabs > 1 ? 2 : 1;
+    const size_t a_bytes = (size_t)nbuf * SL * per_spec;
     if ((e = dalloc(pl, &pl->d_w, sizeof(float) * N * T)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_tw1, sizeof(float2) * (pl->N1 / 2 + 1) * pl->N2)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_tw2, sizeof(float2) * pl->N2)) != cudaSuccess ||
@@ -248,6 +282,17 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         release(pl);
         g_last_error = std::string("pinned allocation: ") + cudaGetErrorString(e);
         return FENGINE_ENOMEM;
+    }
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+        if ((e = cudaStreamCreateWithFlags(&pl->sp[i], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&pl->ev_p1[i], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&pl->ev_p2[i], cudaEventDisableTiming)) != cudaSuccess)
+            break;
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        release(pl);
+        return cuda_fail(e, "stream/event creation");
     }
 
     // weights (Eq. 1's w_{t,j} = w[t + N j])
@@ -306,6 +351,8 @@ fengine_status fengine_get_info(fengine_plan_t pl, fengine_info *info) {
     info->out_bytes = (long long)pl->n_ant * pl->M * pl->n * 4;
     info->device_bytes = pl->device_bytes;
     info->scratch_bytes = pl->scratch_bytes;
+    info->slab_spectra = pl->SL;
+    info->slabs_per_chunk = pl->n_slabs;
     return FENGINE_OK;
 }
 
@@ -357,6 +404,8 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
                                      int64_t first_sample, int8_t *d_out, float *d_prequant,
                                      int32_t *d_window_tap, int64_t *first_spectrum) {
     if (!pl || !d_packed || !d_out) return fail(FENGINE_EINVAL, "null argument");
+    if (((uintptr_t)d_packed & 3) || ((uintptr_t)d_out & 3))
+        return fail(FENGINE_EINVAL, "d_packed and d_out must be 4-byte aligned");
     if (first_sample % pl->N) return fail(FENGINE_EINVAL, "first_sample must be a multiple of 2 n_channels");
     if (pl->started && first_sample != pl->next_sample)
         return fail(FENGINE_ESEQ, "expected first_sample " + std::to_string(pl->next_sample));
@@ -419,8 +468,6 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
         pl->delay_dirty = pl->gains_dirty = false;
     }
 
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    prof_mark(pl, &ev[0], st);
     fe::DelayTableParams dp{};
     dp.seg = pl->d_seg;
     dp.nseg = pl->d_nseg;
@@ -432,8 +479,9 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     dp.ctab = pl->d_ctab;
     dp.ftab = pl->d_ftab;
     dp.err = pl->d_err;
+    prof_begin(pl, 0, st);
     if ((e = fe::launch_delay_table(dp, st)) != cudaSuccess) return cuda_fail(e, "delay table launch");
-    prof_mark(pl, &ev[1], st);
+    prof_end(pl, st);
 
     fe::Phase1Params p1{};
     p1.chunk = d_packed;
@@ -452,14 +500,10 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     p1.w = pl->d_w;
     p1.tw1 = pl->d_tw1;
     p1.ctab = pl->d_ctab;
-    p1.A = pl->d_A;
     p1.window_tap = d_window_tap;
-    if ((e = fe::launch_phase1(pl->T, pl->N1, p1, pl->n_streams, st)) != cudaSuccess)
-        return cuda_fail(e, "phase-1 launch");
-    prof_mark(pl, &ev[2], st);
+    p1.a_spectra = pl->SL;
 
     fe::Phase2Params p2{};
-    p2.A = pl->d_A;
     p2.tw2 = pl->d_tw2;
     p2.gains = pl->d_gains;
     p2.ftab = pl->d_ftab;
@@ -470,14 +514,54 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     p2.R2 = pl->R2;
     p2.out = d_out;
     p2.prequant = reinterpret_cast<float2 *>(d_prequant);
-    if ((e = fe::launch_phase2(pl->N2, p2, pl->n_ant, st)) != cudaSuccess)
-        return cuda_fail(e, "phase-2 launch");
-    prof_mark(pl, &ev[3], st);
+    p2.a_spectra = pl->SL;
 
+    // Slab pipeline: slab s uses intermediate buffer s % 2; phase 1 runs on
+    // internal stream 0, phase 2 on internal stream 1, so phase 1 of slab
+    // s + 1 overlaps phase 2 of slab s. Buffer reuse waits for phase 2 of
+    // slab s - 2. Both internal streams fork from and join back into st.
+    const size_t slab_elems = (size_t)pl->n_streams * pl->SL * (pl->N1 / 2 + 1) * pl->N2;
+    if ((e = cudaEventRecord(pl->ev_fork, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(pl->sp[0], pl->ev_fork, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(pl->sp[1], pl->ev_fork, 0)) != cudaSuccess)
+        return cuda_fail(e, "slab fork");
+    for (int s = 0; s < pl->n_slabs; s++) {
+        const int b = s & 1;
+        float2 *A = pl->d_A + (size_t)b * slab_elems;
+        const int qb = s * pl->SL;
+        const int qc = (pl->M - qb) < pl->SL ? (pl->M - qb) : pl->SL;
+        if (s >= 2 && (e = cudaStreamWaitEvent(pl->sp[0], pl->ev_p2[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "slab wait");
+        p1.A = A;
+        p1.q_begin = qb;
+        p1.q_count = qc;
+        prof_begin(pl, 1, pl->sp[0]);
+        if ((e = fe::launch_phase1(pl->T, pl->N1, p1, pl->n_streams, pl->sp[0])) != cudaSuccess)
+            return cuda_fail(e, "phase-1 launch");
+        prof_end(pl, pl->sp[0]);
+        if ((e = cudaEventRecord(pl->ev_p1[b], pl->sp[0])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(pl->sp[1], pl->ev_p1[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "slab handoff");
+        p2.A = A;
+        p2.q_begin = qb;
+        p2.q_count = qc;
+        prof_begin(pl, 2, pl->sp[1]);
+        if ((e = fe::launch_phase2(pl->N2, p2, pl->n_ant, pl->sp[1])) != cudaSuccess)
+            return cuda_fail(e, "phase-2 launch");
+        prof_end(pl, pl->sp[1]);
+        if ((e = cudaEventRecord(pl->ev_p2[b], pl->sp[1])) != cudaSuccess)
+            return cuda_fail(e, "slab event");
+    }
+    // join: the last phase 2 follows every phase 1 (through the handoff events)
+    if ((e = cudaStreamWaitEvent(st, pl->ev_p2[(pl->n_slabs - 1) & 1], 0)) != cudaSuccess)
+        return cuda_fail(e, "slab join");
+
+    prof_begin(pl, 3, st);
     if ((e = fe::launch_tail_update(pl->d_hist[pl->cur], d_packed, pl->d_hist[1 - pl->cur], pl->hist_bytes,
                                     pl->chunk_bytes, pl->n_streams, st)) != cudaSuccess)
         return cuda_fail(e, "tail launch");
-    prof_mark(pl, &ev[4], st);
+    prof_end(pl, st);
+    if (pl->profiling) pl->prof_calls++;
     pl->cur = 1 - pl->cur;
     pl->started = true;
     pl->next_sample = first_sample + pl->L;
@@ -494,19 +578,20 @@ fengine_status fengine_set_profiling(fengine_plan_t pl, int32_t enable) {
 fengine_status fengine_stage_times(fengine_plan_t pl, float *ms, int32_t *calls) {
     if (!pl || !ms || !calls) return fail(FENGINE_EINVAL, "null argument");
     for (int i = 0; i < 4; i++) ms[i] = 0.0f;
-    const size_t n_calls = pl->prof_used / 5;
-    for (size_t c = 0; c < n_calls; c++) {
-        cudaEvent_t *ev = pl->prof_events.data() + 5 * c;
-        cudaError_t e = cudaEventSynchronize(ev[4]);
+    const size_t n_rec = pl->prof_used / 2;
+    for (size_t r = 0; r < n_rec; r++) {
+        cudaEvent_t a = pl->prof_events[2 * r], b = pl->prof_events[2 * r + 1];
+        cudaError_t e = cudaEventSynchronize(b);
         if (e != cudaSuccess) return cuda_fail(e, "stage timing");
-        for (int i = 0; i < 4; i++) {
-            float t = 0.0f;
-            if ((e = cudaEventElapsedTime(&t, ev[i], ev[i + 1])) != cudaSuccess) return cuda_fail(e, "stage timing");
-            ms[i] += t;
-        }
+        float t = 0.0f;
+        if ((e = cudaEventElapsedTime(&t, a, b)) != cudaSuccess) return cuda_fail(e, "stage timing");
+        const int stage = r < pl->prof_stage.size() ? pl->prof_stage[r] : 0;
+        if (stage >= 0 && stage < 4) ms[stage] += t;
     }
-    *calls = (int32_t)n_calls;
+    *calls = pl->prof_calls;
     pl->prof_used = 0;
+    pl->prof_stage.clear();
+    pl->prof_calls = 0;
     return FENGINE_OK;
 }
 

@@ -45,6 +45,59 @@ __host__ __device__ constexpr int bitrev(int i) {
     return r;
 }
 
+// exp(-2 pi i q / 64) for q in [0, 32] as compile-time constants (cos and
+// sin of multiples of pi/32, evaluated in FP64 and rounded to FP32; the
+// exact values 0, +-1 are written exactly so multiplications by them fold).
+__host__ __device__ __forceinline__ float2 tw64c(int q) {
+    constexpr float c[33] = {
+        1.0f, 9.951847196e-01f, 9.807852507e-01f, 9.569403529e-01f, 9.238795042e-01f,
+        8.819212914e-01f, 8.314695954e-01f, 7.730104327e-01f, 7.071067691e-01f, 6.343932748e-01f,
+        5.555702448e-01f, 4.713967443e-01f, 3.826834261e-01f, 2.902846634e-01f, 1.950903237e-01f,
+        9.801714122e-02f, 0.0f, -9.801714122e-02f, -1.950903237e-01f, -2.902846634e-01f,
+        -3.826834261e-01f, -4.713967443e-01f, -5.555702448e-01f, -6.343932748e-01f, -7.071067691e-01f,
+        -7.730104327e-01f, -8.314695954e-01f, -8.819212914e-01f, -9.238795042e-01f, -9.569403529e-01f,
+        -9.807852507e-01f, -9.951847196e-01f, -1.0f};
+    // sin(-2 pi q / 64) = -cos(2 pi (16 - q) / 64) = -c[|16 - q|] for q in [0, 32]
+    const int m = q <= 16 ? 16 - q : q - 16;
+    return make_float2(c[q], -c[m]);
+}
+
+// Multiply by a compile-time twiddle exp(-2 pi i q / 64), folding q = 0
+// (identity) and q = 16 (-i).
+__device__ __forceinline__ float2 cmul_tw64c(float2 a, int q) {
+    if (q == 0) return a;
+    if (q == 16) return make_float2(a.y, -a.x);
+    return cmul(a, tw64c(q));
+}
+
+// In-register NN-point complex DFT with compile-time twiddles (NN <= 64),
+// radix-2 decimation in time; natural order in and out.
+template <int NN>
+__device__ __forceinline__ void fft_regc(float2 (&z)[NN]) {
+#pragma unroll
+    for (int i = 0; i < NN; i++) {
+        const int j = bitrev<NN>(i);
+        if (i < j) {
+            float2 t = z[i];
+            z[i] = z[j];
+            z[j] = t;
+        }
+    }
+#pragma unroll
+    for (int len = 2; len <= NN; len <<= 1) {
+#pragma unroll
+        for (int i = 0; i < NN; i += len) {
+#pragma unroll
+            for (int j = 0; j < len / 2; j++) {
+                const float2 v = cmul_tw64c(z[i + j + len / 2], j * (64 / len));
+                const float2 u = z[i + j];
+                z[i + j] = cadd(u, v);
+                z[i + j + len / 2] = csub(u, v);
+            }
+        }
+    }
+}
+
 // In-register NN-point complex DFT, X[k] = sum_t z[t] exp(-2 pi i k t / NN),
 // radix-2 decimation in time; natural order in and out. tw64[q] holds
 // exp(-2 pi i q / 64) for q in [0, 32], so NN <= 64.

@@ -51,12 +51,16 @@ struct Phase1Params {
     const float *w;           // [N*T] prototype, w[t + N j]
     const float2 *tw1;        // [(N1/2+1)][N2] exp(-2 pi i k1 t2 / N)
     const int *ctab;          // [stream][M]
-    float2 *A;                // out [stream][M][N1/2+1][N2]
+    float2 *A;                // out [stream][a_spectra][N1/2+1][N2], spectrum q at row q - q_begin
     int *window_tap;          // optional out [stream][M][N]
+    int q_begin, q_count;     // the slab of spectra this launch covers
+    int a_spectra;            // spectra per stream in the intermediate buffer
 };
 
 struct Phase2Params {
-    const float2 *A;          // [stream][M][N1/2+1][N2]
+    const float2 *A;          // [stream][a_spectra][N1/2+1][N2], spectrum q at row q - q_begin
+    int q_begin, q_count;     // the slab of spectra this launch covers
+    int a_spectra;            // spectra per stream in the intermediate buffer
     const float2 *tw2;        // [N2] exp(-2 pi i q / N2)
     const float2 *gains;      // [stream][n]
     const float2 *ftab;       // [stream][M]
@@ -76,11 +80,11 @@ cudaError_t launch_phase2(int N2, const Phase2Params &p, int n_ant, cudaStream_t
 // Tile shapes (host and device agree through these).
 constexpr int kP1Rows = 32;   // spectra per phase-1 CTA
 inline int phase1_W(int N1, int N2) {
-    int w = (N1 >= 64) ? 8 : 32;
+    int w = 512 / N1;           // 512 FIR columns per tile
     return w < N2 ? w : N2;
 }
 inline int phase2_R2(int N2) {
-    int r = 8192 / N2;          // 2 pols * R2 * N2 * 8 B <= 128 KiB of shared memory
+    int r = 4096 / N2;          // 2 pols * R2 * N2 * 8 B <= 64 KiB: two CTAs per SM
     if (r > 32) r = 32;
     if (r < 1) r = 1;
     return r;

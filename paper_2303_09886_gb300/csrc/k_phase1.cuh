@@ -39,12 +39,26 @@ struct P1Shape {
     static constexpr int ROWS = R + T - 1;
 };
 
-// 4 samples of the 5-byte group starting at packed byte b (MSB first,
-// 10-bit two's complement), as exact floats.
-__device__ __forceinline__ float4 unpack_group(const uint8_t *__restrict__ p, long long b) {
-    const unsigned b0 = __ldg(p + b), b1 = __ldg(p + b + 1), b2 = __ldg(p + b + 2),
-                   b3 = __ldg(p + b + 3), b4 = __ldg(p + b + 4);
-    const unsigned hi = (b0 << 24) | (b1 << 16) | (b2 << 8) | b3;   // bits 0..31 of the group
+constexpr int kUB = 8;   // unpack groups per thread per batch
+
+// The two aligned 32-bit words covering the 5-byte group at packed byte b of
+// a 4-byte aligned buffer whose length is a multiple of 4: with wb = b & ~3,
+// the group ends at b + 5 <= length, so length - wb >= 5 and, being a
+// multiple of 4, >= 8 -- both words are inside the buffer.
+__device__ __forceinline__ void load_group(const uint8_t *__restrict__ p, long long b, unsigned &w0,
+                                           unsigned &w1, int &sh) {
+    const unsigned *w = reinterpret_cast<const unsigned *>(p + (b & ~3LL));
+    w0 = __ldg(w);
+    w1 = __ldg(w + 1);
+    sh = 8 * (int)(b & 3);
+}
+
+// 4 samples of a 5-byte group (MSB first, 10-bit two's complement) from its
+// covering words, as exact floats.
+__device__ __forceinline__ float4 decode_group(unsigned w0, unsigned w1, int sh) {
+    const unsigned lo = __funnelshift_r(w0, w1, sh);     // bytes b .. b+3, memory order
+    const unsigned b4 = (w1 >> sh) & 0xFFu;              // byte b+4
+    const unsigned hi = __byte_perm(lo, 0u, 0x0123);     // big-endian: bits 0..31 of the group
     const unsigned u0 = hi >> 22;
     const unsigned u1 = (hi >> 12) & 0x3FFu;
     const unsigned u2 = (hi >> 2) & 0x3FFu;
@@ -61,14 +75,13 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
     extern __shared__ float xs[];              // [ROWS][N1][SW]
     __shared__ int c_sm[R];
     __shared__ int off_sm[R];                  // segment misalignment of each row's run
-    __shared__ float2 tw_sm[33];               // exp(-2 pi i q / 64)
     __shared__ float2 tw1_sm[(H1 + 1) * W];    // exp(-2 pi i k1 t2 / N) for this tile's t2
 
     const int N = p.N, N2 = p.N2;
     const int stream = blockIdx.z;
     const int t2_0 = blockIdx.x * W;
-    const int q0 = blockIdx.y * R;
-    const int Rv = min(R, p.M - q0);
+    const int q0 = p.q_begin + blockIdx.y * R;
+    const int Rv = min(R, p.q_begin + p.q_count - q0);
     const uint8_t *chunk = p.chunk + (long long)stream * p.chunk_bytes;
     const uint8_t *hist = p.hist + (long long)stream * p.hist_bytes;
     const long long HL = p.H + p.L;
@@ -76,11 +89,6 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
     const long long rel_base = (long long)N * (p.m0 + q0) - (p.t_in - p.H) + t2_0;
 
     for (int i = threadIdx.x; i < Rv; i += kP1Threads) c_sm[i] = p.ctab[(long long)stream * p.M + q0 + i];
-    for (int i = threadIdx.x; i < 33; i += kP1Threads) {
-        float s, c;
-        sincospif(-(float)i / 32.0f, &s, &c);
-        tw_sm[i] = make_float2(c, s);
-    }
     for (int i = threadIdx.x; i < (H1 + 1) * W; i += kP1Threads) {
         const int k = i / W, w = i % W;
         tw1_sm[i] = __ldg(p.tw1 + (long long)k * N2 + t2_0 + w);
@@ -97,14 +105,39 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
         off = (int)(rel0 & 3);
         // 1. unpack rows [ra, rb + T - 1), whole aligned groups
         const int rows = rb + T - 1 - ra;
-        for (int e = threadIdx.x; e < rows * N1 * S::NG; e += kP1Threads) {
-            const int gi = e % S::NG;
-            const int seg = e / S::NG;
-            const int t1 = seg % N1, row = ra + seg / N1;
-            const long long g = ((rel0 + (long long)N * row + (long long)N2 * t1) & ~3LL) + 4 * gi;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (g < HL) v = g < p.H ? unpack_group(hist, (g >> 2) * 5) : unpack_group(chunk, ((g - p.H) >> 2) * 5);
-            *reinterpret_cast<float4 *>(xs + row * S::ROW + t1 * S::SW + 4 * gi) = v;
+        const int ngroups = rows * N1 * S::NG;
+        // batches of kUB groups per thread: all word loads of a batch are in
+        // flight before the first is decoded
+        for (int e0 = 0; e0 < ngroups; e0 += kUB * kP1Threads) {
+            unsigned w0[kUB], w1[kUB];
+            int sh[kUB], dst[kUB];
+#pragma unroll
+            for (int u = 0; u < kUB; u++) {
+                const int e = e0 + u * kP1Threads + threadIdx.x;
+                dst[u] = -1;
+                w0[u] = w1[u] = 0u;
+                sh[u] = 0;
+                if (e < ngroups) {
+                    const int gi = e % S::NG;
+                    const int seg = e / S::NG;
+                    const int t1 = seg % N1, row = ra + seg / N1;
+                    const long long g = ((rel0 + (long long)N * row + (long long)N2 * t1) & ~3LL) + 4 * gi;
+                    dst[u] = row * S::ROW + t1 * S::SW + 4 * gi;
+                    if (g < HL) {
+                        const uint8_t *src = g < p.H ? hist : chunk;
+                        const long long b = g < p.H ? (g >> 2) * 5 : ((g - p.H) >> 2) * 5;
+                        load_group(src, b, w0[u], w1[u], sh[u]);
+                    } else {
+                        sh[u] = -1;    // past the received samples: zeros
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUB; u++) {
+                if (dst[u] < 0) continue;
+                const float4 v = sh[u] < 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : decode_group(w0[u], w1[u], sh[u]);
+                *reinterpret_cast<float4 *>(xs + dst[u]) = v;
+            }
         }
         __syncthreads();
         if (p.window_tap) {
@@ -117,6 +150,32 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
             __syncthreads();   // the FIR below overwrites these slots in place
         }
         // 2. FIR down each column, g written over the row it starts at
+        if (ra == 0 && rb == R) {
+            // one delay for the whole tile: no predicates, two columns per
+            // thread (c and c + C/2) through packed FP32x2 FMAs
+            for (int pc = threadIdx.x; pc < S::C / 2; pc += kP1Threads) {
+                const int ca = pc, cb = pc + S::C / 2;
+                const int ta = N2 * (ca / W) + t2_0 + ca % W, tb = N2 * (cb / W) + t2_0 + cb % W;
+                float *xa = xs + (ca / W) * S::SW + off + ca % W;
+                float *xb = xs + (cb / W) * S::SW + off + cb % W;
+                float2 w2[T], win[T];
+#pragma unroll
+                for (int j = 0; j < T; j++)
+                    w2[j] = make_float2(__ldg(p.w + ta + (long long)N * j), __ldg(p.w + tb + (long long)N * j));
+#pragma unroll
+                for (int row = 0; row < R + T - 1; row++) {
+                    win[row % T] = make_float2(xa[row * S::ROW], xb[row * S::ROW]);
+                    const int r = row - (T - 1);
+                    if (r >= 0) {
+                        float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                        for (int j = 0; j < T; j++) acc = __ffma2_rn(w2[j], win[(r + j) % T], acc);
+                        xa[r * S::ROW] = acc.x;
+                        xb[r * S::ROW] = acc.y;
+                    }
+                }
+            }
+        } else
         for (int col = threadIdx.x; col < S::C; col += kP1Threads) {
             const int t1 = col / W, w = col % W;
             const int t = N2 * t1 + t2_0 + w;
@@ -148,15 +207,15 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
         float2 z[H1];
 #pragma unroll
         for (int q = 0; q < H1; q++) z[q] = make_float2(g[(2 * q) * S::SW], g[(2 * q + 1) * S::SW]);
-        fft_reg<H1>(z, tw_sm);
-        float2 *out = p.A + ((long long)stream * p.M + q0 + r) * (H1 + 1) * N2 + t2_0 + w;
+        fft_regc<H1>(z);
+        float2 *out = p.A + ((long long)stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) * N2 + t2_0 + w;
 #pragma unroll
         for (int k = 0; k <= H1; k++) {
             const float2 zk = z[k % H1], zm = z[(H1 - k) % H1];
             // even part E = (Z[k] + conj Z[H1-k]) / 2, odd part O = (Z[k] - conj Z[H1-k]) / 2i
             const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
             const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-            const float2 a = cadd(E, cmul(tw_sm[k * (64 / N1)], O));
+            const float2 a = cadd(E, k == H1 ? make_float2(-O.x, -O.y) : cmul_tw64c(O, k * (64 / N1)));
             out[(long long)k * N2] = cmul(a, tw1_sm[k * W + w]);
         }
     }
@@ -170,7 +229,7 @@ cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t 
     cudaError_t e = cudaFuncSetAttribute(k_phase1<T, N1, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(p.N2 / W, (p.M + kP1Rows - 1) / kP1Rows, n_streams);
+    dim3 grid(p.N2 / W, (p.q_count + kP1Rows - 1) / kP1Rows, n_streams);
     k_phase1<T, N1, W><<<grid, kP1Threads, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -178,10 +237,11 @@ cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t 
 template <int T>
 cudaError_t launch_phase1_n1(int N1, const Phase1Params &p, int n_streams, cudaStream_t s) {
     switch (N1 * 1000 + p.W) {
-        case 8032: return launch_phase1_tw<T, 8, 32>(p, n_streams, s);
+        case 8064: return launch_phase1_tw<T, 8, 64>(p, n_streams, s);
         case 16032: return launch_phase1_tw<T, 16, 32>(p, n_streams, s);
-        case 32032: return launch_phase1_tw<T, 32, 32>(p, n_streams, s);
+        case 32016: return launch_phase1_tw<T, 32, 16>(p, n_streams, s);
         case 64008: return launch_phase1_tw<T, 64, 8>(p, n_streams, s);
+        case 8032: return launch_phase1_tw<T, 8, 32>(p, n_streams, s);
         case 8016: return launch_phase1_tw<T, 8, 16>(p, n_streams, s);
         case 8008: return launch_phase1_tw<T, 8, 8>(p, n_streams, s);
         case 8004: return launch_phase1_tw<T, 8, 4>(p, n_streams, s);

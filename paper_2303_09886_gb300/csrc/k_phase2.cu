@@ -31,7 +31,7 @@ namespace fe {
 
 namespace {
 
-constexpr int kP2Threads = 512;
+constexpr int kP2Threads = 256;
 
 // exp(-2 pi i q / 16), q = 0..15, as compile-time constants.
 __device__ __forceinline__ float2 w16(int q) {
@@ -78,7 +78,7 @@ template <int N2>
 struct P2Shape {
     static constexpr int P = N2 < 16 ? N2 : 16;                   // points per thread per stage
     static constexpr int TPS = N2 / P;                            // threads per sequence
-    static constexpr int R2 = (8192 / N2) > 32 ? 32 : (8192 / N2); // spectra per CTA
+    static constexpr int R2 = (4096 / N2) > 32 ? 32 : (4096 / N2); // spectra per CTA (2 CTAs per SM)
     static constexpr int LD = N2 + N2 / 16 + 1;                   // padded row stride
     static constexpr int LO = N2 < 32 ? N2 : 32;                  // rotation low table size
     static constexpr int HI = N2 / LO;                            // rotation high table size
@@ -150,30 +150,51 @@ __device__ __forceinline__ int dif_pos(int k2) {
 }  // namespace
 
 template <int N2>
-__global__ void __launch_bounds__(kP2Threads) k_phase2(const Phase2Params p) {
+__global__ void __launch_bounds__(kP2Threads, 2) k_phase2(const Phase2Params p) {
     using S = P2Shape<N2>;
     constexpr int R2 = S::R2, LD = S::LD;
     extern __shared__ float2 sm[];
     float2 *buf = sm;                                  // [2 R2][LD]
     float2 *tw = buf + 2 * R2 * LD;                    // [N2] exp(-2 pi i q / N2)
-    float2 *thi = tw + N2;                             // [2 R2][HI]
-    float2 *tlo = thi + 2 * R2 * S::HI;                // [2 R2][LO]
-    float2 *qup = tlo + 2 * R2 * S::LO;                // [2 R2] upper-class factor
-    long long *rowoff = reinterpret_cast<long long *>(qup + 2 * R2);   // [R2] heap row byte offset
+    constexpr int HP = S::HI + 1, LP = S::LO + 1;      // padded table rows (no bank conflicts)
+    float2 *thi = tw + N2;                             // [2 R2][HP]
+    float2 *tlo = thi + 2 * R2 * HP;                   // [2 R2][LP]
+    float2 *qup = tlo + 2 * R2 * LP;                   // [2 R2] upper-class factor
+    float2 *gsm = qup + 2 * R2;                        // [2][N2] gain of each slot's channel
+    long long *rowoff = reinterpret_cast<long long *>(gsm + 2 * N2);   // [R2] heap row byte offset
     int *rowstride = reinterpret_cast<int *>(rowoff + R2);             // [R2] bytes per channel row
 
     const int k1 = blockIdx.x, ant = blockIdx.z;
-    const int q0 = blockIdx.y * R2;
-    const int M = p.M, Rv = min(R2, M - q0);
+    const int q0 = p.q_begin + blockIdx.y * R2;
+    const int M = p.M, Rv = min(R2, p.q_begin + p.q_count - q0);
     const int N1 = p.N1, H1 = N1 / 2, N = p.N, n = N / 2, S_ = p.S;
 
     // stage B[k1][.] rows in (sequence = pol * R2 + r), padded
-    for (int e = threadIdx.x; e < 2 * R2 * N2; e += kP2Threads) {
-        const int sq = e / N2, t2 = e % N2;
-        const int pol = sq / R2, r = sq % R2;
-        if (r < Rv)
-            buf[sq * LD + pad(t2)] =
-                p.A[(((long long)(ant * 2 + pol) * M + q0 + r) * (H1 + 1) + k1) * N2 + t2];
+    {
+        // two complex values per 16-byte load, all of a thread's loads in
+        // flight before the first store; pad() keeps even pairs adjacent
+        constexpr int PER = (R2 * N2 + kP2Threads - 1) / kP2Threads;
+        float4 v[PER];
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int e = u * kP2Threads + threadIdx.x;
+            const int sq = e / (N2 / 2), t2 = 2 * (e % (N2 / 2));
+            const int pol = sq / R2, r = sq % R2;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < R2 * N2 && r < Rv)
+                v[u] = __ldg(reinterpret_cast<const float4 *>(
+                    p.A + (((long long)(ant * 2 + pol) * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) + k1) * N2 +
+                    t2));
+        }
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int e = u * kP2Threads + threadIdx.x;
+            const int sq = e / (N2 / 2), t2 = 2 * (e % (N2 / 2));
+            if (e < R2 * N2) {
+                buf[sq * LD + pad(t2)] = make_float2(v[u].x, v[u].y);
+                buf[sq * LD + pad(t2 + 1)] = make_float2(v[u].z, v[u].w);
+            }
+        }
     }
     for (int e = threadIdx.x; e < N2; e += kP2Threads) tw[e] = __ldg(p.tw2 + e);
     // rotation tables: angle/pi = phi/pi - 2 delta k / N, k = k1 + N1 (LO a + b)
@@ -187,16 +208,24 @@ __global__ void __launch_bounds__(kP2Threads) k_phase2(const Phase2Params p) {
         if (which < S::HI) {
             const float kk = (float)(k1 + N1 * S::LO * which);
             sincospif(f.y - f.x * kk * inv, &sn, &cs);
-            thi[sq * S::HI + which] = make_float2(cs, sn);
+            thi[sq * HP + which] = make_float2(cs, sn);
         } else if (which < S::HI + S::LO) {
             const int b = which - S::HI;
             sincospif(-f.x * (float)(N1 * b) * inv, &sn, &cs);
-            tlo[sq * S::LO + b] = make_float2(cs, sn);
+            tlo[sq * LP + b] = make_float2(cs, sn);
         } else {
             // upper class: Y = G exp(2 i phi - 2 pi i delta) conj(Z)
             sincospif(2.0f * f.y - 2.0f * f.x, &sn, &cs);
             qup[sq] = make_float2(cs, sn);
         }
+    }
+    // gains of this CTA's channels: slot k2 holds channel k1 + N1 k2 (lower
+    // half) or N - (k1 + N1 k2) (upper half)
+    for (int e = threadIdx.x; e < 2 * N2; e += kP2Threads) {
+        const int pol = e / N2, k2 = e % N2;
+        const int kc = k1 + N1 * k2;
+        const int k = k2 >= N2 / 2 ? N - kc : kc;
+        gsm[e] = (k >= 0 && k < n) ? __ldg(p.gains + (long long)(ant * 2 + pol) * n + k) : make_float2(0.f, 0.f);
     }
     if ((int)threadIdx.x < Rv) {
         const int q = q0 + threadIdx.x;
@@ -214,8 +243,7 @@ __global__ void __launch_bounds__(kP2Threads) k_phase2(const Phase2Params p) {
     const bool upper = (k1 != 0 && k1 != H1);
     const int nslot = upper ? N2 : N2 / 2;
     int8_t *out_ant = p.out + (long long)ant * M * n * 4;
-    const float2 *g0 = p.gains + (long long)(ant * 2) * n;
-    const float2 *g1 = g0 + n;
+#pragma unroll 4
     for (int e = threadIdx.x; e < nslot * R2; e += kP2Threads) {
         const int r = e % R2, k2 = e / R2;
         if (r >= Rv) continue;
@@ -229,8 +257,8 @@ __global__ void __launch_bounds__(kP2Threads) k_phase2(const Phase2Params p) {
         for (int pol = 0; pol < 2; pol++) {
             const int sq = pol * R2 + r;
             const float2 F = buf[sq * LD + pos];
-            const float2 z = cmul(cmul(thi[sq * S::HI + a], tlo[sq * S::LO + b]), F);
-            const float2 g = __ldg((pol ? g1 : g0) + k);
+            const float2 z = cmul(cmul(thi[sq * HP + a], tlo[sq * LP + b]), F);
+            const float2 g = gsm[pol * N2 + k2];
             const float2 y = up ? cmul(cmul(g, qup[sq]), cconj(z)) : cmul(g, z);
             if (p.prequant) p.prequant[((long long)(ant * 2 + pol) * M + q0 + r) * n + k] = y;
             const unsigned qr = (unsigned)quant8(y.x) & 0xFFu, qi = (unsigned)quant8(y.y) & 0xFFu;
@@ -243,8 +271,8 @@ __global__ void __launch_bounds__(kP2Threads) k_phase2(const Phase2Params p) {
 size_t phase2_smem_bytes(int N2, int R2) {
     const int LD = N2 + N2 / 16 + 1;
     const int LO = N2 < 32 ? N2 : 32, HI = N2 / LO;
-    return sizeof(float2) * ((size_t)2 * R2 * LD + N2 + 2 * R2 * (HI + LO + 1)) +
-           (sizeof(long long) + sizeof(int)) * R2;
+    return sizeof(float2) * ((size_t)2 * R2 * LD + N2 + 2 * R2 * ((HI + 1) + (LO + 1) + 1)) +
+           sizeof(float2) * 2 * N2 + (sizeof(long long) + sizeof(int)) * R2;
 }
 
 template <int N2>
@@ -255,7 +283,7 @@ static cudaError_t launch_p2(const Phase2Params &p, int n_ant, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_phase2<N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(p.N1 / 2 + 1, (p.M + R2 - 1) / R2, n_ant);
+    dim3 grid(p.N1 / 2 + 1, (p.q_count + R2 - 1) / R2, n_ant);
     k_phase2<N2><<<grid, kP2Threads, smem, s>>>(p);
     return cudaGetLastError();
 }

@@ -25,7 +25,11 @@ STATUS = {0: "FENGINE_OK", 1: "FENGINE_EINVAL", 2: "FENGINE_ENOMEM", 3: "FENGINE
 EXPORTS = ("fengine_strerror", "fengine_last_error", "fengine_abi_version", "fengine_quantise",
            "fengine_default_weights", "fengine_plan_create", "fengine_plan_destroy",
            "fengine_get_info", "fengine_set_delay", "fengine_set_gains", "fengine_reset",
-           "fengine_process_chunk", "fengine_set_profiling", "fengine_stage_times")
+           "fengine_process_chunk", "fengine_set_profiling", "fengine_stage_times",
+           "fengine_batch_create", "fengine_batch_destroy", "fengine_batch_process",
+           "fengine_service_create", "fengine_service_submit", "fengine_service_set_delay",
+           "fengine_service_set_gains", "fengine_service_wait", "fengine_service_get_stats",
+           "fengine_service_destroy")
 
 
 class FEngineError(RuntimeError):
@@ -48,7 +52,13 @@ class Info(ctypes.Structure):
                 ("fft_n1", ctypes.c_int32), ("fft_n2", ctypes.c_int32),
                 ("spectra_per_chunk", ctypes.c_int64), ("history_samples", ctypes.c_int64),
                 ("latency_spectra", ctypes.c_int64), ("out_bytes", ctypes.c_int64),
-                ("device_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t),
+                ("slab_spectra", ctypes.c_int32), ("slabs_per_chunk", ctypes.c_int32)]
+
+
+class ChunkDesc(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("d_packed", ctypes.c_void_p),
+                ("first_sample", ctypes.c_int64), ("d_out", ctypes.c_void_p)]
 
 
 _lib = None
@@ -81,9 +91,15 @@ def load(path: str = LIB_PATH):
     lib.fengine_set_gains.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_float)]
     lib.fengine_reset.argtypes = [vp]
     lib.fengine_process_chunk.argtypes = [vp, vp, vp, i64, vp, vp, vp, ctypes.POINTER(i64)]
+    lib.fengine_set_profiling.argtypes = [vp, i32]
+    lib.fengine_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
+    lib.fengine_batch_create.argtypes = [i32, ctypes.POINTER(vp)]
+    lib.fengine_batch_destroy.argtypes = [vp]
+    lib.fengine_batch_process.argtypes = [vp, vp, ctypes.POINTER(ChunkDesc), i32, ctypes.POINTER(i64)]
     for name in ("fengine_default_weights", "fengine_plan_create", "fengine_plan_destroy",
                  "fengine_get_info", "fengine_set_delay", "fengine_set_gains", "fengine_reset",
-                 "fengine_process_chunk", "fengine_set_profiling", "fengine_stage_times"):
+                 "fengine_process_chunk", "fengine_set_profiling", "fengine_stage_times",
+                 "fengine_batch_create", "fengine_batch_destroy", "fengine_batch_process"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -200,3 +216,131 @@ class Plan:
                                             first_sample, _ptr(out), _ptr(prequant), _ptr(window_tap),
                                             ctypes.byref(fs)))
         return fs.value
+
+
+class Batch:
+    """Many independent plans processed in one call (fengine_batch_process)."""
+
+    def __init__(self, n_pool: int = 8):
+        h = ctypes.c_void_p()
+        _check(load().fengine_batch_create(n_pool, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().fengine_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def process(self, members, stream=None):
+        """members: list of (Plan, packed uint8 CUDA tensor, first_sample, out int8 CUDA tensor).
+        Returns the first spectrum index of every member."""
+        import torch
+        n = len(members)
+        descs = (ChunkDesc * max(n, 1))()
+        for i, (plan, packed, first, out) in enumerate(members):
+            if packed.numel() != plan.n_antennas * 2 * plan.chunk_samples * 5 // 4:
+                raise ValueError(f"member {i}: packed has the wrong size")
+            if out.numel() != plan.info.out_bytes:
+                raise ValueError(f"member {i}: out has the wrong size")
+            descs[i] = ChunkDesc(plan._h.value, _ptr(packed).value, first, _ptr(out).value)
+        fs = (ctypes.c_int64 * max(n, 1))()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(load().fengine_batch_process(self._h, ctypes.c_void_p(s.cuda_stream), descs, n, fs))
+        return [fs[i] for i in range(n)]
+
+
+class ServiceConfig(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class ServiceStats(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("deferred", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64),
+                ("peak_bytes", ctypes.c_int64), ("latency_p50_us", ctypes.c_double),
+                ("latency_p99_us", ctypes.c_double), ("latency_max_us", ctypes.c_double)]
+
+
+def _service_signatures(lib):
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.fengine_service_create.argtypes = [ctypes.POINTER(ServiceConfig), ctypes.POINTER(vp)]
+    lib.fengine_service_submit.argtypes = [vp, vp, vp, i64, vp, ctypes.POINTER(i64)]
+    lib.fengine_service_set_delay.argtypes = [vp, vp, i32, i32, i64, i64, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double]
+    lib.fengine_service_set_gains.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ctypes.c_float)]
+    lib.fengine_service_wait.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_double)]
+    lib.fengine_service_get_stats.argtypes = [vp, ctypes.POINTER(ServiceStats)]
+    lib.fengine_service_destroy.argtypes = [vp]
+    for name in ("fengine_service_create", "fengine_service_submit", "fengine_service_set_delay",
+                 "fengine_service_set_gains", "fengine_service_wait", "fengine_service_get_stats",
+                 "fengine_service_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
+
+
+class Service:
+    """Continuous-batching service over host-memory chunks (fengine_service_*).
+
+    Host buffers passed to submit() must stay alive until wait() returns for
+    the ticket; this wrapper keeps references to them."""
+
+    def __init__(self, n_streams: int = 4, hbm_budget_bytes: int = 8 << 30):
+        lib = load()
+        _service_signatures(lib)
+        h = ctypes.c_void_p()
+        _check(lib.fengine_service_create(ctypes.byref(ServiceConfig(n_streams, hbm_budget_bytes)),
+                                          ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, plan: Plan, h_packed: np.ndarray, first_sample: int, h_out: np.ndarray) -> int:
+        if not (h_packed.flags["C_CONTIGUOUS"] and h_out.flags["C_CONTIGUOUS"]):
+            raise ValueError("host buffers must be contiguous")
+        if h_packed.nbytes != plan.n_antennas * 2 * plan.chunk_samples * 5 // 4 or h_out.nbytes != plan.info.out_bytes:
+            raise ValueError("host buffer size mismatch")
+        t = ctypes.c_int64()
+        _check(load().fengine_service_submit(self._h, plan._h, h_packed.ctypes.data, first_sample,
+                                             h_out.ctypes.data, ctypes.byref(t)))
+        self._keep[t.value] = (h_packed, h_out)
+        return t.value
+
+    def set_delay(self, plan: Plan, ant: int, pol: int, delay: float, rate: float = 0.0, phase: float = 0.0,
+                  phase_rate: float = 0.0, t_apply: int = -(2 ** 62), t_ref: int = 0):
+        _check(load().fengine_service_set_delay(self._h, plan._h, ant, pol, t_apply, t_ref, delay, rate, phase,
+                                                phase_rate))
+
+    def set_gains(self, plan: Plan, ant: int, pol: int, gains):
+        g = np.ascontiguousarray(np.broadcast_to(np.asarray(gains, np.complex64), (plan.n_channels,)))
+        gi = g.view(np.float32)
+        _check(load().fengine_service_set_gains(self._h, plan._h, ant, pol,
+                                                gi.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> float:
+        """Block until the chunk is done; returns its latency in microseconds."""
+        lat = ctypes.c_double()
+        st = load().fengine_service_wait(self._h, ticket, timeout_ms, ctypes.byref(lat))
+        if st != 6:   # keep buffers alive while a timed-out request still runs
+            self._keep.pop(ticket, None)
+        _check(st)
+        return lat.value
+
+    def stats(self) -> dict:
+        s = ServiceStats()
+        _check(load().fengine_service_get_stats(self._h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in ServiceStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().fengine_service_destroy(self._h))
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
