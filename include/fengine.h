@@ -246,6 +246,52 @@ fengine_status fengine_service_get_stats(fengine_service_t svc, fengine_service_
 /* Finish every queued request, then stop. */
 fengine_status fengine_service_destroy(fengine_service_t svc);
 
+/* ---- no-allocation variant (the paper has no counterpart) ----
+ * For callers that cannot allocate device memory: a process whose device
+ * memory is handed out in full by another allocator (a framework's caching
+ * allocator, a fixed per-process budget), or a latency-critical streaming
+ * loop that cannot afford the implicit device synchronisation of
+ * cudaMalloc/cudaFree. fengine_process_chunk_noalloc runs the same kernels
+ * as fengine_process_chunk without a plan and allocates nothing: the caller
+ * passes every input and output in device memory, and the working storage
+ * (delay table, twiddle tables, the inter-phase intermediate) lives in one
+ * file-scope device array of FENGINE_NOALLOC_SCRATCH_BYTES that every GPU
+ * which loads the library holds until the process exits.
+ *  - The first call on a device looks up that array's device address (with
+ *    the device current); make that first call before any stream capture.
+ *  - Every call shares the array and overwrites it: calls whose work
+ *    overlaps on the GPU (different streams, or different host threads
+ *    without ordering) race; order them on one stream.
+ *  - A shape whose working storage exceeds the array (or more than
+ *    FENGINE_NOALLOC_MAX_STREAMS streams) is refused with FENGINE_EINVAL. */
+#define FENGINE_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define FENGINE_NOALLOC_MAX_STREAMS 64
+
+typedef struct {
+    int32_t n_antennas, n_channels, n_taps, spectra_per_heap;  /* as fengine_config */
+    int64_t chunk_samples, max_delay_samples;                   /* L and D, as fengine_config */
+    int64_t first_sample;                                       /* multiple of 2n */
+} fengine_noalloc_args;
+
+/* d_history    device [antenna][pol][5H/4] bytes: samples [first_sample - H,
+ *              first_sample) of each stream, H = 2n(T-1) + D rounded up to a
+ *              multiple of 16 (zeros before a stream starts).
+ * d_packed     device [antenna][pol][5L/4] bytes: samples [first_sample, + L).
+ * d_weights    device [2n T] prototype w[t + 2n j].
+ * d_gains      device [antenna][pol][n] complex gains as (re, im) floats.
+ * delay_models host [antenna][pol][5] doubles: delay, delay_rate, phase,
+ *              phase_rate, t_ref -- one model per stream, as fengine_set_delay.
+ * d_out        device, same layout as fengine_process_chunk's.
+ * All device buffers 4-byte aligned. The output equals fengine_process_chunk's
+ * for the same samples, weights, gains and delay models (within the
+ * rounding of the twiddle tables, which are built on the device here).
+ * Asynchronous on cuda_stream; FENGINE_EDELAY if a coarse delay of the call
+ * leaves [0, D]. */
+fengine_status fengine_process_chunk_noalloc(const fengine_noalloc_args *args, const uint8_t *d_history,
+                                             const uint8_t *d_packed, const float *d_weights,
+                                             const float *d_gains, const double *delay_models,
+                                             int8_t *d_out, void *cuda_stream);
+
 /* Per-stage device timing, a profiling aid. While enabled, every
  * fengine_process_chunk records CUDA events on its stream between its
  * kernels. fengine_stage_times waits for those events, writes the summed

@@ -29,7 +29,7 @@ EXPORTS = ("fengine_strerror", "fengine_last_error", "fengine_abi_version", "fen
            "fengine_batch_create", "fengine_batch_destroy", "fengine_batch_process",
            "fengine_service_create", "fengine_service_submit", "fengine_service_set_delay",
            "fengine_service_set_gains", "fengine_service_wait", "fengine_service_get_stats",
-           "fengine_service_destroy")
+           "fengine_service_destroy", "fengine_process_chunk_noalloc")
 
 
 class FEngineError(RuntimeError):
