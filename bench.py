@@ -201,6 +201,181 @@ def cpu_baseline(wl, budget_s: float = 15.0):
                       f"{wl.name}: unpack + FIR + FFT + delay/gain + quantise, FP64, OpenMP over spectra"}
 
 
+def _base_streams(seed: int, n: int, sigma: float = 32.0):
+    """Packed 10-bit noise for benchmark inputs whose content does not matter
+    for throughput (the parity tests cover the content)."""
+    from paper_2303_09886_gb300 import synth
+    return synth.pack10(synth.digitiser_samples(seed, n, sigma, [(0.123, 50.0, 0.0)]))
+
+
+def run_batched(args):
+    """Workload 4: many uneven independent streams in one batched call.
+
+    64 plans (1 antenna x 2 pols each) with channels drawn from {1024, 4096,
+    8192, 32768}, taps from {4, 8, 16}, chunk lengths uniform in
+    [2^20, 2^26] samples/pol truncated to a multiple of 2n, random delays and
+    gains. One step = one fengine_batch_process over one chunk of every plan."""
+    import torch
+    from paper_2303_09886_gb300 import build as fe_build
+    from paper_2303_09886_gb300 import fengine, synth
+
+    torch.cuda.set_device(0)
+    fe_build.build()
+    fengine.load()
+    g = synth.rng(synth.SEED_BASE + 4)
+    n_plans = args.plans or 64
+    base = _base_streams(synth.SEED_BASE + 4, 1 << 26)
+    d_base = torch.from_numpy(base).cuda()
+    plans, members = [], []
+    total = 0
+    for i in range(n_plans):
+        n = int(g.choice([1024, 4096, 8192, 32768]))
+        T = int(g.choice([4, 8, 16]))
+        L = int(g.integers(1 << 20, (1 << 26) + 1)) // (2 * n) * (2 * n)
+        L = max(L, 2 * n * 32)
+        p = fengine.Plan(1, n, T, L, spectra_per_heap=0, max_delay_samples=2100)
+        for pol in range(2):
+            p.set_delay(0, pol, float(g.uniform(0, 2000)), 1e-9, float(g.uniform(0, 6.28)))
+        gains = synth.random_gains(1000 + i, 2, n)
+        p.set_gains(0, 0, gains[0])
+        p.set_gains(0, 1, gains[1])
+        nbytes = 2 * L * 5 // 4
+        d_in = d_base[:nbytes].view(1, 2, -1) if nbytes <= d_base.numel() else \
+            torch.from_numpy(np.resize(base, nbytes)).cuda().view(1, 2, -1)
+        d_out = torch.empty(p.info.out_bytes, dtype=torch.int8, device="cuda")
+        plans.append(p)
+        members.append([p, d_in, 0, d_out])
+        total += 2 * L
+    batch = fengine.Batch(args.pool)
+    stream = torch.cuda.current_stream()
+    t = [0] * n_plans
+
+    def step():
+        for i, m in enumerate(members):
+            m[2] = t[i]
+            t[i] += m[0].chunk_samples
+        batch.process([tuple(m) for m in members], stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # the same plans one after another on a single stream, for comparison
+    for _ in range(2):
+        for m in members:
+            m[0].process(m[1], t[members.index(m)], m[3], stream=stream)
+            t[members.index(m)] += m[0].chunk_samples
+    torch.cuda.synchronize()
+    e0.record(stream)
+    k2 = max(1, min(args.steps, 5))
+    for _ in range(k2):
+        for i, m in enumerate(members):
+            m[0].process(m[1], t[i], m[3], stream=stream)
+            t[i] += m[0].chunk_samples
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    value = total * args.steps / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched uneven: {n_plans} independent dual-pol streams, channels in "
+                                   "{1024,4096,8192,32768}, taps in {4,8,16}, chunks U[2^20,2^26] samples/pol",
+                       "samples_per_step": total, "pool_streams": args.pool},
+            "sequential_single_stream": {"value": total * k2 / (ms_seq / 1e3) / 1e9, "unit": UNIT,
+                                         "ms_per_step": ms_seq / k2},
+            "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+    return 0
+
+
+def run_service(args):
+    """Workload 5: streaming service. 16 plans (1 antenna x 2 pols, 8192
+    channels, 16 taps), chunks of 2^24 samples/pol arriving by a Poisson
+    process at `--load` times the sustained rate measured first; delay updates
+    every 2^22 samples; HBM budget 40 GB. Reports admitted Gsample/s and
+    chunk latency p50/p99 (submit -> output in host memory)."""
+    import threading as th
+
+    import torch
+    from paper_2303_09886_gb300 import build as fe_build
+    from paper_2303_09886_gb300 import fengine, synth
+
+    torch.cuda.set_device(0)
+    fe_build.build()
+    fengine.load()
+    n_ant, n, T, L = 16, 8192, 16, 1 << 24
+    chunks = args.chunks
+    g = synth.rng(synth.SEED_BASE + 5)
+    base = _base_streams(synth.SEED_BASE + 5, 2 * L)
+    h_in = torch.from_numpy(base).pin_memory().numpy()
+    plans = [fengine.Plan(1, n, T, L, max_delay_samples=2100) for _ in range(n_ant)]
+    outs = [[torch.empty(p.info.out_bytes, dtype=torch.int8).pin_memory().numpy() for _ in range(2)]
+            for p in plans]
+    d0 = g.uniform(0, 2000, n_ant)
+    # sustained rate: the 16 plans back to back through the service, no arrival gaps
+    svc = fengine.Service(n_streams=args.pool, hbm_budget_bytes=40 << 30)
+    t0 = time.perf_counter()
+    tk = []
+    for c in range(2):
+        for a, p in enumerate(plans):
+            svc.set_delay(p, 0, 0, float(d0[a]), 1e-9)
+            svc.set_delay(p, 0, 1, float(d0[a]), 1e-9)
+            tk.append(svc.submit(p, h_in, c * L, outs[a][c % 2]))
+    for x in tk:
+        svc.wait(x)
+    sustained = 2 * n_ant * 2 * L / (time.perf_counter() - t0)
+    svc.close()
+    for p in plans:
+        p.reset()
+    # Poisson arrivals at load x sustained
+    rate = args.load * sustained / (2 * L)          # chunks per second, all antennas
+    svc = fengine.Service(n_streams=args.pool, hbm_budget_bytes=40 << 30)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, n_ant * chunks))
+    order = [(k % n_ant, k // n_ant) for k in range(n_ant * chunks)]
+    tickets = []
+    t_start = time.perf_counter()
+    for (a, c), at in zip(order, arrivals):
+        while time.perf_counter() - t_start < at:
+            time.sleep(0.0002)
+        p = plans[a]
+        for u in range(4):     # delay model refreshed every 2^22 samples
+            t_apply = c * L + u * (1 << 22) - (T - 1) * 2 * n
+            svc.set_delay(p, 0, 0, float(d0[a]) + 1e-9 * t_apply, 1e-9, t_apply=t_apply, t_ref=t_apply)
+            svc.set_delay(p, 0, 1, float(d0[a]) + 1e-9 * t_apply, 1e-9, t_apply=t_apply, t_ref=t_apply)
+        tickets.append(svc.submit(p, h_in, c * L, outs[a][c % 2]))
+    lat = [svc.wait(x) for x in tickets]
+    wall = time.perf_counter() - t_start
+    st = svc.stats()
+    svc.close()
+    line = {"metric": METRIC, "value": n_ant * chunks * 2 * L / wall / 1e9, "unit": UNIT, "n_gpus": 1,
+            "steps": n_ant * chunks, "warmup": 2 * n_ant, "ms_per_step": wall * 1e3 / (n_ant * chunks),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"streaming service: {n_ant} ant x 2 pol, 8192 ch, 16 taps, chunks 2^24 "
+                                   f"samples/pol, Poisson arrivals at {args.load}x sustained, delay updates "
+                                   f"every 2^22 samples, HBM budget 40 GB, {chunks} chunks per antenna",
+                       "pool_streams": args.pool},
+            "service": {"sustained_Gsps": sustained / 1e9, "offered_Gsps": args.load * sustained / 1e9,
+                        "latency_p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                        "latency_p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                        "admitted": st["admitted"], "deferred": st["deferred"],
+                        "peak_bytes": st["peak_bytes"]}}
+    print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,11 +387,21 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--antennas", type=int, default=0, help="override the workload's antenna count")
     ap.add_argument("--chunk-samples", type=int, default=0, help="override the chunk length")
+    ap.add_argument("--plans", type=int, default=0, help="workload 4: number of plans (default 64)")
+    ap.add_argument("--pool", type=int, default=8, help="workloads 4/5: internal CUDA streams")
+    ap.add_argument("--chunks", type=int, default=8, help="workload 5: chunks per antenna")
+    ap.add_argument("--load", type=float, default=1.5, help="workload 5: offered load / sustained rate")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="fp32 plain form, or the tensor-core forms (FP16/BF16 operands, FP32 accumulation)")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
 
+    if args.workload == 4 and args.impl == "fengine":
+        return run_batched(args)
+    if args.workload == 5 and args.impl == "fengine":
+        return run_service(args)
     from paper_2303_09886_gb300.workloads import WORKLOADS
-    wl = WORKLOADS[args.workload]
+    wl = WORKLOADS[min(args.workload, 3) if args.workload in (1, 2, 3) else 2]
     if args.antennas or args.chunk_samples:
         import dataclasses
         wl = dataclasses.replace(wl, n_antennas=args.antennas or wl.n_antennas,
@@ -239,8 +424,10 @@ def main(argv=None):
         dist.barrier()
     fengine.load()
 
+    prec = {"fp32": fengine.FP32, "fp16": fengine.TC_FP16, "bf16": fengine.TC_BF16}[args.precision]
     plan = fengine.Plan(wl.n_antennas, wl.n_channels, wl.n_taps, wl.chunk_samples,
-                        spectra_per_heap=wl.spectra_per_heap, max_delay_samples=wl.max_delay)
+                        spectra_per_heap=wl.spectra_per_heap, max_delay_samples=wl.max_delay,
+                        precision=prec)
     for a, p, d, r, ph, pr in wl.delays():
         plan.set_delay(a, p, d, r, ph, pr)
     g = wl.gains()
@@ -343,10 +530,11 @@ def main(argv=None):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": wl.description, "name": wl.name, "n_antennas": wl.n_antennas,
                    "n_channels": wl.n_channels, "n_taps": wl.n_taps, "chunk_samples": wl.chunk_samples,
-                   "precision": "fp32", "parallelism": f"replicas x{ws}",
+                   "precision": args.precision, "parallelism": f"replicas x{ws}",
                    "l2": f"inputs larger than L2: {h_in.numel() >> 20} MiB packed in + "
                          f"{plan.info.out_bytes >> 20} MiB out per step"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,

@@ -46,6 +46,7 @@ struct fengine_plan_s {
     int device = 0;
     int n_ant = 0, n_streams = 0, n = 0, N = 0, T = 0, S = 0, M = 0, N1 = 0, N2 = 0, W = 0, C = 0, R2 = 0;
     int precision = 0;
+    float dft_scale = 1.0f;
     long long L = 0, D = 0, H = 0, chunk_bytes = 0, hist_bytes = 0;
     // device state
     float *d_w = nullptr;
@@ -216,8 +217,11 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     int S = cfg->spectra_per_heap;
     if (S == 0) S = (int)(M < 256 ? M : 256);
     if (S < 1 || S > M) return fail(FENGINE_EINVAL, "spectra_per_heap must be in [1, L/2n]");
-    if (cfg->precision != FENGINE_FP32)
-        return fail(FENGINE_EUNSUPPORTED, "only FENGINE_FP32 is implemented in this build");
+    if (cfg->precision != FENGINE_FP32 && cfg->precision != FENGINE_TC_FP16 && cfg->precision != FENGINE_TC_BF16)
+        return fail(FENGINE_EINVAL, "unknown precision");
+    if (cfg->precision != FENGINE_FP32 && n != 8192)
+        return fail(FENGINE_EUNSUPPORTED,
+                    "the tensor-core forms are implemented for 8192 channels (16-point first stage) only");
 
     fengine_plan_s *pl = new (std::nothrow) fengine_plan_s();
     if (!pl) return fail(FENGINE_ENOMEM, "host allocation");
@@ -309,6 +313,19 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
             release(pl);
             return fail(FENGINE_EINVAL, "weights must be finite");
         }
+    // Scale for the reduced-precision first stage: |g| <= 512 max_t sum_j |w|
+    // and the 16-point DFT grows it by at most 16, so a power of two s with
+    // s * 16 * 512 * wmax <= 2^14 keeps every operand and result inside FP16.
+    {
+        double wmax = 0.0;
+        for (long long t = 0; t < N; t++) {
+            double a = 0.0;
+            for (int j = 0; j < T; j++) a += std::fabs((double)w[t + N * j]);
+            wmax = a > wmax ? a : wmax;
+        }
+        const double bound = 16.0 * 512.0 * (wmax > 0.0 ? wmax : 1.0);
+        pl->dft_scale = (float)std::ldexp(1.0, (int)std::floor(std::log2(16384.0 / bound)));
+    }
     // twiddles, evaluated in FP64 with exact integer phase reduction
     std::vector<float2> tw1((size_t)(pl->N1 / 2 + 1) * pl->N2), tw2(pl->N2);
     for (int k1 = 0; k1 <= pl->N1 / 2; k1++)
@@ -502,6 +519,8 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     p1.ctab = pl->d_ctab;
     p1.window_tap = d_window_tap;
     p1.a_spectra = pl->SL;
+    p1.precision = pl->precision;
+    p1.dft_scale = pl->dft_scale;
 
     fe::Phase2Params p2{};
     p2.tw2 = pl->d_tw2;

@@ -55,6 +55,8 @@ struct Phase1Params {
     int *window_tap;          // optional out [stream][M][N]
     int q_begin, q_count;     // the slab of spectra this launch covers
     int a_spectra;            // spectra per stream in the intermediate buffer
+    int precision;            // 0 FP32 CUDA cores, 1 FP16 / 2 BF16 tensor-core first stage
+    float dft_scale;          // power of two applied before the reduced-precision stage
 };
 
 struct Phase2Params {

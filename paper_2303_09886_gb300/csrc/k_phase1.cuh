@@ -22,6 +22,9 @@
 // in registers (an N1/2-point complex FFT of even/odd pairs plus the split),
 // multiplies by the twiddle and stores B to the intermediate.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "fe_device.cuh"
 #include "fe_internal.cuh"
 
@@ -68,7 +71,110 @@ __device__ __forceinline__ float4 decode_group(unsigned w0, unsigned w1, int sh)
                        (float)((int)(u2 ^ 0x200u) - 512), (float)((int)(u3 ^ 0x200u) - 512));
 }
 
-template <int T, int N1, int W>
+// ---- reduced-precision form: the 16-point real DFT over t1 on tensor cores
+//
+// For one spectrum row r and 8 consecutive t2 columns the DFT is the real
+// 16 x 16 x 8 product D x G, D[m][t] = cos(2 pi m t / 16) for m < 8,
+// D[8][t] = cos(pi t), D[8 + k][t] = -sin(2 pi k t / 16) for k = 1..7, so
+// that rows m and m + 8 of the result, held by the same lane of
+// mma.m16n8k16, are Re and Im of A[m] (m >= 1) or A[0] and A[8] (m = 0).
+// FP16: one MMA with FP16 operands and FP32 accumulation. BF16: the
+// operands are split into bf16 hi + lo parts and three MMAs
+// (hi.hi + hi.lo + lo.hi) keep the product near FP32 accuracy. Inputs are
+// scaled by the plan's power of two p.dft_scale (from the weights' bound, so
+// every D x G fits FP16) and the results by its inverse.
+
+template <int PREC>
+__device__ __forceinline__ unsigned pack2(float lo, float hi) {
+    if constexpr (PREC == 1) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const unsigned *>(&h);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const unsigned *>(&h);
+    }
+}
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+template <int PREC>
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    if constexpr (PREC == 1) {
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                     "{%8,%9}, {%0,%1,%2,%3};"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    } else {
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                     "{%8,%9}, {%0,%1,%2,%3};"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
+}
+
+// D[m][t] of the 16-point real DFT in the row layout above.
+__device__ __forceinline__ float dft16_entry(int m, int t) {
+    if (m == 8) return (t & 1) ? -1.0f : 1.0f;
+    if (m < 8) {
+        const int q = (4 * m * t) & 63;            // cos(2 pi q / 64) = Re exp(-2 pi i q / 64)
+        return q <= 32 ? tw64c(q).x : tw64c(64 - q).x;
+    }
+    const int q = (4 * (m - 8) * t) & 63;          // -sin(2 pi q / 64) = Im exp(-2 pi i q / 64)
+    return q <= 32 ? tw64c(q).y : -tw64c(64 - q).y;
+}
+
+template <int PREC, int ROW, int SW, int W>
+__device__ __forceinline__ void dft16_tensor(const Phase1Params &p, const float *xs, const int *off_sm,
+                                             const float2 *tw1_sm, int Rv, int stream, int q0, int t2_0) {
+    constexpr int H1 = 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, c = lane & 3;
+    // A fragments (rows g, g+8; columns 2c, 2c+1, 2c+8, 2c+9)
+    unsigned ahi[4], alo[4];
+    {
+        const int rows[4] = {g, g + 8, g, g + 8}, cols[4] = {2 * c, 2 * c, 2 * c + 8, 2 * c + 8};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const float v0 = dft16_entry(rows[i], cols[i]), v1 = dft16_entry(rows[i], cols[i] + 1);
+            ahi[i] = pack2<PREC>(v0, v1);
+            if constexpr (PREC == 2) alo[i] = pack2<PREC>(v0 - bf16_round(v0), v1 - bf16_round(v1));
+        }
+    }
+    const float sc = p.dft_scale, usc = 1.0f / p.dft_scale;
+    const int N2 = p.N2;
+    constexpr int NT = W / 8;                      // n-tiles per spectrum row
+    for (int tile = warp; tile < Rv * NT; tile += kP1Threads / 32) {
+        const int r = tile / NT, w0 = (tile % NT) * 8;
+        const float *x = xs + r * ROW + off_sm[r] + w0 + g;   // column n = g of the tile
+        const float x0 = x[(2 * c) * SW] * sc, x1 = x[(2 * c + 1) * SW] * sc;
+        const float x8 = x[(2 * c + 8) * SW] * sc, x9 = x[(2 * c + 9) * SW] * sc;
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        const unsigned b0 = pack2<PREC>(x0, x1), b1 = pack2<PREC>(x8, x9);
+        mma16816<PREC>(d, ahi, b0, b1);
+        if constexpr (PREC == 2) {
+            const unsigned l0 = pack2<PREC>(x0 - bf16_round(x0), x1 - bf16_round(x1));
+            const unsigned l1 = pack2<PREC>(x8 - bf16_round(x8), x9 - bf16_round(x9));
+            mma16816<PREC>(d, ahi, l0, l1);
+            mma16816<PREC>(d, alo, b0, b1);
+        }
+        // lane holds columns 2c, 2c+1 of rows g (Re) and g + 8 (Im, or A[8] for g = 0)
+        const int w = w0 + 2 * c, t2 = t2_0 + w;
+        float2 *out = p.A + ((long long)stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) * N2 + t2;
+        if (g == 0) {
+            const float4 a0 = make_float4(d[0] * usc, 0.f, d[1] * usc, 0.f);
+            *reinterpret_cast<float4 *>(out) = a0;
+            const float2 e0 = cmul(make_float2(d[2] * usc, 0.f), tw1_sm[8 * W + w]);
+            const float2 e1 = cmul(make_float2(d[3] * usc, 0.f), tw1_sm[8 * W + w + 1]);
+            *reinterpret_cast<float4 *>(out + (long long)8 * N2) = make_float4(e0.x, e0.y, e1.x, e1.y);
+        } else {
+            const float2 e0 = cmul(make_float2(d[0] * usc, d[2] * usc), tw1_sm[g * W + w]);
+            const float2 e1 = cmul(make_float2(d[1] * usc, d[3] * usc), tw1_sm[g * W + w + 1]);
+            *reinterpret_cast<float4 *>(out + (long long)g * N2) = make_float4(e0.x, e0.y, e1.x, e1.y);
+        }
+    }
+}
+
+template <int T, int N1, int W, int PREC = 0>
 __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) {
     using S = P1Shape<T, N1, W>;
     constexpr int R = S::R, H1 = N1 / 2;
@@ -201,6 +307,9 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
     }
 
     // 3. real N1-point DFT over t1, twiddle, store B[k1][t2]
+    if constexpr (PREC != 0) {
+        dft16_tensor<PREC, S::ROW, S::SW, W>(p, xs, off_sm, tw1_sm, Rv, stream, q0, t2_0);
+    } else
     for (int pi = threadIdx.x; pi < Rv * W; pi += kP1Threads) {
         const int r = pi / W, w = pi % W;
         const float *g = xs + r * S::ROW + off_sm[r] + w;
@@ -221,21 +330,27 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
     }
 }
 
-template <int T, int N1, int W>
+template <int T, int N1, int W, int PREC = 0>
 cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t s) {
     using S = P1Shape<T, N1, W>;
     if (p.W != W || p.N2 % W) return cudaErrorInvalidValue;
     const size_t smem = (size_t)S::ROWS * S::ROW * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_phase1<T, N1, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_phase1<T, N1, W, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(p.N2 / W, (p.q_count + kP1Rows - 1) / kP1Rows, n_streams);
-    k_phase1<T, N1, W><<<grid, kP1Threads, smem, s>>>(p);
+    k_phase1<T, N1, W, PREC><<<grid, kP1Threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <int T>
 cudaError_t launch_phase1_n1(int N1, const Phase1Params &p, int n_streams, cudaStream_t s) {
+    if (p.precision != 0) {
+        // reduced-precision form: tensor-core 16-point first stage (N1 = 16)
+        if (N1 != 16 || p.W != 32) return cudaErrorInvalidValue;
+        return p.precision == 1 ? launch_phase1_tw<T, 16, 32, 1>(p, n_streams, s)
+                                : launch_phase1_tw<T, 16, 32, 2>(p, n_streams, s);
+    }
     switch (N1 * 1000 + p.W) {
         case 8064: return launch_phase1_tw<T, 8, 64>(p, n_streams, s);
         case 16032: return launch_phase1_tw<T, 16, 32>(p, n_streams, s);

@@ -115,6 +115,7 @@ void dispatcher(fengine_service_s *s) {
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
         // retire completed requests: give their memory and stream slot back
+        bool retired = false;
         for (auto &kv : s->all) {
             Request &r = *kv.second;
             if (r.done && r.stream >= 0 && r.kind == 0 && (r.d_in || r.d_out)) {
@@ -126,8 +127,10 @@ void dispatcher(fengine_service_s *s) {
                 s->completed++;
                 s->latencies_us.push_back(
                     std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count());
+                retired = true;
             }
         }
+        if (retired) s->done_cv.notify_all();   // waiters need the buffers released too
         if (s->stop && s->queue.empty()) break;
         // admit in arrival order; a request that cannot go blocks later
         // requests of its own plan only (per-plan order), not other plans

@@ -17,6 +17,7 @@ from oracle import oracle as O
 from paper_2303_09886_gb300 import fengine, synth
 
 REL_RMS_FP32 = 1e-5
+REL_RMS_REDUCED = 2e-3     # FP16 / BF16 tensor-core forms
 
 
 @dataclasses.dataclass
@@ -39,13 +40,14 @@ def streams(seed, n_ant, total, sigma, tones=(), chirp=None):
 
 
 def run_gpu(samples, n_ch, T, L, n_chunks, delays, gains, S=0, D=0, weights=None, start=0,
-            taps=True, prequant=True, chunk_sizes=None):
+            taps=True, prequant=True, precision=fengine.FP32):
     """Process consecutive chunks of `samples` (starting at absolute `start`).
     delays[a][p]: list of Seg; gains[a][p]: complex array or None.
     Returns list of dicts per call (numpy copies of every output)."""
     import torch
     n_ant = samples.shape[0]
-    plan = fengine.Plan(n_ant, n_ch, T, L, spectra_per_heap=S, max_delay_samples=D, weights=weights)
+    plan = fengine.Plan(n_ant, n_ch, T, L, spectra_per_heap=S, max_delay_samples=D, weights=weights,
+                        precision=precision)
     for a in range(n_ant):
         for p in range(2):
             for sg in delays[a][p]:

@@ -112,6 +112,32 @@ def test_identity_weights_give_the_plain_dft_of_the_window():
     _report("identity weights", compare_call(s, c, M, S, n, T, delays, None, weights=w))
 
 
+@pytest.mark.parametrize("precision", [fengine.TC_FP16, fengine.TC_BF16])
+def test_reduced_precision_forms(precision):
+    """Tensor-core first DFT stage (FP16 / BF16 operands, FP32 accumulation):
+    pre-quantisation relative RMS <= 2e-3 against the FP64 oracle, 8-bit
+    output within 1 LSB; 8192 channels, 16 taps, random delays and gains."""
+    from tests.fe_harness import REL_RMS_REDUCED
+    n, T, L = 8192, 16, 16384 * 40
+    g = np.random.default_rng(15)
+    tones = [(f, a, 0.3) for f, a in zip(g.uniform(0.01, 0.49, 3), g.uniform(20, 100, 3))]
+    s = streams(synth.SEED_BASE + 12, 2, 2 * L, 40.0, tones=tones)
+    delays = [[[Seg(delay=float(g.uniform(0, 2000)), rate=1e-9, phase=float(g.uniform(0, 6.28)))]
+               for _ in range(2)] for _ in range(2)]
+    gains = synth.random_gains(98, 4, n).reshape(2, 2, n)
+    gains = [[gains[a, p] for p in range(2)] for a in range(2)]
+    res, M, S = run_gpu(s, n, T, L, 2, delays, gains, S=16, D=2100, precision=precision)
+    for c in res:
+        st = compare_call(s, c, M, S, n, T, delays, gains, rel_rms=REL_RMS_REDUCED)
+        _report(f"tensor-core precision {precision}", st)
+
+
+def test_reduced_precision_rejects_unsupported_shapes():
+    with pytest.raises(fengine.FEngineError) as e:
+        fengine.Plan(1, 1024, 16, 2048 * 8, precision=fengine.TC_FP16)
+    assert e.value.status == 7
+
+
 def test_chunking_invariance():
     """The same stream split into chunks of 1, 2 or 4 x 32 spectra gives
     bit-identical 8-bit output and pre-quantisation spectra."""
