@@ -113,14 +113,14 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], 
 }
 
 // D[m][t] of the 16-point real DFT in the row layout above.
+// (Evaluated once per thread with sincospif on the exactly reduced phase
+// (m t mod 16) / 8; the values are rounded to FP16/BF16 afterwards.)
 __device__ __forceinline__ float dft16_entry(int m, int t) {
     if (m == 8) return (t & 1) ? -1.0f : 1.0f;
-    if (m < 8) {
-        const int q = (4 * m * t) & 63;            // cos(2 pi q / 64) = Re exp(-2 pi i q / 64)
-        return q <= 32 ? tw64c(q).x : tw64c(64 - q).x;
-    }
-    const int q = (4 * (m - 8) * t) & 63;          // -sin(2 pi q / 64) = Im exp(-2 pi i q / 64)
-    return q <= 32 ? tw64c(q).y : -tw64c(64 - q).y;
+    const int k = m < 8 ? m : m - 8;
+    float s, c;
+    sincospif((float)((k * t) & 15) / 8.0f, &s, &c);
+    return m < 8 ? c : -s;
 }
 
 template <int PREC, int ROW, int SW, int W>
@@ -157,19 +157,19 @@ __device__ __forceinline__ void dft16_tensor(const Phase1Params &p, const float 
             mma16816<PREC>(d, ahi, l0, l1);
             mma16816<PREC>(d, alo, b0, b1);
         }
-        // lane holds columns 2c, 2c+1 of rows g (Re) and g + 8 (Im, or A[8] for g = 0)
+        // lane holds columns 2c, 2c+1 of rows g (Re A[g]) and g + 8 (Im A[g], or
+        // A[8] for g = 0, whose own Im is zero); every lane stores A[g], the
+        // g = 0 lanes store A[8] as well
         const int w = w0 + 2 * c, t2 = t2_0 + w;
         float2 *out = p.A + ((long long)stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) * N2 + t2;
+        const float i0 = g ? d[2] : 0.f, i1 = g ? d[3] : 0.f;
+        const float2 e0 = cmul(make_float2(d[0] * usc, i0 * usc), tw1_sm[g * W + w]);
+        const float2 e1 = cmul(make_float2(d[1] * usc, i1 * usc), tw1_sm[g * W + w + 1]);
+        *reinterpret_cast<float4 *>(out + (long long)g * N2) = make_float4(e0.x, e0.y, e1.x, e1.y);
         if (g == 0) {
-            const float4 a0 = make_float4(d[0] * usc, 0.f, d[1] * usc, 0.f);
-            *reinterpret_cast<float4 *>(out) = a0;
-            const float2 e0 = cmul(make_float2(d[2] * usc, 0.f), tw1_sm[8 * W + w]);
-            const float2 e1 = cmul(make_float2(d[3] * usc, 0.f), tw1_sm[8 * W + w + 1]);
-            *reinterpret_cast<float4 *>(out + (long long)8 * N2) = make_float4(e0.x, e0.y, e1.x, e1.y);
-        } else {
-            const float2 e0 = cmul(make_float2(d[0] * usc, d[2] * usc), tw1_sm[g * W + w]);
-            const float2 e1 = cmul(make_float2(d[1] * usc, d[3] * usc), tw1_sm[g * W + w + 1]);
-            *reinterpret_cast<float4 *>(out + (long long)g * N2) = make_float4(e0.x, e0.y, e1.x, e1.y);
+            const float2 f0 = cmul(make_float2(d[2] * usc, 0.f), tw1_sm[8 * W + w]);
+            const float2 f1 = cmul(make_float2(d[3] * usc, 0.f), tw1_sm[8 * W + w + 1]);
+            *reinterpret_cast<float4 *>(out + (long long)8 * N2) = make_float4(f0.x, f0.y, f1.x, f1.y);
         }
     }
 }
