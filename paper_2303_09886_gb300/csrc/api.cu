@@ -212,6 +212,9 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         return fail(FENGINE_EINVAL, "chunk_samples must be a positive multiple of 2 n_channels");
     const long long M = cfg->chunk_samples / N;
     if (M > (1LL << 30)) return fail(FENGINE_EINVAL, "chunk too long");
+    // the kernels index a stream's history + chunk with 32-bit sample offsets
+    if (cfg->chunk_samples + 2LL * n * T + cfg->max_delay_samples + 16 >= (1LL << 31))
+        return fail(FENGINE_EINVAL, "history + chunk must stay below 2^31 samples per stream");
     if (cfg->max_delay_samples < 0 || cfg->max_delay_samples > (1LL << 30))
         return fail(FENGINE_EINVAL, "max_delay_samples out of range");
     int S = cfg->spectra_per_heap;

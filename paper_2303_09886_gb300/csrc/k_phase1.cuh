@@ -44,31 +44,28 @@ struct P1Shape {
 
 constexpr int kUB = 8;   // unpack groups per thread per batch
 
-// The two aligned 32-bit words covering the 5-byte group at packed byte b of
-// a 4-byte aligned buffer whose length is a multiple of 4: with wb = b & ~3,
-// the group ends at b + 5 <= length, so length - wb >= 5 and, being a
+// A 5-byte group at packed byte b of a 4-byte aligned buffer whose length is
+// a multiple of 4 is read with the two aligned 32-bit words at b & ~3: the
+// group ends at b + 5 <= length, so length - (b & ~3) >= 5 and, being a
 // multiple of 4, >= 8 -- both words are inside the buffer.
-__device__ __forceinline__ void load_group(const uint8_t *__restrict__ p, long long b, unsigned &w0,
-                                           unsigned &w1, int &sh) {
-    const unsigned *w = reinterpret_cast<const unsigned *>(p + (b & ~3LL));
-    w0 = __ldg(w);
-    w1 = __ldg(w + 1);
-    sh = 8 * (int)(b & 3);
+
+// Exact float of the 10-bit two's-complement field in the low bits of x:
+// (field ^ 512) is the offset-binary value in [0, 1024), placed in the
+// mantissa of 2^23 and the bias 2^23 + 512 subtracted (both steps exact).
+__device__ __forceinline__ float field10_to_float(unsigned x) {
+    return __uint_as_float(((x & 0x3FFu) ^ 0x200u) | 0x4B000000u) - 8389120.0f;
 }
 
-// 4 samples of a 5-byte group (MSB first, 10-bit two's complement) from its
-// covering words, as exact floats.
-__device__ __forceinline__ float4 decode_group(unsigned w0, unsigned w1, int sh) {
-    const unsigned lo = __funnelshift_r(w0, w1, sh);     // bytes b .. b+3, memory order
-    const unsigned b4 = (w1 >> sh) & 0xFFu;              // byte b+4
-    const unsigned hi = __byte_perm(lo, 0u, 0x0123);     // big-endian: bits 0..31 of the group
-    const unsigned u0 = hi >> 22;
-    const unsigned u1 = (hi >> 12) & 0x3FFu;
-    const unsigned u2 = (hi >> 2) & 0x3FFu;
-    const unsigned u3 = ((hi & 0x3u) << 8) | b4;
-    // two's complement 10-bit: v = (u ^ 512) - 512
-    return make_float4((float)((int)(u0 ^ 0x200u) - 512), (float)((int)(u1 ^ 0x200u) - 512),
-                       (float)((int)(u2 ^ 0x200u) - 512), (float)((int)(u3 ^ 0x200u) - 512));
+// 4 samples of the 5-byte group whose first byte is byte j of w0 (the group
+// continues into w1): byte permutes build the group's bits 0-31 and 8-39 in
+// big-endian order, and the four 10-bit fields are shifted out of them.
+// All-zero words decode to four zero samples (a zero field is the value 0),
+// which is what a group past the received samples must read as.
+__device__ __forceinline__ float4 decode_group_perm(unsigned w0, unsigned w1, unsigned j) {
+    const unsigned hi = __byte_perm(w0, w1, 0x0123u + j * 0x1111u);   // group bits 0..31
+    const unsigned lo = __byte_perm(w0, w1, 0x1234u + j * 0x1111u);   // group bits 8..39
+    return make_float4(field10_to_float(hi >> 22), field10_to_float(lo >> 20), field10_to_float(lo >> 10),
+                       field10_to_float(lo));
 }
 
 // ---- reduced-precision form: the 16-point real DFT over t1 on tensor cores
@@ -214,35 +211,38 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
         const int ngroups = rows * N1 * S::NG;
         // batches of kUB groups per thread: all word loads of a batch are in
         // flight before the first is decoded
+        // sample indices relative to the first history sample fit 32 bits (the
+        // plan keeps H + L < 2^31)
+        const unsigned rel0u = (unsigned)rel0, Hu = (unsigned)p.H, HLu = (unsigned)HL;
         for (int e0 = 0; e0 < ngroups; e0 += kUB * kP1Threads) {
-            unsigned w0[kUB], w1[kUB];
-            int sh[kUB], dst[kUB];
+            unsigned w0[kUB], w1[kUB], j[kUB];
+            int dst[kUB];
 #pragma unroll
             for (int u = 0; u < kUB; u++) {
                 const int e = e0 + u * kP1Threads + threadIdx.x;
                 dst[u] = -1;
                 w0[u] = w1[u] = 0u;
-                sh[u] = 0;
+                j[u] = 0u;
                 if (e < ngroups) {
                     const int gi = e % S::NG;
                     const int seg = e / S::NG;
                     const int t1 = seg % N1, row = ra + seg / N1;
-                    const long long g = ((rel0 + (long long)N * row + (long long)N2 * t1) & ~3LL) + 4 * gi;
+                    const unsigned g = ((rel0u + (unsigned)(N * row + N2 * t1)) & ~3u) + 4u * gi;
                     dst[u] = row * S::ROW + t1 * S::SW + 4 * gi;
-                    if (g < HL) {
-                        const uint8_t *src = g < p.H ? hist : chunk;
-                        const long long b = g < p.H ? (g >> 2) * 5 : ((g - p.H) >> 2) * 5;
-                        load_group(src, b, w0[u], w1[u], sh[u]);
-                    } else {
-                        sh[u] = -1;    // past the received samples: zeros
+                    if (g < HLu) {   // else past the received samples: zeros
+                        const bool h = g < Hu;
+                        const unsigned b = ((h ? g : g - Hu) >> 2) * 5u;
+                        const unsigned *wp = reinterpret_cast<const unsigned *>((h ? hist : chunk) + (b & ~3u));
+                        w0[u] = __ldg(wp);
+                        w1[u] = __ldg(wp + 1);
+                        j[u] = b & 3u;
                     }
                 }
             }
 #pragma unroll
             for (int u = 0; u < kUB; u++) {
                 if (dst[u] < 0) continue;
-                const float4 v = sh[u] < 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : decode_group(w0[u], w1[u], sh[u]);
-                *reinterpret_cast<float4 *>(xs + dst[u]) = v;
+                *reinterpret_cast<float4 *>(xs + dst[u]) = decode_group_perm(w0[u], w1[u], j[u]);
             }
         }
         __syncthreads();

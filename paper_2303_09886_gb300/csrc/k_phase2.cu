@@ -104,16 +104,21 @@ __device__ __forceinline__ void dif_stage(float2 *buf, int nseq, const float2 *t
                 const int bf = tl + u * S::TPS;   // butterfly index in [0, per_seq)
                 const int blk = bf / sub, j = bf - blk * sub;
                 const int base = blk * Lspan + j;
+                // pad(base + r sub) = pad(base) + padc(r sub): (base & 15) + (r sub & 15)
+                // never carries into bit 4 (j < sub when sub < 16; r sub & 15 = 0
+                // otherwise; base & 15 <= 12 with r < 4 when Lspan < 16)
+                float2 *xb = x + pad(base);
                 float2 v[R];
 #pragma unroll
-                for (int r = 0; r < R; r++) v[r] = x[pad(base + r * sub)];
+                for (int r = 0; r < R; r++) v[r] = xb[(r * sub) + ((r * sub) >> 4)];
                 dft_reg<R>(v);
                 if constexpr (Lspan != R) {
+                    const int js = j * tws;
 #pragma unroll
-                    for (int k = 1; k < R; k++) v[k] = cmul(v[k], tw[j * k * tws]);
+                    for (int k = 1; k < R; k++) v[k] = cmul(v[k], tw[k * js]);
                 }
 #pragma unroll
-                for (int r = 0; r < R; r++) x[pad(base + r * sub)] = v[r];
+                for (int r = 0; r < R; r++) xb[(r * sub) + ((r * sub) >> 4)] = v[r];
             }
         }
     }
@@ -242,29 +247,38 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_phase2(const Phase2Params p) 
     // epilogue: rotate, gain, quantise, corner turn
     const bool upper = (k1 != 0 && k1 != H1);
     const int nslot = upper ? N2 : N2 / 2;
-    int8_t *out_ant = p.out + (long long)ant * M * n * 4;
+    // each thread keeps one spectrum r (kP2Threads is a multiple of R2) and
+    // walks the slots k2; lanes with consecutive r write consecutive 4-byte
+    // cells of one channel row
+    const int r = threadIdx.x % R2;
+    if (r >= Rv) return;
+    int8_t *out_r = p.out + (long long)ant * M * n * 4 + rowoff[r];
+    const int rs = rowstride[r];
+    const float2 *F0 = buf + r * LD, *F1 = buf + (R2 + r) * LD;
+    const float2 *th0 = thi + r * HP, *th1 = thi + (R2 + r) * HP;
+    const float2 *tl0 = tlo + r * LP, *tl1 = tlo + (R2 + r) * LP;
+    const float2 qu0 = qup[r], qu1 = qup[R2 + r];
+    float2 *pre0 = p.prequant ? p.prequant + ((long long)(ant * 2) * M + q0 + r) * n : nullptr;
+    float2 *pre1 = p.prequant ? p.prequant + ((long long)(ant * 2 + 1) * M + q0 + r) * n : nullptr;
 #pragma unroll 4
-    for (int e = threadIdx.x; e < nslot * R2; e += kP2Threads) {
-        const int r = e % R2, k2 = e / R2;
-        if (r >= Rv) continue;
+    for (int k2 = threadIdx.x / R2; k2 < nslot; k2 += kP2Threads / R2) {
         const bool up = k2 >= N2 / 2;
         const int kc = k1 + N1 * k2;                    // this slot's DFT index
         const int k = up ? N - kc : kc;                 // channel written
         const int a = k2 / S::LO, b = k2 % S::LO;
         const int pos = pad(dif_pos<N2>(k2));
-        unsigned packed = 0;
-#pragma unroll
-        for (int pol = 0; pol < 2; pol++) {
-            const int sq = pol * R2 + r;
-            const float2 F = buf[sq * LD + pos];
-            const float2 z = cmul(cmul(thi[sq * HP + a], tlo[sq * LP + b]), F);
-            const float2 g = gsm[pol * N2 + k2];
-            const float2 y = up ? cmul(cmul(g, qup[sq]), cconj(z)) : cmul(g, z);
-            if (p.prequant) p.prequant[((long long)(ant * 2 + pol) * M + q0 + r) * n + k] = y;
-            const unsigned qr = (unsigned)quant8(y.x) & 0xFFu, qi = (unsigned)quant8(y.y) & 0xFFu;
-            packed |= (qr | (qi << 8)) << (16 * pol);
+        const float2 z0 = cmul(cmul(th0[a], tl0[b]), F0[pos]);
+        const float2 z1 = cmul(cmul(th1[a], tl1[b]), F1[pos]);
+        const float2 g0 = gsm[k2], g1 = gsm[N2 + k2];
+        const float2 y0 = up ? cmul(cmul(g0, qu0), cconj(z0)) : cmul(g0, z0);
+        const float2 y1 = up ? cmul(cmul(g1, qu1), cconj(z1)) : cmul(g1, z1);
+        if (pre0) {
+            pre0[k] = y0;
+            pre1[k] = y1;
         }
-        *reinterpret_cast<unsigned *>(out_ant + rowoff[r] + (long long)k * rowstride[r]) = packed;
+        const unsigned packed = ((unsigned)quant8(y0.x) & 0xFFu) | (((unsigned)quant8(y0.y) & 0xFFu) << 8) |
+                                (((unsigned)quant8(y1.x) & 0xFFu) << 16) | ((unsigned)quant8(y1.y) << 24);
+        *reinterpret_cast<unsigned *>(out_r + (long long)k * rs) = packed;
     }
 }
 

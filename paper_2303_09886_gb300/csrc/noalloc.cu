@@ -107,6 +107,7 @@ fengine_status fengine_process_chunk_noalloc(const fengine_noalloc_args *a, cons
     const long long M = a->chunk_samples / N;
     const int S = a->spectra_per_heap == 0 ? (int)(M < 256 ? M : 256) : a->spectra_per_heap;
     if (S < 1 || S > M || M > (1LL << 30)) return FENGINE_EINVAL;
+    if (a->chunk_samples + N * T + a->max_delay_samples + 16 >= (1LL << 31)) return FENGINE_EINVAL;
     if (((uintptr_t)d_history & 3) || ((uintptr_t)d_packed & 3) || ((uintptr_t)d_out & 3)) return FENGINE_EINVAL;
     for (int s = 0; s < ns; s++) {
         // the one delay model of each stream must keep c in [0, D] over the call

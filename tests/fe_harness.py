@@ -135,5 +135,14 @@ def compare_call(samples, call, M, S, n_ch, T, delays, gains, weights=None, star
         assert d.max() <= 1, f"int8 output differs by {d.max()} LSB (antenna {a})"
         exact += int(np.sum(d == 0))
         total += d.size
+        # the requantiser itself: the 8-bit output is exactly R7 (round half
+        # away from zero, saturate to +-127) of the GPU's own FP32 spectra
+        if call["pre"] is not None:
+            pre = call["pre"][a].astype(np.complex128)          # [pol][m][k]
+            comp = np.stack([pre.real, pre.imag], axis=-1)      # [pol][m][k][2]
+            r = np.where(comp >= 0, np.floor(comp + 0.5), -np.floor(-comp + 0.5))
+            qq = np.clip(r, -127, 127).astype(np.int8)
+            np.testing.assert_array_equal(got, O.corner_turn(qq[0], qq[1], S),
+                                          err_msg=f"requantiser (antenna {a})")
     stats["exact_fraction"] = exact / total
     return stats
