@@ -51,6 +51,8 @@ struct fengine_plan_s {
     // device state
     float *d_w = nullptr;
     float2 *d_tw1 = nullptr, *d_tw2 = nullptr, *d_gains = nullptr, *d_ftab = nullptr, *d_A = nullptr;
+    uint4 *d_tc = nullptr;        // tensor-core second-stage tables (reduced-precision forms)
+    float tc_unscale = 1.0f;
     uint8_t *d_hist[2] = {nullptr, nullptr};
     int cur = 0;
     DelaySeg *d_seg = nullptr;
@@ -94,6 +96,7 @@ void release(fengine_plan_s *pl) {
     cudaFree(pl->d_w);
     cudaFree(pl->d_tw1);
     cudaFree(pl->d_tw2);
+    cudaFree(pl->d_tc);
     cudaFree(pl->d_gains);
     cudaFree(pl->d_ftab);
     cudaFree(pl->d_A);
@@ -329,10 +332,30 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         const double bound = 16.0 * 512.0 * (wmax > 0.0 ? wmax : 1.0);
         pl->dft_scale = (float)std::ldexp(1.0, (int)std::floor(std::log2(16384.0 / bound)));
     }
+    // The reduced-precision second stage reads B[k1][t2] scaled by
+    // s1 = 2 dft_scale (|s1 B| <= 16 * 512 * wmax * s1 <= 2^15, inside FP16),
+    // folded into the first-stage twiddle; its own twiddle carries 2^-5 and
+    // the rotation 32 / s1 undoes both.
+    const float s1 = 2.0f * pl->dft_scale;
+    std::vector<uint4> tc;
+    if (pl->precision != FENGINE_FP32) {
+        pl->tc_unscale = 32.0f / s1;
+        tc.resize(fe::kPhase2TcTableLen);
+        fe::build_phase2_tc_tables(pl->precision, tc.data());
+        if ((e = dalloc(pl, &pl->d_tc, sizeof(uint4) * tc.size())) != cudaSuccess ||
+            (e = cudaMemcpy(pl->d_tc, tc.data(), sizeof(uint4) * tc.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            release(pl);
+            return cuda_fail(e, "tensor-core tables");
+        }
+    }
     // twiddles, evaluated in FP64 with exact integer phase reduction
     std::vector<float2> tw1((size_t)(pl->N1 / 2 + 1) * pl->N2), tw2(pl->N2);
     for (int k1 = 0; k1 <= pl->N1 / 2; k1++)
-        for (int t2 = 0; t2 < pl->N2; t2++) tw1[(size_t)k1 * pl->N2 + t2] = unit_root((long long)k1 * t2, N);
+        for (int t2 = 0; t2 < pl->N2; t2++) {
+            float2 v = unit_root((long long)k1 * t2, N);
+            if (pl->precision != FENGINE_FP32) v = make_float2(v.x * s1, v.y * s1);   // exact: power of two
+            tw1[(size_t)k1 * pl->N2 + t2] = v;
+        }
     for (int q = 0; q < pl->N2; q++) tw2[q] = unit_root(q, pl->N2);
     pl->segs.assign(ns, std::vector<DelaySeg>{DelaySeg{-(1LL << 62), 0, 0.0, 0.0, 0.0, 0.0}});
     pl->gains.assign((size_t)ns * n, make_float2(1.0f, 0.0f));
@@ -537,6 +560,9 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     p2.out = d_out;
     p2.prequant = reinterpret_cast<float2 *>(d_prequant);
     p2.a_spectra = pl->SL;
+    p2.precision = pl->precision;
+    p2.tc = pl->d_tc;
+    p2.tc_unscale = pl->tc_unscale;
 
     // Slab pipeline: slab s uses intermediate buffer s % 2; phase 1 runs on
     // internal stream 0, phase 2 on internal stream 1, so phase 1 of slab
@@ -568,7 +594,8 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
         p2.q_begin = qb;
         p2.q_count = qc;
         prof_begin(pl, 2, pl->sp[1]);
-        if ((e = fe::launch_phase2(pl->N2, p2, pl->n_ant, pl->sp[1])) != cudaSuccess)
+        if ((e = pl->precision != FENGINE_FP32 ? fe::launch_phase2_tc(p2, pl->n_ant, pl->sp[1])
+                                               : fe::launch_phase2(pl->N2, p2, pl->n_ant, pl->sp[1])) != cudaSuccess)
             return cuda_fail(e, "phase-2 launch");
         prof_end(pl, pl->sp[1]);
         if ((e = cudaEventRecord(pl->ev_p2[b], pl->sp[1])) != cudaSuccess)

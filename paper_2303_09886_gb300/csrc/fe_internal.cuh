@@ -69,6 +69,9 @@ struct Phase2Params {
     int N, N1, M, S, R2;      // FFT length, first-stage size, spectra/call, spectra/heap, spectra/CTA
     int8_t *out;              // [ant][heap][n][S_h][pol][2]
     float2 *prequant;         // optional [stream][M][n]
+    int precision;            // 0 FP32 CUDA cores, 1 FP16 / 2 BF16 tensor-core second stage
+    const uint4 *tc;          // tensor-core tables (build_phase2_tc_tables), precision != 0
+    float tc_unscale;         // inverse of the scale the reduced-precision path carries
 };
 
 // Launchers (return cudaGetLastError() of the launch).
@@ -92,5 +95,14 @@ inline int phase2_R2(int N2) {
     return r;
 }
 size_t phase2_smem_bytes(int N2, int R2);
+
+// Reduced-precision second stage (N2 = 1024 only): two 32-point DFT
+// contractions on tensor cores. The tables hold the DFT matrices as per-lane
+// mma fragments and the 32 x 32 twiddle (times 2^-5); kPhase2TcTableLen
+// uint4 entries, built on the host for precision 1 (FP16) or 2 (BF16).
+constexpr int kPhase2TcTableLen = 2560;
+void build_phase2_tc_tables(int precision, uint4 *out);
+size_t phase2_tc_smem_bytes(int precision);
+cudaError_t launch_phase2_tc(const Phase2Params &p, int n_ant, cudaStream_t s);
 
 }  // namespace fe

@@ -22,10 +22,8 @@
 // in registers (an N1/2-point complex FFT of even/odd pairs plus the split),
 // multiplies by the twiddle and stores B to the intermediate.
 #pragma once
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
 #include "fe_device.cuh"
+#include "fe_mma.cuh"
 #include "fe_internal.cuh"
 
 namespace fe {
@@ -80,34 +78,6 @@ __device__ __forceinline__ float4 decode_group_perm(unsigned w0, unsigned w1, un
 // (hi.hi + hi.lo + lo.hi) keep the product near FP32 accuracy. Inputs are
 // scaled by the plan's power of two p.dft_scale (from the weights' bound, so
 // every D x G fits FP16) and the results by its inverse.
-
-template <int PREC>
-__device__ __forceinline__ unsigned pack2(float lo, float hi) {
-    if constexpr (PREC == 1) {
-        const __half2 h = __floats2half2_rn(lo, hi);
-        return *reinterpret_cast<const unsigned *>(&h);
-    } else {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-        return *reinterpret_cast<const unsigned *>(&h);
-    }
-}
-
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-template <int PREC>
-__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    if constexpr (PREC == 1) {
-        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-                     "{%8,%9}, {%0,%1,%2,%3};"
-                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    } else {
-        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-                     "{%8,%9}, {%0,%1,%2,%3};"
-                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    }
-}
 
 // D[m][t] of the 16-point real DFT in the row layout above.
 // (Evaluated once per thread with sincospif on the exactly reduced phase
@@ -264,20 +234,27 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
                 const int ta = N2 * (ca / W) + t2_0 + ca % W, tb = N2 * (cb / W) + t2_0 + cb % W;
                 float *xa = xs + (ca / W) * S::SW + off + ca % W;
                 float *xb = xs + (cb / W) * S::SW + off + cb % W;
-                float2 w2[T], win[T];
+                // outputs in pairs (r, r + 1), two independent FMA chains, from a
+                // ring of T + 1 window rows
+                float2 w2[T], win[T + 1];
 #pragma unroll
                 for (int j = 0; j < T; j++)
                     w2[j] = make_float2(__ldg(p.w + ta + (long long)N * j), __ldg(p.w + tb + (long long)N * j));
 #pragma unroll
                 for (int row = 0; row < R + T - 1; row++) {
-                    win[row % T] = make_float2(xa[row * S::ROW], xb[row * S::ROW]);
-                    const int r = row - (T - 1);
-                    if (r >= 0) {
-                        float2 acc = make_float2(0.0f, 0.0f);
+                    win[row % (T + 1)] = make_float2(xa[row * S::ROW], xb[row * S::ROW]);
+                    const int r = row - T;      // pair (r, r + 1) is complete once row r + T is in
+                    if (r >= 0 && (r & 1) == 0) {
+                        float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
 #pragma unroll
-                        for (int j = 0; j < T; j++) acc = __ffma2_rn(w2[j], win[(r + j) % T], acc);
-                        xa[r * S::ROW] = acc.x;
-                        xb[r * S::ROW] = acc.y;
+                        for (int j = 0; j < T; j++) {
+                            acc0 = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc0);
+                            acc1 = __ffma2_rn(w2[j], win[(r + 1 + j) % (T + 1)], acc1);
+                        }
+                        xa[r * S::ROW] = acc0.x;
+                        xb[r * S::ROW] = acc0.y;
+                        xa[(r + 1) * S::ROW] = acc1.x;
+                        xb[(r + 1) * S::ROW] = acc1.y;
                     }
                 }
             }

@@ -1,0 +1,398 @@
+// Phase 2, reduced-precision form (N2 = 1024): the second stage of the
+// four-step DFT as two 32-point DFT contractions on tensor cores
+// (mma.sync m16n8k16, FP16 or BF16 operands, FP32 accumulation), then the
+// fine-delay rotation, gain, requantisation and corner turn of the FP32
+// form (Sec. 2.1 steps 4-6, Sec. 2.2, Sec. 3.6).
+//
+// With t2 = 32 a + b and k2 = c + 32 d (a, b, c, d in [0, 32)):
+//   Y[c][b]     = sum_a exp(-2 pi i c a / 32) B[32 a + b]        (contraction 1)
+//   Y'[c][b]    = exp(-2 pi i c b / 1024) Y[c][b]                (twiddle)
+//   F[c + 32 d] = sum_b Y'[c][b] exp(-2 pi i d b / 32)           (contraction 2)
+// Each contraction is a real 64 x 64 product over (index, re/im) pairs.
+// Contraction 1 has the DFT matrix as operand A (rows: c, re/im) and the
+// data as operand B (columns: b); contraction 2 has the data as operand A
+// (rows: c) and the DFT matrix as operand B (columns: d, re/im). Inside a
+// 16-wide K tile, positions 2q + e and 2q + 8 + e (q < 4, e = re/im) hold
+// index 8 kt + 2q and 8 kt + 2q + 1. With that order the accumulator of
+// contraction 1 -- lane (g, q) holds Y[8 mt + g][8 nt + 2q + {0, 1}] -- is,
+// after the twiddle and rounding, exactly lane (g, q)'s operand A of
+// contraction 2: the data never leaves the registers between the two.
+//
+// One CTA owns one class k1 and 8 consecutive spectra of both polarisations
+// of one antenna; warp w computes spectrum w, one polarisation after the
+// other. The DFT matrices (as per-lane fragments) and the twiddles come from
+// plan tables; scale factors keep every FP16 operand below 2^15: the plan
+// scales the first-stage twiddle by s1 (from the weights' bound), the
+// twiddle table carries 2^-5 (contraction 1 grows values by at most 32),
+// and the rotation tables carry the inverse of both.
+//
+// BF16 form: every operand x is split into hi = bf16(x) and lo =
+// bf16(x - hi), and each product is hi.hi + hi.lo + lo.hi.
+#include <cmath>
+#include <cstring>
+
+#include "fe_device.cuh"
+#include "fe_internal.cuh"
+#include "fe_mma.cuh"
+
+namespace fe {
+
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcR = 8;          // spectra per CTA, one warp each
+constexpr int kTcN2 = 1024;
+constexpr int kGainLd = kTcN2 + kTcN2 / 8;   // padded gain row (conflict-free 8-byte loads)
+constexpr int kPQ = 96;                      // per sequence: P[32], Pup[32], Q[32]
+
+// padded gain slot: lanes (g, q) of one load touch k2 = base + g + 32 q
+__device__ __forceinline__ int gain_slot(int k2) { return k2 + 4 * (k2 >> 5); }
+
+// 32-bit word of output cell (slot k2, spectrum r) in the staging buffer:
+// the 8 cells of a slot are permuted by an XOR of k2's bits 2, 5 and 6 so
+// that the lanes (g, q) of one store (k2 = base + g + 32 q) hit 32 banks.
+__device__ __forceinline__ int stage_word(int k2, int r) {
+    return k2 * kTcR + (r ^ (((k2 >> 2) & 1) | ((k2 >> 4) & 6)));
+}
+
+__device__ __forceinline__ unsigned short q8pair(float2 y) {
+    return (unsigned short)(((unsigned)quant8(y.x) & 0xFFu) | (((unsigned)quant8(y.y) & 0xFFu) << 8));
+}
+
+}  // namespace
+
+// shared memory: tables (hi; lo for BF16) + P/Q + gains + staging + row info
+size_t phase2_tc_smem_bytes(int precision) {
+    const int nl = precision == 2 ? 2 : 1;
+    return sizeof(uint4) * 512 * (1 + 2 * nl) + sizeof(float2) * 2 * kTcR * kPQ + sizeof(float2) * 2 * kGainLd +
+           sizeof(unsigned) * kTcN2 * kTcR + (sizeof(long long) + sizeof(int)) * kTcR;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(const Phase2Params p) {
+    constexpr bool LO = PREC == 2;
+    extern __shared__ uint4 smu[];
+    // plan table order: a1 [4 mt][4 kt][32], b2 [4 kt2][4 ntp][32], tw [4 mt][4 nt][32], a1 lo, b2 lo
+    const uint4 *a1s = smu, *b2s = smu + 512;
+    const float4 *tws = reinterpret_cast<const float4 *>(smu + 1024);
+    const uint4 *a1l = smu + 1536, *b2l = smu + 2048;
+    float2 *pq = reinterpret_cast<float2 *>(smu + (LO ? 2560 : 1536));   // [2 kTcR][kPQ]
+    float2 *gsm = pq + 2 * kTcR * kPQ;                                   // [2][kGainLd]
+    unsigned *stg = reinterpret_cast<unsigned *>(gsm + 2 * kGainLd);     // [kTcN2][kTcR]
+    long long *rowoff = reinterpret_cast<long long *>(stg + kTcN2 * kTcR);
+    int *rowstride = reinterpret_cast<int *>(rowoff + kTcR);
+
+    const int k1 = blockIdx.x, ant = blockIdx.z;
+    const int q0 = p.q_begin + blockIdx.y * kTcR;
+    const int M = p.M, Rv = min(kTcR, p.q_begin + p.q_count - q0);
+    const int N1 = p.N1, H1 = N1 / 2, N = p.N, n = N / 2, S_ = p.S;
+    const bool upper = (k1 != 0 && k1 != H1);
+    const int nslot = upper ? kTcN2 : kTcN2 / 2;
+
+    for (int i = threadIdx.x; i < (LO ? 2560 : 1536); i += kTcThreads) smu[i] = __ldg(p.tc + i);
+    // rotation factors of each (pol, spectrum) sequence, angles over pi:
+    //   P[c]   = u exp(i pi (phi/pi - 2 delta (k1 + N1 c) / N))    (lower half)
+    //   Pup[c] = u exp(i pi (phi/pi - 2 delta + 2 delta (k1 + N1 c) / N))
+    //   Q[d]   = exp(-i pi 2 delta 32 N1 d / N)
+    // so that channel k1 + N1 k2 (k2 = c + 32 d) takes P[c] Q[d] F and the
+    // upper-half channel N - (k1 + N1 k2) takes Pup[c] conj(Q[d] F).
+    const float inv = 2.0f / (float)N, u = p.tc_unscale;
+    for (int e = threadIdx.x; e < 2 * kTcR * kPQ; e += kTcThreads) {
+        const int sq = e / kPQ, j = e % kPQ;
+        const int pol = sq / kTcR, r = sq % kTcR;
+        if (r >= Rv) continue;
+        const float2 f = p.ftab[(long long)(ant * 2 + pol) * M + q0 + r];   // (delta, phi / pi)
+        const int c = j & 31;
+        float ang, sc = u;
+        if (j < 32) {
+            ang = f.y - f.x * (float)(k1 + N1 * c) * inv;
+        } else if (j < 64) {
+            ang = f.y - 2.0f * f.x + f.x * (float)(k1 + N1 * c) * inv;
+        } else {
+            ang = -f.x * (float)(32 * N1 * c) * inv;
+            sc = 1.0f;
+        }
+        float sn, cs;
+        sincospif(ang, &sn, &cs);
+        pq[e] = make_float2(sc * cs, sc * sn);
+    }
+    // gains of this CTA's slots (slot k2 is channel k1 + N1 k2 in the lower
+    // half, N - (k1 + N1 k2) in the upper)
+    for (int e = threadIdx.x; e < 2 * kTcN2; e += kTcThreads) {
+        const int pol = e / kTcN2, k2 = e % kTcN2;
+        const int kc = k1 + N1 * k2;
+        const int k = k2 >= kTcN2 / 2 ? N - kc : kc;
+        gsm[pol * kGainLd + gain_slot(k2)] =
+            (k >= 0 && k < n) ? __ldg(p.gains + (long long)(ant * 2 + pol) * n + k) : make_float2(0.f, 0.f);
+    }
+    if ((int)threadIdx.x < Rv) {
+        const int q = q0 + threadIdx.x;
+        const int h = q / S_, s = q - h * S_;
+        const int Sh = min(S_, M - h * S_);
+        rowoff[threadIdx.x] = (long long)h * S_ * n * 4 + s * 4;
+        rowstride[threadIdx.x] = Sh * 4;
+    }
+    __syncthreads();
+
+    const int r = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    unsigned short *stg16 = reinterpret_cast<unsigned short *>(stg);
+    if (r < Rv) {
+        for (int pol = 0; pol < 2; pol++) {
+            const int stream = ant * 2 + pol;
+            const float2 *src =
+                p.A + ((long long)(stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) + k1) * kTcN2;
+            // contraction 1, one K tile at a time; operand B of tile kt is
+            // B[32 a + b] at a = 8 kt + 2 tq + h, b = 8 nt + g (the next
+            // tile's loads are in flight during this tile's products)
+            float d1[4][4][4];
+#pragma unroll
+            for (int mt = 0; mt < 4; mt++)
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                    for (int x = 0; x < 4; x++) d1[mt][nt][x] = 0.0f;
+            float2 v[4][2];
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                for (int h = 0; h < 2; h++) v[nt][h] = __ldg(src + 32 * (2 * tq + h) + 8 * nt + g);
+#pragma unroll
+            for (int kt = 0; kt < 4; kt++) {
+                unsigned bh[4][2], bl[4][2];
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const float2 x = v[nt][h];
+                        bh[nt][h] = pack2<PREC>(x.x, x.y);
+                        if constexpr (LO) bl[nt][h] = pack2<PREC>(x.x - bf16_round(x.x), x.y - bf16_round(x.y));
+                    }
+                if (kt < 3) {
+#pragma unroll
+                    for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                        for (int h = 0; h < 2; h++)
+                            v[nt][h] = __ldg(src + 32 * (8 * (kt + 1) + 2 * tq + h) + 8 * nt + g);
+                }
+#pragma unroll
+                for (int mt = 0; mt < 4; mt++) {
+                    const uint4 A = a1s[(mt * 4 + kt) * 32 + lane];
+#pragma unroll
+                    for (int nt = 0; nt < 4; nt++) mma16816<PREC>(d1[mt][nt], A, bh[nt][0], bh[nt][1]);
+                    if constexpr (LO) {
+                        const uint4 Al = a1l[(mt * 4 + kt) * 32 + lane];
+#pragma unroll
+                        for (int nt = 0; nt < 4; nt++) {
+                            mma16816<PREC>(d1[mt][nt], A, bl[nt][0], bl[nt][1]);
+                            mma16816<PREC>(d1[mt][nt], Al, bh[nt][0], bh[nt][1]);
+                        }
+                    }
+                }
+            }
+            // twiddle; lane (g, tq) then holds operand A of contraction 2 for
+            // m tile mp (rows c = 16 mp + g, + 8) and K tile kt2 (b = 8 kt2 + 2 tq, + 1):
+            // a0 = Y'[c][b], a1 = Y'[c + 8][b], a2 = Y'[c][b + 1], a3 = Y'[c + 8][b + 1]
+            unsigned ah[2][4][4], al[2][4][4];
+#pragma unroll
+            for (int mt = 0; mt < 4; mt++) {
+                const int mp = mt >> 1, i = mt & 1;
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++) {
+                    const float4 t = tws[(mt * 4 + nt) * 32 + lane];
+                    const float2 y0 = cmul(make_float2(d1[mt][nt][0], d1[mt][nt][2]), make_float2(t.x, t.y));
+                    const float2 y1 = cmul(make_float2(d1[mt][nt][1], d1[mt][nt][3]), make_float2(t.z, t.w));
+                    ah[mp][nt][i] = pack2<PREC>(y0.x, y0.y);
+                    ah[mp][nt][2 + i] = pack2<PREC>(y1.x, y1.y);
+                    if constexpr (LO) {
+                        al[mp][nt][i] = pack2<PREC>(y0.x - bf16_round(y0.x), y0.y - bf16_round(y0.y));
+                        al[mp][nt][2 + i] = pack2<PREC>(y1.x - bf16_round(y1.x), y1.y - bf16_round(y1.y));
+                    }
+                }
+            }
+            const float2 *pqs = pq + (pol * kTcR + r) * kPQ;
+            float2 *pre = p.prequant ? p.prequant + ((long long)stream * M + q0 + r) * n : nullptr;
+            const float2 *gp = gsm + pol * kGainLd;
+            // contraction 2 and the epilogue, per m tile and per half of the
+            // output columns (d < 16: lower-half channels, d >= 16: upper)
+#pragma unroll
+            for (int mp = 0; mp < 2; mp++) {
+#pragma unroll
+                for (int half = 0; half < 2; half++) {
+                    if (half == 1 && !upper) break;
+                    float d2[4][4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+#pragma unroll
+                        for (int x = 0; x < 4; x++) d2[j][x] = 0.0f;
+#pragma unroll
+                    for (int kt2 = 0; kt2 < 4; kt2++) {
+#pragma unroll
+                        for (int jp = 0; jp < 2; jp++) {
+                            const int ntp = 2 * half + jp;
+                            const uint4 B = b2s[(kt2 * 4 + ntp) * 32 + lane];
+                            mma16816<PREC>(d2[2 * jp], ah[mp][kt2], B.x, B.y);
+                            mma16816<PREC>(d2[2 * jp + 1], ah[mp][kt2], B.z, B.w);
+                            if constexpr (LO) {
+                                const uint4 Bl = b2l[(kt2 * 4 + ntp) * 32 + lane];
+                                mma16816<PREC>(d2[2 * jp], ah[mp][kt2], Bl.x, Bl.y);
+                                mma16816<PREC>(d2[2 * jp + 1], ah[mp][kt2], Bl.z, Bl.w);
+                                mma16816<PREC>(d2[2 * jp], al[mp][kt2], B.x, B.y);
+                                mma16816<PREC>(d2[2 * jp + 1], al[mp][kt2], B.z, B.w);
+                            }
+                        }
+                    }
+                    // rotation, gain, requantisation into the staging cells
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const int nt2 = 4 * half + j;
+                        const float2 Qd = pqs[64 + 4 * nt2 + tq];
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            const int c = 16 * mp + 8 * h + g;
+                            const int k2 = c + 32 * (4 * nt2 + tq);
+                            const float2 F = make_float2(d2[j][2 * h], d2[j][2 * h + 1]);
+                            float2 y;
+                            int k;
+                            if (half == 0) {
+                                y = cmul(gp[gain_slot(k2)], cmul(cmul(pqs[c], Qd), F));
+                                k = k1 + N1 * k2;
+                            } else {
+                                y = cmul(gp[gain_slot(k2)], cmul(cmul(pqs[32 + c], cconj(Qd)), cconj(F)));
+                                k = N - (k1 + N1 * k2);
+                            }
+                            if (pre) pre[k] = y;
+                            stg16[2 * stage_word(k2, r) + pol] = q8pair(y);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // corner turn: cell (slot k2, spectrum r) -> heap row of channel k
+    int8_t *out = p.out + (long long)ant * M * n * 4;
+    for (int e = threadIdx.x; e < nslot * kTcR; e += kTcThreads) {
+        const int k2 = e / kTcR, rr = e % kTcR;
+        if (rr >= Rv) continue;
+        const int kc = k1 + N1 * k2;
+        const int k = k2 >= kTcN2 / 2 ? N - kc : kc;
+        *reinterpret_cast<unsigned *>(out + rowoff[rr] + (long long)k * rowstride[rr]) = stg[stage_word(k2, rr)];
+    }
+}
+
+// ---- host: the plan tables
+
+namespace {
+
+// Contraction 1's operand A: row m = 16 mt + 8 o + i is output c = 8 mt + i
+// (o = 0 real, 1 imaginary part); K position 16 kt + p is input
+// a = 8 kt + 2 ((p & 7) >> 1) + (p >> 3), part p & 1. The block of the real
+// form of exp(-2 pi i c a / 32) = C - i S is [[C, S], [-S, C]].
+double dft_block(int idx_prod, int out_im, int in_im) {
+    const double th = 2.0 * M_PI * (double)(idx_prod % 32) / 32.0;
+    const double C = std::cos(th), S = std::sin(th);
+    if (!out_im) return in_im ? S : C;
+    return in_im ? C : -S;
+}
+
+int k_index(int k) { return 8 * (k / 16) + 2 * ((k % 16 & 7) >> 1) + ((k % 16) >> 3); }
+
+double a1_value(int m, int k) {
+    const int c = 8 * (m / 16) + (m % 16 & 7);
+    return dft_block(c * k_index(k), (m % 16) >> 3, k & 1);
+}
+
+// Contraction 2's operand B: K position as above (input b), column
+// n = 8 nt + l is output d = 4 nt + (l >> 1), part l & 1.
+double b2_value(int k, int n) {
+    const int d = 4 * (n / 8) + ((n % 8) >> 1);
+    return dft_block(d * k_index(k), n & 1, k & 1);
+}
+
+// Two matrix entries as one 32-bit operand register (first entry in the low
+// half); part 0 is the rounded value, part 1 the BF16 remainder.
+unsigned pack_pair(double v0, double v1, int precision, int part) {
+    unsigned short h[2];
+    const double v[2] = {v0, v1};
+    for (int i = 0; i < 2; i++) {
+        if (precision == 1) {
+            const __half x = __float2half_rn((float)v[i]);
+            std::memcpy(&h[i], &x, 2);
+        } else {
+            __nv_bfloat16 x = __float2bfloat16_rn((float)v[i]);
+            if (part) x = __float2bfloat16_rn((float)(v[i] - (double)__bfloat162float(x)));
+            std::memcpy(&h[i], &x, 2);
+        }
+    }
+    return (unsigned)h[0] | ((unsigned)h[1] << 16);
+}
+
+}  // namespace
+
+void build_phase2_tc_tables(int precision, uint4 *out) {
+    std::memset(out, 0, sizeof(uint4) * kPhase2TcTableLen);
+    for (int part = 0; part < (precision == 2 ? 2 : 1); part++) {
+        uint4 *a1 = out + (part ? 1536 : 0), *b2 = out + (part ? 2048 : 512);
+        for (int lane = 0; lane < 32; lane++) {
+            const int g = lane >> 2, q = lane & 3;
+            for (int mt = 0; mt < 4; mt++)
+                for (int kt = 0; kt < 4; kt++) {
+                    const int r0 = 16 * mt + g, c0 = 16 * kt + 2 * q;
+                    uint4 f;
+                    f.x = pack_pair(a1_value(r0, c0), a1_value(r0, c0 + 1), precision, part);
+                    f.y = pack_pair(a1_value(r0 + 8, c0), a1_value(r0 + 8, c0 + 1), precision, part);
+                    f.z = pack_pair(a1_value(r0, c0 + 8), a1_value(r0, c0 + 9), precision, part);
+                    f.w = pack_pair(a1_value(r0 + 8, c0 + 8), a1_value(r0 + 8, c0 + 9), precision, part);
+                    a1[(mt * 4 + kt) * 32 + lane] = f;
+                }
+            for (int kt = 0; kt < 4; kt++)
+                for (int ntp = 0; ntp < 4; ntp++) {
+                    const int k0 = 16 * kt + 2 * q;
+                    unsigned v[4];
+                    for (int j = 0; j < 2; j++) {
+                        const int col = 8 * (2 * ntp + j) + g;
+                        v[2 * j] = pack_pair(b2_value(k0, col), b2_value(k0 + 1, col), precision, part);
+                        v[2 * j + 1] = pack_pair(b2_value(k0 + 8, col), b2_value(k0 + 9, col), precision, part);
+                    }
+                    b2[(kt * 4 + ntp) * 32 + lane] = make_uint4(v[0], v[1], v[2], v[3]);
+                }
+        }
+    }
+    // twiddle exp(-2 pi i c b / 1024) 2^-5 at c = 8 mt + g, b = 8 nt + 2 q + e
+    for (int lane = 0; lane < 32; lane++) {
+        const int g = lane >> 2, q = lane & 3;
+        for (int mt = 0; mt < 4; mt++)
+            for (int nt = 0; nt < 4; nt++) {
+                float t[4];
+                for (int e = 0; e < 2; e++) {
+                    const int c = 8 * mt + g, b = 8 * nt + 2 * q + e;
+                    const double th = 2.0 * M_PI * (double)((c * b) % kTcN2) / (double)kTcN2;
+                    t[2 * e] = (float)(std::cos(th) / 32.0);
+                    t[2 * e + 1] = (float)(-std::sin(th) / 32.0);
+                }
+                std::memcpy(&out[1024 + (mt * 4 + nt) * 32 + lane], t, sizeof(t));
+            }
+    }
+}
+
+cudaError_t launch_phase2_tc(const Phase2Params &p, int n_ant, cudaStream_t s) {
+    if (p.N / p.N1 != kTcN2 || !p.tc || (p.precision != 1 && p.precision != 2)) return cudaErrorInvalidValue;
+    const size_t smem = phase2_tc_smem_bytes(p.precision);
+    dim3 grid(p.N1 / 2 + 1, (p.q_count + kTcR - 1) / kTcR, n_ant);
+    cudaError_t e;
+    if (p.precision == 1) {
+        if ((e = cudaFuncSetAttribute(k_phase2_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        k_phase2_tc<1><<<grid, kTcThreads, smem, s>>>(p);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_phase2_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        k_phase2_tc<2><<<grid, kTcThreads, smem, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fe

@@ -112,13 +112,16 @@ def test_identity_weights_give_the_plain_dft_of_the_window():
     _report("identity weights", compare_call(s, c, M, S, n, T, delays, None, weights=w))
 
 
-@pytest.mark.parametrize("precision", [fengine.TC_FP16, fengine.TC_BF16])
-def test_reduced_precision_forms(precision):
-    """Tensor-core first DFT stage (FP16 / BF16 operands, FP32 accumulation):
+@pytest.mark.parametrize("precision,spectra,heap", [(fengine.TC_FP16, 40, 16), (fengine.TC_BF16, 40, 16),
+                                                    (fengine.TC_FP16, 37, 12), (fengine.TC_BF16, 37, 12)])
+def test_reduced_precision_forms(precision, spectra, heap):
+    """Tensor-core DFT stages (FP16 / BF16 operands, FP32 accumulation):
     pre-quantisation relative RMS <= 2e-3 against the FP64 oracle, 8-bit
-    output within 1 LSB; 8192 channels, 16 taps, random delays and gains."""
+    output within 1 LSB; 8192 channels, 16 taps, random delays and gains.
+    37 spectra per call leave a ragged last tile of the second stage, and
+    heaps of 12 spectra split its 8-spectrum tiles across heap rows."""
     from tests.fe_harness import REL_RMS_REDUCED
-    n, T, L = 8192, 16, 16384 * 40
+    n, T, L = 8192, 16, 16384 * spectra
     g = np.random.default_rng(15)
     tones = [(f, a, 0.3) for f, a in zip(g.uniform(0.01, 0.49, 3), g.uniform(20, 100, 3))]
     s = streams(synth.SEED_BASE + 12, 2, 2 * L, 40.0, tones=tones)
@@ -126,7 +129,7 @@ def test_reduced_precision_forms(precision):
                for _ in range(2)] for _ in range(2)]
     gains = synth.random_gains(98, 4, n).reshape(2, 2, n)
     gains = [[gains[a, p] for p in range(2)] for a in range(2)]
-    res, M, S = run_gpu(s, n, T, L, 2, delays, gains, S=16, D=2100, precision=precision)
+    res, M, S = run_gpu(s, n, T, L, 2, delays, gains, S=heap, D=2100, precision=precision)
     for c in res:
         st = compare_call(s, c, M, S, n, T, delays, gains, rel_rms=REL_RMS_REDUCED)
         _report(f"tensor-core precision {precision}", st)
