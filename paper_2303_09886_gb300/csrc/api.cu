@@ -46,7 +46,6 @@ struct fengine_plan_s {
     int device = 0;
     int n_ant = 0, n_streams = 0, n = 0, N = 0, T = 0, S = 0, M = 0, N1 = 0, N2 = 0, W = 0, C = 0, R2 = 0;
     int precision = 0;
-    float dft_scale = 1.0f;
     long long L = 0, D = 0, H = 0, chunk_bytes = 0, hist_bytes = 0;
     // device state
     float *d_w = nullptr;
@@ -227,7 +226,7 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         return fail(FENGINE_EINVAL, "unknown precision");
     if (cfg->precision != FENGINE_FP32 && n != 8192)
         return fail(FENGINE_EUNSUPPORTED,
-                    "the tensor-core forms are implemented for 8192 channels (16-point first stage) only");
+                    "the tensor-core forms are implemented for 8192 channels (1024-point second stage) only");
 
     fengine_plan_s *pl = new (std::nothrow) fengine_plan_s();
     if (!pl) return fail(FENGINE_ENOMEM, "host allocation");
@@ -319,9 +318,12 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
             release(pl);
             return fail(FENGINE_EINVAL, "weights must be finite");
         }
-    // Scale for the reduced-precision first stage: |g| <= 512 max_t sum_j |w|
-    // and the 16-point DFT grows it by at most 16, so a power of two s with
-    // s * 16 * 512 * wmax <= 2^14 keeps every operand and result inside FP16.
+    // The reduced-precision second stage reads B[k1][t2] scaled by a power
+    // of two s1 with |s1 B| <= 2^15 (inside FP16): |g| <= 512 max_t sum_j |w|
+    // and the real N1-point first stage grows it by at most N1. The scale is
+    // folded into the first-stage twiddle (exact), the second stage's own
+    // twiddle carries 2^-5 and its rotation 32 / s1 undoes both.
+    float s1 = 1.0f;
     {
         double wmax = 0.0;
         for (long long t = 0; t < N; t++) {
@@ -329,14 +331,10 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
             for (int j = 0; j < T; j++) a += std::fabs((double)w[t + N * j]);
             wmax = a > wmax ? a : wmax;
         }
-        const double bound = 16.0 * 512.0 * (wmax > 0.0 ? wmax : 1.0);
-        pl->dft_scale = (float)std::ldexp(1.0, (int)std::floor(std::log2(16384.0 / bound)));
+        const double bound = (double)pl->N1 * 512.0 * (wmax > 0.0 ? wmax : 1.0);
+        s1 = (float)std::ldexp(1.0, (int)std::floor(std::log2(32768.0 / bound)));
     }
-    // The reduced-precision second stage reads B[k1][t2] scaled by
-    // s1 = 2 dft_scale (|s1 B| <= 16 * 512 * wmax * s1 <= 2^15, inside FP16),
-    // folded into the first-stage twiddle; its own twiddle carries 2^-5 and
-    // the rotation 32 / s1 undoes both.
-    const float s1 = 2.0f * pl->dft_scale;
+    const float tw1_scale = s1;
     std::vector<uint4> tc;
     if (pl->precision != FENGINE_FP32) {
         pl->tc_unscale = 32.0f / s1;
@@ -353,7 +351,7 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     for (int k1 = 0; k1 <= pl->N1 / 2; k1++)
         for (int t2 = 0; t2 < pl->N2; t2++) {
             float2 v = unit_root((long long)k1 * t2, N);
-            if (pl->precision != FENGINE_FP32) v = make_float2(v.x * s1, v.y * s1);   // exact: power of two
+            if (pl->precision != FENGINE_FP32) v = make_float2(v.x * tw1_scale, v.y * tw1_scale);
             tw1[(size_t)k1 * pl->N2 + t2] = v;
         }
     for (int q = 0; q < pl->N2; q++) tw2[q] = unit_root(q, pl->N2);
@@ -545,8 +543,6 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     p1.ctab = pl->d_ctab;
     p1.window_tap = d_window_tap;
     p1.a_spectra = pl->SL;
-    p1.precision = pl->precision;
-    p1.dft_scale = pl->dft_scale;
 
     fe::Phase2Params p2{};
     p2.tw2 = pl->d_tw2;

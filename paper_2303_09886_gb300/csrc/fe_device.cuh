@@ -70,6 +70,40 @@ __device__ __forceinline__ float2 cmul_tw64c(float2 a, int q) {
     return cmul(a, tw64c(q));
 }
 
+// In-register real DFT of NN points (NN = 2, 4, ..., 64): bins 0..NN/2 of
+// X[k] = sum_t x[t] exp(-2 pi i k t / NN), radix-2 decimation in time on the
+// real sequence. With E and O the half-length DFTs of the even and odd
+// samples (both real sequences, so E[NN/2 - k] = conj E[k]),
+//   X[k] = E[k] + w^k O[k],  X[NN/2 - k] = conj(E[k] - w^k O[k]),  k <= NN/4,
+// w = exp(-2 pi i / NN); w^(NN/4) = -i and the k = 0 terms are real.
+template <int NN>
+__device__ __forceinline__ void rdft_reg(const float (&x)[NN], float2 (&X)[NN / 2 + 1]) {
+    if constexpr (NN == 2) {
+        X[0] = make_float2(x[0] + x[1], 0.0f);
+        X[1] = make_float2(x[0] - x[1], 0.0f);
+    } else {
+        constexpr int H = NN / 2, Q = NN / 4;
+        float xe[H], xo[H];
+#pragma unroll
+        for (int t = 0; t < H; t++) {
+            xe[t] = x[2 * t];
+            xo[t] = x[2 * t + 1];
+        }
+        float2 E[Q + 1], O[Q + 1];
+        rdft_reg<H>(xe, E);
+        rdft_reg<H>(xo, O);
+        X[0] = make_float2(E[0].x + O[0].x, 0.0f);
+        X[H] = make_float2(E[0].x - O[0].x, 0.0f);
+#pragma unroll
+        for (int k = 1; k < Q; k++) {
+            const float2 t = cmul_tw64c(O[k], k * (64 / NN));
+            X[k] = cadd(E[k], t);
+            X[H - k] = make_float2(E[k].x - t.x, t.y - E[k].y);
+        }
+        X[Q] = make_float2(E[Q].x, -O[Q].x);
+    }
+}
+
 // In-register NN-point complex DFT with compile-time twiddles (NN <= 64),
 // radix-2 decimation in time; natural order in and out.
 template <int NN>

@@ -5,7 +5,9 @@
 //   k_phase1<T,N1>  unpack + coarse delay + PFB FIR (Eq. 1) + first FFT stage
 //                   (real N1-point DFT over t1, twiddle by exp(-2 pi i k1 t2 / N))
 //   k_phase2<N2>    N2-point FFT over t2 + fine-delay rotation + gain +
-//                   requantise + channel-major corner turn
+//                   requantise + channel-major corner turn (FP32 form), or
+//   k_phase2_tc     the same with the 1024-point FFT as two 32-point DFT
+//                   contractions on tensor cores (FP16 / BF16 forms)
 //   k_tail_update   keep the last H packed samples of every stream
 // with the four-step split t = N2 t1 + t2, k = k1 + N1 k2 of the 2n-point
 // real DFT (the exp(-2 pi i k1 t2 / N) cross term is the twiddle).
@@ -55,8 +57,6 @@ struct Phase1Params {
     int *window_tap;          // optional out [stream][M][N]
     int q_begin, q_count;     // the slab of spectra this launch covers
     int a_spectra;            // spectra per stream in the intermediate buffer
-    int precision;            // 0 FP32 CUDA cores, 1 FP16 / 2 BF16 tensor-core first stage
-    float dft_scale;          // power of two applied before the reduced-precision stage
 };
 
 struct Phase2Params {

@@ -7,23 +7,25 @@
 //   B[k1][t2]     = exp(-2 pi i k1 t2 / N) * sum_t1 g[N2 t1 + t2] exp(-2 pi i k1 t1 / N1).
 // g is real, so only k1 in [0, N1/2] is kept (the rest is the conjugate).
 //
-// One CTA owns a tile of kP1Rows consecutive spectra x C = N1 * W columns
+// One CTA owns kP1Rows consecutive output spectra x C = N1 * W columns
 // {N2 t1 + t2 : t1 < N1, t2 in [t2_0, t2_0 + W)} of one (antenna, pol)
-// stream. For each run of spectra with one coarse delay (Sec. 3.3: each PFB
-// window uses one consistent delay) it
-//   1. unpacks the (rows + T - 1) x N1 row segments of delayed samples into
-//      shared memory as FP32 (exact for 10-bit integers): every thread decodes
-//      whole 5-byte groups of 4 samples aligned to the packed stream, so each
-//      segment of W samples is stored with its 0-3 sample misalignment;
-//   2. runs the T-tap FIR down each column with the weights and a sliding
-//      window of T samples in registers (one shared-memory load and T FMAs
-//      per output), writing g in place;
-// and finally, for each (spectrum, t2), does the real N1-point DFT over t1
-// in registers (an N1/2-point complex FFT of even/odd pairs plus the split),
-// multiplies by the twiddle and stores B to the intermediate.
+// stream. Output row r is the FIR over input rows r .. r + T - 1 (input row
+// i holds the samples of spectrum q0 + i; Eq. 1's w[t + N j] weights row
+// r + j). For each run of output rows with one coarse delay (Sec. 3.3: each
+// PFB window uses one consistent delay) it
+//   1. unpacks the run's input rows into shared memory as FP32 (exact for
+//      10-bit integers): four lanes share a row segment (row, t1) of W
+//      samples and decode whole 5-byte groups aligned to the packed stream,
+//      so a segment is stored with its 0-3 sample misalignment;
+//   2. runs the T-tap FIR down each column: each thread owns two columns
+//      (packed FP32x2 FMAs) and a ring of T + 1 input rows in registers, and
+//      emits output rows in pairs (two independent FMA chains), writing g in
+//      place;
+// and finally, for each (output row, t2), does the real N1-point DFT over
+// t1 in registers, multiplies by the twiddle and stores B to the
+// intermediate.
 #pragma once
 #include "fe_device.cuh"
-#include "fe_mma.cuh"
 #include "fe_internal.cuh"
 
 namespace fe {
@@ -35,12 +37,12 @@ struct P1Shape {
     static constexpr int R = kP1Rows;
     static constexpr int NG = (W + 3) / 4 + 1;   // 4-sample groups per row segment
     static constexpr int SW = 4 * NG;            // shared-memory floats per row segment
-    static constexpr int ROW = N1 * SW;          // floats per tile row
+    static constexpr int ROW = N1 * SW;          // floats per buffered row
     static constexpr int C = N1 * W;             // FIR columns per tile
-    static constexpr int ROWS = R + T - 1;
+    static constexpr int ROWS = R + T - 1;       // input rows of a full tile
+    static constexpr int NI = (NG + 3) / 4;      // groups per lane per segment
+    static constexpr int SPT = 2;                // segments per 4-lane group per batch
 };
-
-constexpr int kUB = 8;   // unpack groups per thread per batch
 
 // A 5-byte group at packed byte b of a 4-byte aligned buffer whose length is
 // a multiple of 4 is read with the two aligned 32-bit words at b & ~3: the
@@ -66,82 +68,97 @@ __device__ __forceinline__ float4 decode_group_perm(unsigned w0, unsigned w1, un
                        field10_to_float(lo));
 }
 
-// ---- reduced-precision form: the 16-point real DFT over t1 on tensor cores
-//
-// For one spectrum row r and 8 consecutive t2 columns the DFT is the real
-// 16 x 16 x 8 product D x G, D[m][t] = cos(2 pi m t / 16) for m < 8,
-// D[8][t] = cos(pi t), D[8 + k][t] = -sin(2 pi k t / 16) for k = 1..7, so
-// that rows m and m + 8 of the result, held by the same lane of
-// mma.m16n8k16, are Re and Im of A[m] (m >= 1) or A[0] and A[8] (m = 0).
-// FP16: one MMA with FP16 operands and FP32 accumulation. BF16: the
-// operands are split into bf16 hi + lo parts and three MMAs
-// (hi.hi + hi.lo + lo.hi) keep the product near FP32 accuracy. Inputs are
-// scaled by the plan's power of two p.dft_scale (from the weights' bound, so
-// every D x G fits FP16) and the results by its inverse.
+// Packed words of one chunk's row segments, loaded ahead of their decode.
+template <class S>
+struct P1Pending {
+    unsigned w0[S::SPT][S::NI], w1[S::SPT][S::NI], j[S::SPT], ga[S::SPT];
+    int mode[S::SPT];   // 0 nothing, 1 fast (words loaded), 2 slow (decoded with its own loads)
+    int dst[S::SPT];    // float offset of the segment in the buffer
+};
 
-// D[m][t] of the 16-point real DFT in the row layout above.
-// (Evaluated once per thread with sincospif on the exactly reduced phase
-// (m t mod 16) / 8; the values are rounded to FP16/BF16 afterwards.)
-__device__ __forceinline__ float dft16_entry(int m, int t) {
-    if (m == 8) return (t & 1) ? -1.0f : 1.0f;
-    const int k = m < 8 ? m : m - 8;
-    float s, c;
-    sincospif((float)((k * t) & 15) / 8.0f, &s, &c);
-    return m < 8 ? c : -s;
-}
+struct P1Stream {
+    const uint8_t *chunk, *hist;
+    unsigned rel0, H, HL;   // relative sample index of (input row 0, t1 0, w 0); history; history + chunk
+};
 
-template <int PREC, int ROW, int SW, int W>
-__device__ __forceinline__ void dft16_tensor(const Phase1Params &p, const float *xs, const int *off_sm,
-                                             const float2 *tw1_sm, int Rv, int stream, int q0, int t2_0) {
-    constexpr int H1 = 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, c = lane & 3;
-    // A fragments (rows g, g+8; columns 2c, 2c+1, 2c+8, 2c+9)
-    unsigned ahi[4], alo[4];
-    {
-        const int rows[4] = {g, g + 8, g, g + 8}, cols[4] = {2 * c, 2 * c, 2 * c + 8, 2 * c + 8};
+// Issue the loads of segments seg0 + u * (kP1Threads / 4) + (this lane's
+// slot), u < SPT, of input rows [i0, i_end): segment (i - i0) * N1 + t1.
+// Four lanes share a segment: lane l4 takes groups l4 + 4 k, 20 k bytes
+// apart, so its byte alignment and word offsets are fixed per segment. A
+// warp's 8 segments are permuted so that the two sharing an 8-lane phase of
+// the 16-byte stores are 4 apart in t1 (4 SW floats: no bank conflicts).
+template <class S, int N1>
+__device__ __forceinline__ void p1_load(P1Pending<S> &pd, const P1Stream &st, int seg0, int i0, int i_end, int N,
+                                        int N2) {
+    const int l4 = threadIdx.x & 3, sl = (threadIdx.x >> 2) & 7;
+    const int seg_lane = (threadIdx.x >> 5) * 8 + (sl & 1) * 4 + (sl >> 1);
+    const int nseg = (i_end - i0) * N1;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const float v0 = dft16_entry(rows[i], cols[i]), v1 = dft16_entry(rows[i], cols[i] + 1);
-            ahi[i] = pack2<PREC>(v0, v1);
-            if constexpr (PREC == 2) alo[i] = pack2<PREC>(v0 - bf16_round(v0), v1 - bf16_round(v1));
-        }
-    }
-    const float sc = p.dft_scale, usc = 1.0f / p.dft_scale;
-    const int N2 = p.N2;
-    constexpr int NT = W / 8;                      // n-tiles per spectrum row
-    for (int tile = warp; tile < Rv * NT; tile += kP1Threads / 32) {
-        const int r = tile / NT, w0 = (tile % NT) * 8;
-        const float *x = xs + r * ROW + off_sm[r] + w0 + g;   // column n = g of the tile
-        const float x0 = x[(2 * c) * SW] * sc, x1 = x[(2 * c + 1) * SW] * sc;
-        const float x8 = x[(2 * c + 8) * SW] * sc, x9 = x[(2 * c + 9) * SW] * sc;
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
-        const unsigned b0 = pack2<PREC>(x0, x1), b1 = pack2<PREC>(x8, x9);
-        mma16816<PREC>(d, ahi, b0, b1);
-        if constexpr (PREC == 2) {
-            const unsigned l0 = pack2<PREC>(x0 - bf16_round(x0), x1 - bf16_round(x1));
-            const unsigned l1 = pack2<PREC>(x8 - bf16_round(x8), x9 - bf16_round(x9));
-            mma16816<PREC>(d, ahi, l0, l1);
-            mma16816<PREC>(d, alo, b0, b1);
-        }
-        // lane holds columns 2c, 2c+1 of rows g (Re A[g]) and g + 8 (Im A[g], or
-        // A[8] for g = 0, whose own Im is zero); every lane stores A[g], the
-        // g = 0 lanes store A[8] as well
-        const int w = w0 + 2 * c, t2 = t2_0 + w;
-        float2 *out = p.A + ((long long)stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) * N2 + t2;
-        const float i0 = g ? d[2] : 0.f, i1 = g ? d[3] : 0.f;
-        const float2 e0 = cmul(make_float2(d[0] * usc, i0 * usc), tw1_sm[g * W + w]);
-        const float2 e1 = cmul(make_float2(d[1] * usc, i1 * usc), tw1_sm[g * W + w + 1]);
-        *reinterpret_cast<float4 *>(out + (long long)g * N2) = make_float4(e0.x, e0.y, e1.x, e1.y);
-        if (g == 0) {
-            const float2 f0 = cmul(make_float2(d[2] * usc, 0.f), tw1_sm[8 * W + w]);
-            const float2 f1 = cmul(make_float2(d[3] * usc, 0.f), tw1_sm[8 * W + w + 1]);
-            *reinterpret_cast<float4 *>(out + (long long)8 * N2) = make_float4(f0.x, f0.y, f1.x, f1.y);
+    for (int u = 0; u < S::SPT; u++) {
+        const int seg = seg0 + u * (kP1Threads / 4) + seg_lane;
+        const int t1 = seg & (N1 - 1), i = i0 + seg / N1;
+        pd.mode[u] = 0;
+        pd.j[u] = 0u;
+        pd.ga[u] = 0u;
+        pd.dst[u] = i * S::ROW + t1 * S::SW;
+        if (seg < nseg) {
+            // sample indices relative to the first history sample fit 32 bits
+            // (the plan keeps H + L < 2^31)
+            const unsigned ga = (st.rel0 + (unsigned)(N * i + N2 * t1)) & ~3u;   // first group's sample
+            const unsigned ge = ga + 4u * S::NG;                                 // one past the last
+            pd.ga[u] = ga;
+            const bool in_hist = ge <= st.H, in_chunk = ga >= st.H && ge <= st.HL;
+            pd.mode[u] = (in_hist || in_chunk) ? 1 : 2;
+            if (pd.mode[u] == 1) {
+                const unsigned bl = ((in_hist ? ga : ga - st.H) >> 2) * 5u + 5u * l4;
+                const unsigned *wp =
+                    reinterpret_cast<const unsigned *>((in_hist ? st.hist : st.chunk) + (bl & ~3u));
+                pd.j[u] = bl & 3u;
+#pragma unroll
+                for (int k = 0; k < S::NI; k++) {
+                    if (l4 + 4 * k < S::NG) {
+                        pd.w0[u][k] = __ldg(wp + 5 * k);
+                        pd.w1[u][k] = __ldg(wp + 5 * k + 1);
+                    }
+                }
+            }
         }
     }
 }
 
-template <int T, int N1, int W, int PREC = 0>
+template <class S>
+__device__ __forceinline__ void p1_decode(const P1Pending<S> &pd, const P1Stream &st, float *buf) {
+    const int l4 = threadIdx.x & 3;
+#pragma unroll
+    for (int u = 0; u < S::SPT; u++) {
+        float *dst = buf + pd.dst[u];
+        if (pd.mode[u] == 1) {
+#pragma unroll
+            for (int k = 0; k < S::NI; k++)
+                if (l4 + 4 * k < S::NG)
+                    *reinterpret_cast<float4 *>(dst + 4 * l4 + 16 * k) =
+                        decode_group_perm(pd.w0[u][k], pd.w1[u][k], pd.j[u]);
+        } else if (pd.mode[u] == 2) {
+            // straddles the history/chunk boundary or the end of the received
+            // samples (zeros past it)
+            for (int gi = l4; gi < S::NG; gi += 4) {
+                const unsigned g = pd.ga[u] + 4u * gi;
+                unsigned v0 = 0u, v1 = 0u, j = 0u;
+                if (g < st.HL) {
+                    const bool h = g < st.H;
+                    const unsigned bb = ((h ? g : g - st.H) >> 2) * 5u;
+                    const unsigned *wq = reinterpret_cast<const unsigned *>((h ? st.hist : st.chunk) + (bb & ~3u));
+                    v0 = __ldg(wq);
+                    v1 = __ldg(wq + 1);
+                    j = bb & 3u;
+                }
+                *reinterpret_cast<float4 *>(dst + 4 * gi) = decode_group_perm(v0, v1, j);
+            }
+        }
+    }
+}
+
+template <int T, int N1, int W>
 __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) {
     using S = P1Shape<T, N1, W>;
     constexpr int R = S::R, H1 = N1 / 2;
@@ -155,10 +172,12 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
     const int t2_0 = blockIdx.x * W;
     const int q0 = p.q_begin + blockIdx.y * R;
     const int Rv = min(R, p.q_begin + p.q_count - q0);
-    const uint8_t *chunk = p.chunk + (long long)stream * p.chunk_bytes;
-    const uint8_t *hist = p.hist + (long long)stream * p.hist_bytes;
-    const long long HL = p.H + p.L;
-    // rel index (from the first history sample) of tile row 0, column t = 0, before the delay
+    P1Stream st;
+    st.chunk = p.chunk + (long long)stream * p.chunk_bytes;
+    st.hist = p.hist + (long long)stream * p.hist_bytes;
+    st.H = (unsigned)p.H;
+    st.HL = (unsigned)(p.H + p.L);
+    // rel index (from the first history sample) of input row 0, column t = 0, before the delay
     const long long rel_base = (long long)N * (p.m0 + q0) - (p.t_in - p.H) + t2_0;
 
     for (int i = threadIdx.x; i < Rv; i += kP1Threads) c_sm[i] = p.ctab[(long long)stream * p.M + q0 + i];
@@ -168,55 +187,25 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
     }
     __syncthreads();
 
-    int off = 0;   // misalignment (0..3) of every segment of the current run
+    P1Pending<S> pd;
     int ra = 0;
     while (ra < Rv) {
         const int cd = c_sm[ra];
         int rb = ra + 1;
         while (rb < Rv && c_sm[rb] == cd) rb++;
-        const long long rel0 = rel_base - cd;  // rel of (row 0, t1 0, w 0) at this delay
-        off = (int)(rel0 & 3);
-        // 1. unpack rows [ra, rb + T - 1), whole aligned groups
-        const int rows = rb + T - 1 - ra;
-        const int ngroups = rows * N1 * S::NG;
-        // batches of kUB groups per thread: all word loads of a batch are in
-        // flight before the first is decoded
-        // sample indices relative to the first history sample fit 32 bits (the
-        // plan keeps H + L < 2^31)
-        const unsigned rel0u = (unsigned)rel0, Hu = (unsigned)p.H, HLu = (unsigned)HL;
-        for (int e0 = 0; e0 < ngroups; e0 += kUB * kP1Threads) {
-            unsigned w0[kUB], w1[kUB], j[kUB];
-            int dst[kUB];
-#pragma unroll
-            for (int u = 0; u < kUB; u++) {
-                const int e = e0 + u * kP1Threads + threadIdx.x;
-                dst[u] = -1;
-                w0[u] = w1[u] = 0u;
-                j[u] = 0u;
-                if (e < ngroups) {
-                    const int gi = e % S::NG;
-                    const int seg = e / S::NG;
-                    const int t1 = seg % N1, row = ra + seg / N1;
-                    const unsigned g = ((rel0u + (unsigned)(N * row + N2 * t1)) & ~3u) + 4u * gi;
-                    dst[u] = row * S::ROW + t1 * S::SW + 4 * gi;
-                    if (g < HLu) {   // else past the received samples: zeros
-                        const bool h = g < Hu;
-                        const unsigned b = ((h ? g : g - Hu) >> 2) * 5u;
-                        const unsigned *wp = reinterpret_cast<const unsigned *>((h ? hist : chunk) + (b & ~3u));
-                        w0[u] = __ldg(wp);
-                        w1[u] = __ldg(wp + 1);
-                        j[u] = b & 3u;
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kUB; u++) {
-                if (dst[u] < 0) continue;
-                *reinterpret_cast<float4 *>(xs + dst[u]) = decode_group_perm(w0[u], w1[u], j[u]);
-            }
+        const long long rel0 = rel_base - cd;   // rel of (input row 0, t1 0, w 0) at this delay
+        st.rel0 = (unsigned)rel0;
+        const int off = (int)(rel0 & 3);         // misalignment of every segment of the run
+        const int i_end = rb + T - 1;            // input rows [ra, i_end)
+        // 1. unpack, SPT segments per 4-lane group per batch with all their
+        // loads in flight before the first decode
+        for (int seg0 = 0; seg0 < (i_end - ra) * N1; seg0 += S::SPT * (kP1Threads / 4)) {
+            p1_load<S, N1>(pd, st, seg0, ra, i_end, N, N2);
+            p1_decode<S>(pd, st, xs);
         }
         __syncthreads();
         if (p.window_tap) {
+            // the window tap of output row r is its first input row, i = r
             for (int e = threadIdx.x; e < (rb - ra) * S::C; e += kP1Threads) {
                 const int row = ra + e / S::C, col = e % S::C;
                 const int t1 = col / W, w = col % W;
@@ -235,7 +224,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
                 float *xa = xs + (ca / W) * S::SW + off + ca % W;
                 float *xb = xs + (cb / W) * S::SW + off + cb % W;
                 // outputs in pairs (r, r + 1), two independent FMA chains, from a
-                // ring of T + 1 window rows
+                // ring of T + 1 input rows
                 float2 w2[T], win[T + 1];
 #pragma unroll
                 for (int j = 0; j < T; j++)
@@ -256,6 +245,15 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
                         xa[(r + 1) * S::ROW] = acc1.x;
                         xb[(r + 1) * S::ROW] = acc1.y;
                     }
+                }
+                if constexpr ((R & 1) != 0) {
+                    // R odd: the last output row has no partner
+                    constexpr int r = R - 1;
+                    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int j = 0; j < T; j++) acc = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc);
+                    xa[r * S::ROW] = acc.x;
+                    xb[r * S::ROW] = acc.y;
                 }
             }
         } else
@@ -284,50 +282,38 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
     }
 
     // 3. real N1-point DFT over t1, twiddle, store B[k1][t2]
-    if constexpr (PREC != 0) {
-        dft16_tensor<PREC, S::ROW, S::SW, W>(p, xs, off_sm, tw1_sm, Rv, stream, q0, t2_0);
-    } else
-    for (int pi = threadIdx.x; pi < Rv * W; pi += kP1Threads) {
-        const int r = pi / W, w = pi % W;
+    for (int e = threadIdx.x; e < Rv * W; e += kP1Threads) {
+        const int r = e / W, w = e % W;
         const float *g = xs + r * S::ROW + off_sm[r] + w;
-        float2 z[H1];
+        float x[N1];
 #pragma unroll
-        for (int q = 0; q < H1; q++) z[q] = make_float2(g[(2 * q) * S::SW], g[(2 * q + 1) * S::SW]);
-        fft_regc<H1>(z);
+        for (int t1 = 0; t1 < N1; t1++) x[t1] = g[t1 * S::SW];
+        float2 X[H1 + 1];
+        rdft_reg<N1>(x, X);
         float2 *out = p.A + ((long long)stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) * N2 + t2_0 + w;
+        const float2 t0 = tw1_sm[w];   // exp(0), times the plan's scale
+        out[0] = make_float2(X[0].x * t0.x, X[0].x * t0.y);
 #pragma unroll
-        for (int k = 0; k <= H1; k++) {
-            const float2 zk = z[k % H1], zm = z[(H1 - k) % H1];
-            // even part E = (Z[k] + conj Z[H1-k]) / 2, odd part O = (Z[k] - conj Z[H1-k]) / 2i
-            const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-            const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-            const float2 a = cadd(E, k == H1 ? make_float2(-O.x, -O.y) : cmul_tw64c(O, k * (64 / N1)));
-            out[(long long)k * N2] = cmul(a, tw1_sm[k * W + w]);
-        }
+        for (int k = 1; k < H1; k++) out[(long long)k * N2] = cmul(X[k], tw1_sm[k * W + w]);
+        const float2 th = tw1_sm[H1 * W + w];
+        out[(long long)H1 * N2] = make_float2(X[H1].x * th.x, X[H1].x * th.y);
     }
 }
 
-template <int T, int N1, int W, int PREC = 0>
+template <int T, int N1, int W>
 cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t s) {
     using S = P1Shape<T, N1, W>;
     if (p.W != W || p.N2 % W) return cudaErrorInvalidValue;
     const size_t smem = (size_t)S::ROWS * S::ROW * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_phase1<T, N1, W, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_phase1<T, N1, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(p.N2 / W, (p.q_count + kP1Rows - 1) / kP1Rows, n_streams);
-    k_phase1<T, N1, W, PREC><<<grid, kP1Threads, smem, s>>>(p);
+    k_phase1<T, N1, W><<<grid, kP1Threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <int T>
 cudaError_t launch_phase1_n1(int N1, const Phase1Params &p, int n_streams, cudaStream_t s) {
-    if (p.precision != 0) {
-        // reduced-precision form: tensor-core 16-point first stage (N1 = 16)
-        if (N1 != 16 || p.W != 32) return cudaErrorInvalidValue;
-        return p.precision == 1 ? launch_phase1_tw<T, 16, 32, 1>(p, n_streams, s)
-                                : launch_phase1_tw<T, 16, 32, 2>(p, n_streams, s);
-    }
     switch (N1 * 1000 + p.W) {
         case 8064: return launch_phase1_tw<T, 8, 64>(p, n_streams, s);
         case 16032: return launch_phase1_tw<T, 16, 32>(p, n_streams, s);

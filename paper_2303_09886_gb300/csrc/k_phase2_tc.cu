@@ -43,29 +43,26 @@ constexpr int kTcThreads = 256;
 constexpr int kTcR = 8;          // spectra per CTA, one warp each
 constexpr int kTcN2 = 1024;
 constexpr int kGainLd = kTcN2 + kTcN2 / 8;   // padded gain row (conflict-free 8-byte loads)
-constexpr int kPQ = 96;                      // per sequence: P[32], Pup[32], Q[32]
+constexpr int kPQ = 65;                      // per sequence: P[32], Q[32], qu
+constexpr int kStgLd = kTcN2 + kTcN2 / 4 + 4; // staging row stride in words (= 4 mod 32)
 
-// padded gain slot: lanes (g, q) of one load touch k2 = base + g + 32 q
+// Padded slots. A lane (g, q) of the epilogue handles k2 = g + 32 q + const
+// (const < 32 apart from multiples of 128), so (k2 >> 5) = q + const / 32:
+//   gain slot    k2 + 4 (k2 >> 5)  -> 8-byte loads without bank conflicts,
+//   staging word k2 + 8 (k2 >> 5)  -> 2-byte stores without bank conflicts,
+// and the row stride kStgLd = 4 (mod 32) keeps the corner-turn reads (four
+// spectra of one slot per thread) conflict-free as well.
 __device__ __forceinline__ int gain_slot(int k2) { return k2 + 4 * (k2 >> 5); }
-
-// 32-bit word of output cell (slot k2, spectrum r) in the staging buffer:
-// the 8 cells of a slot are permuted by an XOR of k2's bits 2, 5 and 6 so
-// that the lanes (g, q) of one store (k2 = base + g + 32 q) hit 32 banks.
-__device__ __forceinline__ int stage_word(int k2, int r) {
-    return k2 * kTcR + (r ^ (((k2 >> 2) & 1) | ((k2 >> 4) & 6)));
-}
-
-__device__ __forceinline__ unsigned short q8pair(float2 y) {
-    return (unsigned short)(((unsigned)quant8(y.x) & 0xFFu) | (((unsigned)quant8(y.y) & 0xFFu) << 8));
-}
+__device__ __forceinline__ int stage_slot(int k2) { return k2 + 8 * (k2 >> 5); }
 
 }  // namespace
 
 // shared memory: tables (hi; lo for BF16) + P/Q + gains + staging + row info
 size_t phase2_tc_smem_bytes(int precision) {
     const int nl = precision == 2 ? 2 : 1;
-    return sizeof(uint4) * 512 * (1 + 2 * nl) + sizeof(float2) * 2 * kTcR * kPQ + sizeof(float2) * 2 * kGainLd +
-           sizeof(unsigned) * kTcN2 * kTcR + (sizeof(long long) + sizeof(int)) * kTcR;
+    const size_t pq = (sizeof(float2) * 2 * kTcR * kPQ + 15) / 16 * 16;
+    return sizeof(uint4) * 512 * (1 + 2 * nl) + pq + sizeof(float2) * 2 * kGainLd +
+           sizeof(unsigned) * kStgLd * kTcR + (sizeof(long long) + sizeof(int)) * kTcR;
 }
 
 template <int PREC>
@@ -77,9 +74,9 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
     const float4 *tws = reinterpret_cast<const float4 *>(smu + 1024);
     const uint4 *a1l = smu + 1536, *b2l = smu + 2048;
     float2 *pq = reinterpret_cast<float2 *>(smu + (LO ? 2560 : 1536));   // [2 kTcR][kPQ]
-    float2 *gsm = pq + 2 * kTcR * kPQ;                                   // [2][kGainLd]
-    unsigned *stg = reinterpret_cast<unsigned *>(gsm + 2 * kGainLd);     // [kTcN2][kTcR]
-    long long *rowoff = reinterpret_cast<long long *>(stg + kTcN2 * kTcR);
+    float2 *gsm = pq + (2 * kTcR * kPQ + 1) / 2 * 2;                     // [2][kGainLd]
+    unsigned *stg = reinterpret_cast<unsigned *>(gsm + 2 * kGainLd);     // [kTcR][kStgLd]
+    long long *rowoff = reinterpret_cast<long long *>(stg + kStgLd * kTcR);
     int *rowstride = reinterpret_cast<int *>(rowoff + kTcR);
 
     const int k1 = blockIdx.x, ant = blockIdx.z;
@@ -91,26 +88,25 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
 
     for (int i = threadIdx.x; i < (LO ? 2560 : 1536); i += kTcThreads) smu[i] = __ldg(p.tc + i);
     // rotation factors of each (pol, spectrum) sequence, angles over pi:
-    //   P[c]   = u exp(i pi (phi/pi - 2 delta (k1 + N1 c) / N))    (lower half)
-    //   Pup[c] = u exp(i pi (phi/pi - 2 delta + 2 delta (k1 + N1 c) / N))
-    //   Q[d]   = exp(-i pi 2 delta 32 N1 d / N)
-    // so that channel k1 + N1 k2 (k2 = c + 32 d) takes P[c] Q[d] F and the
-    // upper-half channel N - (k1 + N1 k2) takes Pup[c] conj(Q[d] F).
+    //   P[c] = u exp(i pi (phi/pi - 2 delta (k1 + N1 c) / N)),
+    //   Q[d] = exp(-i pi 2 delta 32 N1 d / N),  qu = exp(i pi (2 phi/pi - 2 delta)),
+    // so that channel k1 + N1 k2 (k2 = c + 32 d) is P[c] Q[d] F[k2] and the
+    // upper-half channel N - (k1 + N1 k2) is qu conj(P[c] Q[d] F[k2]).
     const float inv = 2.0f / (float)N, u = p.tc_unscale;
     for (int e = threadIdx.x; e < 2 * kTcR * kPQ; e += kTcThreads) {
-        const int sq = e / kPQ, j = e % kPQ;
+        const int sq = e / kPQ, j = e - sq * kPQ;
         const int pol = sq / kTcR, r = sq % kTcR;
         if (r >= Rv) continue;
         const float2 f = p.ftab[(long long)(ant * 2 + pol) * M + q0 + r];   // (delta, phi / pi)
         const int c = j & 31;
-        float ang, sc = u;
+        float ang, sc = 1.0f;
         if (j < 32) {
             ang = f.y - f.x * (float)(k1 + N1 * c) * inv;
+            sc = u;
         } else if (j < 64) {
-            ang = f.y - 2.0f * f.x + f.x * (float)(k1 + N1 * c) * inv;
-        } else {
             ang = -f.x * (float)(32 * N1 * c) * inv;
-            sc = 1.0f;
+        } else {
+            ang = 2.0f * f.y - 2.0f * f.x;
         }
         float sn, cs;
         sincospif(ang, &sn, &cs);
@@ -210,8 +206,11 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
                 }
             }
             const float2 *pqs = pq + (pol * kTcR + r) * kPQ;
+            const float2 qu = pqs[64];
             float2 *pre = p.prequant ? p.prequant + ((long long)stream * M + q0 + r) * n : nullptr;
-            const float2 *gp = gsm + pol * kGainLd;
+            // lane parts of the gain slot and staging slot of k2 = g + 32 tq + 16 mp + 8 h + 128 nt2
+            const float2 *gp = gsm + pol * kGainLd + g + 36 * tq;
+            unsigned short *sp = stg16 + 2 * (r * kStgLd + g + 40 * tq) + pol;
             // contraction 2 and the epilogue, per m tile and per half of the
             // output columns (d < 16: lower-half channels, d >= 16: upper)
 #pragma unroll
@@ -243,25 +242,24 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
                     }
                     // rotation, gain, requantisation into the staging cells
 #pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        const int nt2 = 4 * half + j;
-                        const float2 Qd = pqs[64 + 4 * nt2 + tq];
+                    for (int h = 0; h < 2; h++) {
+                        const int cl = 16 * mp + 8 * h;          // c = cl + g
+                        float2 Pc = pqs[cl + g];
+                        if (half == 1) Pc = cmul(qu, cconj(Pc));
 #pragma unroll
-                        for (int h = 0; h < 2; h++) {
-                            const int c = 16 * mp + 8 * h + g;
-                            const int k2 = c + 32 * (4 * nt2 + tq);
-                            const float2 F = make_float2(d2[j][2 * h], d2[j][2 * h + 1]);
-                            float2 y;
-                            int k;
-                            if (half == 0) {
-                                y = cmul(gp[gain_slot(k2)], cmul(cmul(pqs[c], Qd), F));
-                                k = k1 + N1 * k2;
-                            } else {
-                                y = cmul(gp[gain_slot(k2)], cmul(cmul(pqs[32 + c], cconj(Qd)), cconj(F)));
-                                k = N - (k1 + N1 * k2);
+                        for (int j = 0; j < 4; j++) {
+                            const int nt2 = 4 * half + j;
+                            float2 rot = pqs[32 + 4 * nt2 + tq];
+                            rot = half == 0 ? cmul(Pc, rot) : cmul(Pc, cconj(rot));
+                            float2 F = make_float2(d2[j][2 * h], d2[j][2 * h + 1]);
+                            if (half == 1) F = cconj(F);
+                            const float2 y = cmul(gp[cl + 144 * nt2], cmul(rot, F));
+                            if (pre) {
+                                const int k2 = cl + g + 32 * (4 * nt2 + tq);
+                                pre[half == 0 ? k1 + N1 * k2 : N - (k1 + N1 * k2)] = y;
                             }
-                            if (pre) pre[k] = y;
-                            stg16[2 * stage_word(k2, r) + pol] = q8pair(y);
+                            sp[2 * (cl + 160 * nt2)] =
+                                (unsigned short)__byte_perm((unsigned)quant8(y.x), (unsigned)quant8(y.y), 0x0040u);
                         }
                     }
                 }
@@ -270,14 +268,30 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
     }
     __syncthreads();
 
-    // corner turn: cell (slot k2, spectrum r) -> heap row of channel k
+    // corner turn: cell (slot k2, spectrum r) -> heap row of channel k. When
+    // each group of four spectra shares a heap and its cells are 16-byte
+    // aligned (spectra per heap and the heap's size multiples of 4), a thread
+    // writes four spectra of a slot with one 16-byte store.
     int8_t *out = p.out + (long long)ant * M * n * 4;
-    for (int e = threadIdx.x; e < nslot * kTcR; e += kTcThreads) {
-        const int k2 = e / kTcR, rr = e % kTcR;
-        if (rr >= Rv) continue;
-        const int kc = k1 + N1 * k2;
-        const int k = k2 >= kTcN2 / 2 ? N - kc : kc;
-        *reinterpret_cast<unsigned *>(out + rowoff[rr] + (long long)k * rowstride[rr]) = stg[stage_word(k2, rr)];
+    const bool vec = Rv == kTcR && S_ % 4 == 0 && rowstride[0] % 16 == 0 && rowstride[4] % 16 == 0;
+    if (vec) {
+        for (int e = threadIdx.x; e < nslot * 2; e += kTcThreads) {
+            const int k2 = e >> 1, r4 = 4 * (e & 1);
+            const int kc = k1 + N1 * k2;
+            const int k = k2 >= kTcN2 / 2 ? N - kc : kc;
+            const unsigned *cell = stg + r4 * kStgLd + stage_slot(k2);
+            const uint4 v = make_uint4(cell[0], cell[kStgLd], cell[2 * kStgLd], cell[3 * kStgLd]);
+            *reinterpret_cast<uint4 *>(out + rowoff[r4] + (long long)k * rowstride[r4]) = v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < nslot * kTcR; e += kTcThreads) {
+            const int k2 = e / kTcR, rr = e % kTcR;
+            if (rr >= Rv) continue;
+            const int kc = k1 + N1 * k2;
+            const int k = k2 >= kTcN2 / 2 ? N - kc : kc;
+            *reinterpret_cast<unsigned *>(out + rowoff[rr] + (long long)k * rowstride[rr]) =
+                stg[rr * kStgLd + stage_slot(k2)];
+        }
     }
 }
 
