@@ -376,6 +376,41 @@ def run_service(args):
     return 0
 
 
+def _time_form(fengine, torch, wl, name, d_in, args):
+    """Device time of `args.steps` calls of one precision form on the resident input."""
+    prec = {"fp32": fengine.FP32, "fp16": fengine.TC_FP16, "bf16": fengine.TC_BF16}[name]
+    plan = fengine.Plan(wl.n_antennas, wl.n_channels, wl.n_taps, wl.chunk_samples,
+                        spectra_per_heap=wl.spectra_per_heap, max_delay_samples=wl.max_delay, precision=prec)
+    for a, p, d, r, ph, pr in wl.delays():
+        plan.set_delay(a, p, d, r, ph, pr)
+    g = wl.gains()
+    if g is not None:
+        for a in range(wl.n_antennas):
+            for p in range(2):
+                plan.set_gains(a, p, g[a, p])
+    d_out = torch.empty(plan.info.out_bytes, dtype=torch.int8, device="cuda")
+    stream = torch.cuda.current_stream()
+    t = 0
+    for _ in range(args.warmup):
+        plan.process(d_in, t, d_out, stream=stream)
+        t += wl.chunk_samples
+    plan.set_profiling(True)
+    plan.stage_times()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.process(d_in, t, d_out, stream=stream)
+        t += wl.chunk_samples
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stage_ms, calls = plan.stage_times()
+    plan.close()
+    return {"value": wl.samples_per_step * args.steps / (ms / 1e3) / 1e9, "ms_per_step": ms / args.steps,
+            "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()}}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,6 +426,7 @@ def main(argv=None):
     ap.add_argument("--pool", type=int, default=8, help="workloads 4/5: internal CUDA streams")
     ap.add_argument("--chunks", type=int, default=8, help="workload 5: chunks per antenna")
     ap.add_argument("--load", type=float, default=1.5, help="workload 5: offered load / sustained rate")
+    ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision forms")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="fp32 plain form, or the tensor-core forms (FP16/BF16 operands, FP32 accumulation)")
     args = ap.parse_args(argv)
@@ -480,19 +516,53 @@ def main(argv=None):
     # chunk from pinned memory, the call, D2H of the 8-bit output, every step
     e2e = None
     if not args.no_e2e:
-        h_out = torch.empty(plan.info.out_bytes, dtype=torch.int8).pin_memory()
-        for _ in range(2):
-            d_in.copy_(h_in, non_blocking=True)
-            step()
-            h_out.copy_(d_out, non_blocking=True)
+        # End to end through the public API with host buffers, pipelined the
+        # way a streaming receiver runs: two device input and output buffers,
+        # the H2D copy of step k + 1 and the D2H copy of step k - 1 on their
+        # own streams while step k computes. Every step's copies lie inside
+        # the timed region (it opens before the first H2D and closes after
+        # the last D2H).
+        d_ins = [d_in, torch.empty_like(d_in)]
+        d_outs = [d_out, torch.empty_like(d_out)]
+        h_outs = [torch.empty(plan.info.out_bytes, dtype=torch.int8).pin_memory() for _ in range(2)]
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def run_e2e(k_steps):
+            ev_in = [torch.cuda.Event() for _ in range(2)]
+            ev_done = [torch.cuda.Event() for _ in range(2)]
+            ev_out = [torch.cuda.Event() for _ in range(2)]
+            s_in.wait_stream(stream)
+            s_out.wait_stream(stream)
+            with torch.cuda.stream(s_in):
+                d_ins[0].copy_(h_in, non_blocking=True)
+            ev_in[0].record(s_in)
+            for k in range(k_steps):
+                b = k & 1
+                if k + 1 < k_steps:
+                    if k >= 1:
+                        s_in.wait_event(ev_done[1 - b])      # compute k - 1 has read that buffer
+                    with torch.cuda.stream(s_in):
+                        d_ins[1 - b].copy_(h_in, non_blocking=True)
+                    ev_in[1 - b].record(s_in)
+                stream.wait_event(ev_in[b])
+                if k >= 2:
+                    stream.wait_event(ev_out[b])             # D2H of step k - 2 has drained d_outs[b]
+                plan.process(d_ins[b], t_next[0], d_outs[b], stream=stream)
+                t_next[0] += L
+                ev_done[b].record(stream)
+                s_out.wait_event(ev_done[b])
+                with torch.cuda.stream(s_out):
+                    h_outs[b].copy_(d_outs[b], non_blocking=True)
+                ev_out[b].record(s_out)
+            stream.wait_stream(s_in)
+            stream.wait_stream(s_out)
+
+        run_e2e(3)
         torch.cuda.synchronize()
         k2 = max(3, min(args.steps, 20))
         e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e2.record(stream)
-        for _ in range(k2):
-            d_in.copy_(h_in, non_blocking=True)
-            step()
-            h_out.copy_(d_out, non_blocking=True)
+        run_e2e(k2)
         e3.record(stream)
         torch.cuda.synchronize()
         ems = e2.elapsed_time(e3)
@@ -501,8 +571,17 @@ def main(argv=None):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ems = float(t.item())
         e2e = {"value": ws * wl.samples_per_step * k2 / (ems / 1e3) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(h_in.numel()), "d2h_bytes_per_step": int(h_out.numel()),
-               "steps": k2}
+               "h2d_bytes_per_step": int(h_in.numel()), "d2h_bytes_per_step": int(h_outs[0].numel()),
+               "steps": k2, "pipelined": "H2D of step k+1 and D2H of step k-1 overlap step k"}
+    # the other precision forms on the same input, same timing (context for
+    # the FP32-plain vs tensor-core comparison; 8192-channel shapes only)
+    forms = None
+    if ws == 1 and not args.no_forms and wl.n_channels == 8192:
+        forms = {args.precision: {"value": value, "ms_per_step": ms_max / args.steps,
+                                  "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()}}}
+        for name in ("fp32", "fp16", "bf16"):
+            if name != args.precision:
+                forms[name] = _time_form(fengine, torch, wl, name, d_in, args)
     clocks.stop()
 
     if rank != 0:
@@ -548,6 +627,7 @@ def main(argv=None):
                  "bytes_per_sample": {"algorithmic": 2.25, "with_intermediates": 2.25 + 2 * inter}},
         "e2e": e2e,
         "gpu_launches": (2 + 2 * slabs) * args.steps,
+        "forms": forms,
         "clocks": clocks.summary(w0, w1),
     }
     if not args.no_cpu and ws == 1:
