@@ -36,7 +36,17 @@ UNIT = "Gsample/s"
 # DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the hash of the kernel sources it was
 # taken on; reported as null once the sources change.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) of one launch of each slab kernel from an ncu
+# capture (profiles/, 1 antenna x 2 pol x 2^24 samples/pol: one slab launch of
+# 2 x 256 spectra, the same 8.4 M input samples as one slab launch of the
+# 4-antenna workload). ncu flushes the caches before each replay, so these are
+# cold-cache figures. Keyed by kernel; valid only for the sources they were
+# taken from (src = hash of csrc/).
+NCU_TRAFFIC = {
+    "k_phase1<16,16,32>": {"bytes_per_launch": 12265472 + 18176, "src": "e27c87cc862ccde6"},
+    "k_phase2<1024>": {"bytes_per_launch": 37925632 + 256, "src": "e27c87cc862ccde6"},
+    "k_phase2_tc<1>": {"bytes_per_launch": 37964032 + 15104, "src": "e27c87cc862ccde6"},
+}
 
 
 def _src_hash() -> str:
@@ -601,7 +611,10 @@ def main(argv=None):
     peak, peak_kind = _peaks()
     # algorithmic bytes of one launch (its slab's samples) / its mean duration
     achieved = bytes_per_sample[dom] * (spl / slabs) / (launch_ms / 1e3) / 1e9
-    tr = NCU_TRAFFIC.get(dom)
+    N2 = plan.info.fft_n2
+    kname = {"phase1": f"k_phase1<{wl.n_taps},{N1},{min(512 // N1, N2)}>",
+             "phase2": {"fp32": f"k_phase2<{N2}>", "fp16": "k_phase2_tc<1>", "bf16": "k_phase2_tc<2>"}[args.precision]}[dom]
+    tr = NCU_TRAFFIC.get(kname)
     traffic = tr["bytes_per_launch"] if tr and tr.get("src") == _src_hash() else None
     step_ms = ms_max / args.steps
     path_alg = 2.25 * spl / (step_ms / 1e3) / 1e9
@@ -616,7 +629,7 @@ def main(argv=None):
                    "precision": args.precision, "parallelism": f"replicas x{ws}",
                    "l2": f"inputs larger than L2: {h_in.numel() >> 20} MiB packed in + "
                          f"{plan.info.out_bytes >> 20} MiB out per step"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_sample": bytes_per_sample[dom],
                      "launch_ms": launch_ms, "launches_per_step": slabs,

@@ -115,7 +115,7 @@ __device__ __forceinline__ void dif_stage(float2 *buf, int nseq, const float2 *t
                 if constexpr (Lspan != R) {
                     const int js = j * tws;
 #pragma unroll
-                    for (int k = 1; k < R; k++) v[k] = cmul(v[k], tw[k * js]);
+                    for (int k = 1; k < R; k++) v[k] = cmul(v[k], __ldg(tw + k * js));
                 }
 #pragma unroll
                 for (int r = 0; r < R; r++) xb[(r * sub) + ((r * sub) >> 4)] = v[r];
@@ -155,18 +155,16 @@ __device__ __forceinline__ int dif_pos(int k2) {
 }  // namespace
 
 template <int N2>
-__global__ void __launch_bounds__(kP2Threads, 2) k_phase2(const Phase2Params p) {
+__global__ void __launch_bounds__(kP2Threads, 3) k_phase2(const Phase2Params p) {
     using S = P2Shape<N2>;
     constexpr int R2 = S::R2, LD = S::LD;
     extern __shared__ float2 sm[];
     float2 *buf = sm;                                  // [2 R2][LD]
-    float2 *tw = buf + 2 * R2 * LD;                    // [N2] exp(-2 pi i q / N2)
     constexpr int HP = S::HI + 1, LP = S::LO + 1;      // padded table rows (no bank conflicts)
-    float2 *thi = tw + N2;                             // [2 R2][HP]
+    float2 *thi = buf + 2 * R2 * LD;                   // [2 R2][HP]
     float2 *tlo = thi + 2 * R2 * HP;                   // [2 R2][LP]
     float2 *qup = tlo + 2 * R2 * LP;                   // [2 R2] upper-class factor
-    float2 *gsm = qup + 2 * R2;                        // [2][N2] gain of each slot's channel
-    long long *rowoff = reinterpret_cast<long long *>(gsm + 2 * N2);   // [R2] heap row byte offset
+    long long *rowoff = reinterpret_cast<long long *>(qup + 2 * R2);   // [R2] heap row byte offset
     int *rowstride = reinterpret_cast<int *>(rowoff + R2);             // [R2] bytes per channel row
 
     const int k1 = blockIdx.x, ant = blockIdx.z;
@@ -201,7 +199,6 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_phase2(const Phase2Params p) 
             }
         }
     }
-    for (int e = threadIdx.x; e < N2; e += kP2Threads) tw[e] = __ldg(p.tw2 + e);
     // rotation tables: angle/pi = phi/pi - 2 delta k / N, k = k1 + N1 (LO a + b)
     const float inv = 2.0f / (float)N;
     for (int e = threadIdx.x; e < 2 * R2 * (S::HI + S::LO + 1); e += kP2Threads) {
@@ -224,14 +221,6 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_phase2(const Phase2Params p) 
             qup[sq] = make_float2(cs, sn);
         }
     }
-    // gains of this CTA's channels: slot k2 holds channel k1 + N1 k2 (lower
-    // half) or N - (k1 + N1 k2) (upper half)
-    for (int e = threadIdx.x; e < 2 * N2; e += kP2Threads) {
-        const int pol = e / N2, k2 = e % N2;
-        const int kc = k1 + N1 * k2;
-        const int k = k2 >= N2 / 2 ? N - kc : kc;
-        gsm[e] = (k >= 0 && k < n) ? __ldg(p.gains + (long long)(ant * 2 + pol) * n + k) : make_float2(0.f, 0.f);
-    }
     if ((int)threadIdx.x < Rv) {
         const int q = q0 + threadIdx.x;
         const int h = q / S_, s = q - h * S_;
@@ -242,7 +231,7 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_phase2(const Phase2Params p) 
     __syncthreads();
 
     // in-place DIF FFT over the 2 Rv sequences
-    dif_all<N2, N2>(buf, 2 * R2, tw);
+    dif_all<N2, N2>(buf, 2 * R2, p.tw2);   // twiddles read through the L1 cache
 
     // epilogue: rotate, gain, quantise, corner turn
     const bool upper = (k1 != 0 && k1 != H1);
@@ -269,7 +258,7 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_phase2(const Phase2Params p) 
         const int pos = pad(dif_pos<N2>(k2));
         const float2 z0 = cmul(cmul(th0[a], tl0[b]), F0[pos]);
         const float2 z1 = cmul(cmul(th1[a], tl1[b]), F1[pos]);
-        const float2 g0 = gsm[k2], g1 = gsm[N2 + k2];
+        const float2 g0 = __ldg(p.gains + (long long)(ant * 2) * n + k), g1 = __ldg(p.gains + (long long)(ant * 2 + 1) * n + k);
         const float2 y0 = up ? cmul(cmul(g0, qu0), cconj(z0)) : cmul(g0, z0);
         const float2 y1 = up ? cmul(cmul(g1, qu1), cconj(z1)) : cmul(g1, z1);
         if (pre0) {
@@ -285,8 +274,8 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_phase2(const Phase2Params p) 
 size_t phase2_smem_bytes(int N2, int R2) {
     const int LD = N2 + N2 / 16 + 1;
     const int LO = N2 < 32 ? N2 : 32, HI = N2 / LO;
-    return sizeof(float2) * ((size_t)2 * R2 * LD + N2 + 2 * R2 * ((HI + 1) + (LO + 1) + 1)) +
-           sizeof(float2) * 2 * N2 + (sizeof(long long) + sizeof(int)) * R2;
+    return sizeof(float2) * ((size_t)2 * R2 * LD + 2 * R2 * ((HI + 1) + (LO + 1) + 1)) +
+           (sizeof(long long) + sizeof(int)) * R2;
 }
 
 template <int N2>
