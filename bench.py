@@ -40,21 +40,25 @@ UNIT = "Gsample/s"
 # capture (profiles/, 1 antenna x 2 pol x 2^24 samples/pol: one slab launch of
 # 2 x 256 spectra, the same 8.4 M input samples as one slab launch of the
 # 4-antenna workload). ncu flushes the caches before each replay, so these are
-# cold-cache figures. Keyed by kernel; valid only for the sources they were
-# taken from (src = hash of csrc/).
+# cold-cache figures. Valid only for the sources they were taken from (src =
+# hash of the kernel's source files).
+KERNEL_SOURCES = {
+    "k_phase1": ['k_phase1.cuh', 'k_phase1_t1.cu', 'k_phase1_t2.cu', 'k_phase1_t4.cu', 'k_phase1_t8.cu', 'k_phase1_t16.cu', 'k_phase1_t32.cu', 'fe_device.cuh', 'fe_internal.cuh'],
+    "k_phase2": ['k_phase2.cu', 'fe_device.cuh', 'fe_internal.cuh'],
+    "k_phase2_tc": ['k_phase2_tc.cu', 'fe_mma.cuh', 'fe_device.cuh', 'fe_internal.cuh'],
+}
 NCU_TRAFFIC = {
-    "k_phase1<16,16,32>": {"bytes_per_launch": 12265472 + 18176, "src": "e27c87cc862ccde6"},
-    "k_phase2<1024>": {"bytes_per_launch": 37925632 + 256, "src": "e27c87cc862ccde6"},
-    "k_phase2_tc<1>": {"bytes_per_launch": 37964032 + 15104, "src": "e27c87cc862ccde6"},
+    "k_phase1<16,16,32>": {"bytes_per_launch": 12265728 + 18176, "src": "c660b3bf3aa91e1f"},
+    "k_phase2<1024>": {"bytes_per_launch": 37927168 + 256, "src": "14ae78ff12ad7729"},
+    "k_phase2_tc<1>": {"bytes_per_launch": 37964032 + 15104, "src": "b609bd875dcffd25"},
 }
 
 
-def _src_hash() -> str:
+def _src_hash(kernel: str) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2303_09886_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -615,7 +619,7 @@ def main(argv=None):
     kname = {"phase1": f"k_phase1<{wl.n_taps},{N1},{min(512 // N1, N2)}>",
              "phase2": {"fp32": f"k_phase2<{N2}>", "fp16": "k_phase2_tc<1>", "bf16": "k_phase2_tc<2>"}[args.precision]}[dom]
     tr = NCU_TRAFFIC.get(kname)
-    traffic = tr["bytes_per_launch"] if tr and tr.get("src") == _src_hash() else None
+    traffic = tr["bytes_per_launch"] if tr and tr.get("src") == _src_hash(kname.split("<")[0]) else None
     step_ms = ms_max / args.steps
     path_alg = 2.25 * spl / (step_ms / 1e3) / 1e9
     path_all = (2.25 + 2 * inter) * spl / (step_ms / 1e3) / 1e9
