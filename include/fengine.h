@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define FENGINE_ABI_VERSION 1
+#define FENGINE_ABI_VERSION 2
 #define FENGINE_MAX_DELAY_SEGMENTS 16
 
 typedef enum {
@@ -53,6 +53,12 @@ typedef enum {
     FENGINE_EDELAY = 8        /* a coarse delay of this call leaves [0, max_delay] */
 } fengine_status;
 
+/* Precision forms. The reduced-precision forms run the N2 = 1024-point
+ * second DFT stage as two 32-point DFT contractions on tensor cores (FP32
+ * accumulation; BF16 operands split into hi + lo parts); they need a split
+ * with N2 = 1024, i.e. n_channels >= 4096 (FENGINE_EUNSUPPORTED otherwise).
+ * Pre-quantisation spectra stay within 2e-3 relative RMS of the FP64
+ * oracle (measured: FP16 3.7e-4, BF16 5.2e-6). */
 typedef enum {
     FENGINE_FP32 = 0,    /* FP32 FIR and FFT on CUDA cores */
     FENGINE_TC_FP16 = 1, /* reduced-precision form (FP16 operands, FP32 accumulation) */
@@ -72,6 +78,14 @@ typedef struct {
     int64_t max_delay_samples; /* D >= 0: every coarse delay must lie in [0, D] */
     const float *weights;      /* host, 2n*T prototype w[t + 2n j] (Eq. 1's w_{t,j});
                                   NULL = built-in Hann-windowed sinc, sum w^2 = 1 */
+    /* Tuning knobs (no counterpart in the paper; 0 = built-in choice, see
+     * fengine_autotune). They change how the work is split, not what is
+     * computed: results agree with the oracle within the same bars. */
+    int32_t fft_n1;            /* N1 of the four-step split N = N1 * N2: 8, 16, 32 or 64
+                                  with N2 <= 1024 (and N2 >= 512 / N1 for N1 > 8);
+                                  built-in: max(8, N / 1024) */
+    int32_t slab_spectra;      /* spectra per slab of the two-phase pipeline, a multiple
+                                  of 32; built-in: an FP32 intermediate of about 40 MiB */
 } fengine_config;
 
 typedef struct fengine_plan_s *fengine_plan_t;
@@ -165,6 +179,26 @@ fengine_status fengine_process_chunk(fengine_plan_t plan, void *cuda_stream,
                                      const uint8_t *d_packed, int64_t first_sample,
                                      int8_t *d_out, float *d_prequant,
                                      int32_t *d_window_tap, int64_t *first_spectrum);
+
+/* ---- autotuning (no counterpart in the paper) ----
+ *
+ * Times every valid work split of cfg -- fft_n1 in {8, 16, 32, 64} (only
+ * N / 1024 for the tensor-core forms) x slab_spectra in {built-in, 32, 64,
+ * 128, 256} -- by creating a plan for it and running `calls` calls (after
+ * two warm-up calls) on zero-filled input on cuda_stream, timed with CUDA
+ * events, and writes cfg with the fastest split into *tuned. The work does
+ * not depend on the sample values. Allocates (and frees) a temporary input
+ * and output on the current device and synchronises cuda_stream. entries
+ * (host, may be NULL) receives up to max_entries measured candidates,
+ * *n_entries (may be NULL) their number. */
+typedef struct {
+    int32_t fft_n1, slab_spectra;   /* the split (slab_spectra as the plan resolved it) */
+    float ms_per_call;              /* mean device time of one fengine_process_chunk */
+} fengine_tune_entry;
+
+fengine_status fengine_autotune(const fengine_config *cfg, void *cuda_stream, int32_t calls,
+                                fengine_config *tuned, fengine_tune_entry *entries, int32_t max_entries,
+                                int32_t *n_entries);
 
 /* ---- batching: many independent plans per call (uneven streams with
  * different channel counts, tap counts and chunk lengths; engines are

@@ -224,9 +224,20 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     if (S < 1 || S > M) return fail(FENGINE_EINVAL, "spectra_per_heap must be in [1, L/2n]");
     if (cfg->precision != FENGINE_FP32 && cfg->precision != FENGINE_TC_FP16 && cfg->precision != FENGINE_TC_BF16)
         return fail(FENGINE_EINVAL, "unknown precision");
-    if (cfg->precision != FENGINE_FP32 && n != 8192)
+    // four-step split: N1 from the config or the built-in max(8, N / 1024);
+    // the phase-1 tiles exist for N1 = 8 (W = min(64, N2)) and N1 = 16, 32,
+    // 64 (W = 512 / N1 <= N2), the phase-2 kernels for N2 <= 1024
+    const int N1 = cfg->fft_n1 ? cfg->fft_n1 : (int)(N / 1024 > 8 ? N / 1024 : 8);
+    if (!(N1 == 8 || N1 == 16 || N1 == 32 || N1 == 64) || N % N1 || N / N1 > 1024 || N / N1 < 4 ||
+        (N1 > 8 && N / N1 < 512 / N1))
+        return fail(FENGINE_EINVAL, "fft_n1 must be 8, 16, 32 or 64 with N / fft_n1 <= 1024 (and >= 512 / fft_n1 "
+                                    "for fft_n1 > 8)");
+    if (cfg->slab_spectra < 0 || cfg->slab_spectra % 32)
+        return fail(FENGINE_EINVAL, "slab_spectra must be 0 or a positive multiple of 32");
+    if (cfg->precision != FENGINE_FP32 && N / N1 != 1024)
         return fail(FENGINE_EUNSUPPORTED,
-                    "the tensor-core forms are implemented for 8192 channels (1024-point second stage) only");
+                    "the tensor-core forms need a 1024-point second stage (n_channels >= 4096, "
+                    "fft_n1 = 2 n_channels / 1024)");
 
     fengine_plan_s *pl = new (std::nothrow) fengine_plan_s();
     if (!pl) return fail(FENGINE_ENOMEM, "host allocation");
@@ -241,7 +252,7 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     pl->L = cfg->chunk_samples;
     pl->D = cfg->max_delay_samples;
     pl->precision = cfg->precision;
-    pl->N1 = (int)(N / 1024 > 8 ? N / 1024 : 8);
+    pl->N1 = N1;
     pl->N2 = (int)(N / pl->N1);
     pl->W = fe::phase1_W(pl->N1, pl->N2);
     pl->C = pl->N1 * pl->W;
@@ -259,7 +270,7 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     // next to the streaming input and output. A multiple of 32 spectra (both
     // phases' tiles).
     const size_t per_spec = (size_t)ns * (pl->N1 / 2 + 1) * pl->N2 * sizeof(float2);
-    long long SL = (long long)((40u << 20) / per_spec) / 32 * 32;
+    long long SL = cfg->slab_spectra ? cfg->slab_spectra : (long long)((40u << 20) / per_spec) / 32 * 32;
     if (SL < 32) SL = 32;
     const long long M32 = (M + 31) / 32 * 32;
     if (SL > M32) SL = M32;

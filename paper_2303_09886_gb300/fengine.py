@@ -29,7 +29,7 @@ EXPORTS = ("fengine_strerror", "fengine_last_error", "fengine_abi_version", "fen
            "fengine_batch_create", "fengine_batch_destroy", "fengine_batch_process",
            "fengine_service_create", "fengine_service_submit", "fengine_service_set_delay",
            "fengine_service_set_gains", "fengine_service_wait", "fengine_service_get_stats",
-           "fengine_service_destroy", "fengine_process_chunk_noalloc")
+           "fengine_service_destroy", "fengine_process_chunk_noalloc", "fengine_autotune")
 
 
 class FEngineError(RuntimeError):
@@ -43,7 +43,12 @@ class Config(ctypes.Structure):
                 ("n_channels", ctypes.c_int32), ("n_taps", ctypes.c_int32),
                 ("chunk_samples", ctypes.c_int64), ("spectra_per_heap", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_delay_samples", ctypes.c_int64),
-                ("weights", ctypes.POINTER(ctypes.c_float))]
+                ("weights", ctypes.POINTER(ctypes.c_float)),
+                ("fft_n1", ctypes.c_int32), ("slab_spectra", ctypes.c_int32)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("fft_n1", ctypes.c_int32), ("slab_spectra", ctypes.c_int32), ("ms_per_call", ctypes.c_float)]
 
 
 class Info(ctypes.Structure):
@@ -96,7 +101,9 @@ def load(path: str = LIB_PATH):
     lib.fengine_batch_create.argtypes = [i32, ctypes.POINTER(vp)]
     lib.fengine_batch_destroy.argtypes = [vp]
     lib.fengine_batch_process.argtypes = [vp, vp, ctypes.POINTER(ChunkDesc), i32, ctypes.POINTER(i64)]
-    for name in ("fengine_default_weights", "fengine_plan_create", "fengine_plan_destroy",
+    lib.fengine_autotune.argtypes = [ctypes.POINTER(Config), vp, i32, ctypes.POINTER(Config),
+                                     ctypes.POINTER(TuneEntry), i32, ctypes.POINTER(i32)]
+    for name in ("fengine_autotune", "fengine_default_weights", "fengine_plan_create", "fengine_plan_destroy",
                  "fengine_get_info", "fengine_set_delay", "fengine_set_gains", "fengine_reset",
                  "fengine_process_chunk", "fengine_set_profiling", "fengine_stage_times",
                  "fengine_batch_create", "fengine_batch_destroy", "fengine_batch_process"):
@@ -139,7 +146,7 @@ class Plan:
 
     def __init__(self, n_antennas: int, n_channels: int, n_taps: int, chunk_samples: int,
                  spectra_per_heap: int = 0, max_delay_samples: int = 0, weights=None,
-                 precision: int = FP32):
+                 precision: int = FP32, fft_n1: int = 0, slab_spectra: int = 0):
         lib = load()
         self._w = None
         if weights is not None:
@@ -148,7 +155,8 @@ class Plan:
                 raise ValueError("weights must have 2 * n_channels * n_taps entries")
         cfg = Config(n_antennas, 2, n_channels, n_taps, chunk_samples, spectra_per_heap, precision,
                      max_delay_samples,
-                     self._w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if self._w is not None else None)
+                     self._w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if self._w is not None else None,
+                     fft_n1, slab_spectra)
         h = ctypes.c_void_p()
         _check(lib.fengine_plan_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -216,6 +224,23 @@ class Plan:
                                             first_sample, _ptr(out), _ptr(prequant), _ptr(window_tap),
                                             ctypes.byref(fs)))
         return fs.value
+
+
+def autotune(n_antennas: int, n_channels: int, n_taps: int, chunk_samples: int, spectra_per_heap: int = 0,
+             max_delay_samples: int = 0, precision: int = FP32, calls: int = 5, stream=None):
+    """fengine_autotune: time every valid work split and return
+    ({"fft_n1": .., "slab_spectra": ..} of the fastest, [(fft_n1, slab_spectra, ms_per_call), ...])."""
+    import torch
+    cfg = Config(n_antennas, 2, n_channels, n_taps, chunk_samples, spectra_per_heap, precision,
+                 max_delay_samples, None, 0, 0)
+    tuned = Config()
+    entries = (TuneEntry * 32)()
+    n = ctypes.c_int32()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(load().fengine_autotune(ctypes.byref(cfg), ctypes.c_void_p(s.cuda_stream), calls, ctypes.byref(tuned),
+                                   entries, 32, ctypes.byref(n)))
+    table = [(entries[i].fft_n1, entries[i].slab_spectra, float(entries[i].ms_per_call)) for i in range(n.value)]
+    return {"fft_n1": tuned.fft_n1, "slab_spectra": tuned.slab_spectra}, table
 
 
 class Batch:

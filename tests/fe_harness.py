@@ -40,14 +40,14 @@ def streams(seed, n_ant, total, sigma, tones=(), chirp=None):
 
 
 def run_gpu(samples, n_ch, T, L, n_chunks, delays, gains, S=0, D=0, weights=None, start=0,
-            taps=True, prequant=True, precision=fengine.FP32):
+            taps=True, prequant=True, precision=fengine.FP32, fft_n1=0, slab_spectra=0):
     """Process consecutive chunks of `samples` (starting at absolute `start`).
     delays[a][p]: list of Seg; gains[a][p]: complex array or None.
     Returns list of dicts per call (numpy copies of every output)."""
     import torch
     n_ant = samples.shape[0]
     plan = fengine.Plan(n_ant, n_ch, T, L, spectra_per_heap=S, max_delay_samples=D, weights=weights,
-                        precision=precision)
+                        precision=precision, fft_n1=fft_n1, slab_spectra=slab_spectra)
     for a in range(n_ant):
         for p in range(2):
             for sg in delays[a][p]:

@@ -35,7 +35,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_strerror(lib):
-    assert lib.fengine_abi_version() == 1
+    assert lib.fengine_abi_version() == 2
     for st in range(9):
         assert lib.fengine_strerror(st)
     assert b"unknown" in lib.fengine_strerror(99)
@@ -72,10 +72,13 @@ def test_quantiser_matches_oracle_on_every_tie_and_neighbour(lib):
 @pytest.mark.parametrize("kw,status", [
     (dict(n_pols=3), 1), (dict(n_channels=1000), 1), (dict(n_taps=3), 1),
     (dict(chunk_samples=1000), 1), (dict(spectra_per_heap=10 ** 6), 1),
-    (dict(max_delay_samples=-1), 1), (dict(n_antennas=0), 1)])
+    (dict(max_delay_samples=-1), 1), (dict(n_antennas=0), 1),
+    (dict(fft_n1=12), 1), (dict(fft_n1=128), 1), (dict(fft_n1=2), 1), (dict(slab_spectra=33), 1),
+    (dict(slab_spectra=-32), 1), (dict(precision=1), 7), (dict(precision=2, n_channels=2048), 7),
+    (dict(precision=1, n_channels=8192, fft_n1=32, chunk_samples=16384 * 4), 7)])
 def test_plan_config_validation_before_any_device_call(lib, kw, status):
     cfg = dict(n_antennas=1, n_pols=2, n_channels=1024, n_taps=16, chunk_samples=2048 * 8,
-               spectra_per_heap=0, precision=0, max_delay_samples=0, weights=None)
+               spectra_per_heap=0, precision=0, max_delay_samples=0, weights=None, fft_n1=0, slab_spectra=0)
     cfg.update(kw)
     c = fengine.Config(**cfg)
     h = ctypes.c_void_p()
@@ -91,3 +94,13 @@ def test_binding_refuses_without_library(tmp_path):
             fengine.load(str(tmp_path / "missing.so"))
         finally:
             fengine._lib = saved
+
+
+def test_autotune_rejects_bad_arguments_before_any_device_call(lib):
+    c = fengine.Config(n_antennas=1, n_pols=2, n_channels=1024, n_taps=16, chunk_samples=2048 * 8,
+                       spectra_per_heap=0, precision=0, max_delay_samples=0, weights=None, fft_n1=0,
+                       slab_spectra=0)
+    tuned = fengine.Config()
+    n = ctypes.c_int32(-1)
+    assert lib.fengine_autotune(ctypes.byref(c), None, 0, ctypes.byref(tuned), None, 0, ctypes.byref(n)) == 1
+    assert lib.fengine_autotune(None, None, 3, ctypes.byref(tuned), None, 0, ctypes.byref(n)) == 1
