@@ -47,10 +47,10 @@ KERNEL_SOURCES = {
     "k_phase2": ['k_phase2.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase2_tc": ['k_phase2_tc.cu', 'fe_mma.cuh', 'fe_device.cuh', 'fe_internal.cuh'],
 }
-NCU_TRAFFIC = {
-    "k_phase1<16,16,32>": {"bytes_per_launch": 12265728 + 18176, "src": "c660b3bf3aa91e1f"},
-    "k_phase2<1024>": {"bytes_per_launch": 37927168 + 256, "src": "14ae78ff12ad7729"},
-    "k_phase2_tc<1>": {"bytes_per_launch": 37964032 + 15104, "src": "b609bd875dcffd25"},
+NCU_TRAFFIC = {   # DRAM bytes per input sample of the launch (captured launch: 8388608 samples)
+    "k_phase1<16,16,32>": {"bytes_per_sample": (12265728 + 18176) / 8388608, "src": "c660b3bf3aa91e1f"},
+    "k_phase2<1024>": {"bytes_per_sample": (37927168 + 256) / 8388608, "src": "14ae78ff12ad7729"},
+    "k_phase2_tc<1>": {"bytes_per_sample": (37964032 + 15104) / 8388608, "src": "b609bd875dcffd25"},
 }
 
 
@@ -390,11 +390,24 @@ def run_service(args):
     return 0
 
 
+def _tuned_split(fengine, wl, prec, args):
+    """The work split of the plan: the autotuner's pick (fengine_autotune) unless --no-autotune."""
+    if args.no_autotune:
+        return {"fft_n1": 0, "slab_spectra": 0, "autotuned": False}
+    best, table = fengine.autotune(wl.n_antennas, wl.n_channels, wl.n_taps, wl.chunk_samples,
+                                   spectra_per_heap=wl.spectra_per_heap, max_delay_samples=wl.max_delay,
+                                   precision=prec, calls=3)
+    return {**best, "autotuned": True,
+            "candidates_ms_per_call": {f"n1={a},slab={b}": round(ms, 4) for a, b, ms in table}}
+
+
 def _time_form(fengine, torch, wl, name, d_in, args):
     """Device time of `args.steps` calls of one precision form on the resident input."""
     prec = {"fp32": fengine.FP32, "fp16": fengine.TC_FP16, "bf16": fengine.TC_BF16}[name]
+    split = _tuned_split(fengine, wl, prec, args)
     plan = fengine.Plan(wl.n_antennas, wl.n_channels, wl.n_taps, wl.chunk_samples,
-                        spectra_per_heap=wl.spectra_per_heap, max_delay_samples=wl.max_delay, precision=prec)
+                        spectra_per_heap=wl.spectra_per_heap, max_delay_samples=wl.max_delay, precision=prec,
+                        fft_n1=split["fft_n1"], slab_spectra=split["slab_spectra"])
     for a, p, d, r, ph, pr in wl.delays():
         plan.set_delay(a, p, d, r, ph, pr)
     g = wl.gains()
@@ -420,9 +433,11 @@ def _time_form(fengine, torch, wl, name, d_in, args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     stage_ms, calls = plan.stage_times()
+    plan_n1, plan_sl = plan.info.fft_n1, plan.info.slab_spectra
     plan.close()
     return {"value": wl.samples_per_step * args.steps / (ms / 1e3) / 1e9, "ms_per_step": ms / args.steps,
-            "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()}}
+            "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()},
+            "split": {"fft_n1": int(plan_n1), "slab_spectra": int(plan_sl), "autotuned": split["autotuned"]}}
 
 
 def main(argv=None):
@@ -441,6 +456,7 @@ def main(argv=None):
     ap.add_argument("--chunks", type=int, default=8, help="workload 5: chunks per antenna")
     ap.add_argument("--load", type=float, default=1.5, help="workload 5: offered load / sustained rate")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision forms")
+    ap.add_argument("--no-autotune", action="store_true", help="use the built-in work split instead of the autotuner's")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="fp32 plain form, or the tensor-core forms (FP16/BF16 operands, FP32 accumulation)")
     args = ap.parse_args(argv)
@@ -475,9 +491,10 @@ def main(argv=None):
     fengine.load()
 
     prec = {"fp32": fengine.FP32, "fp16": fengine.TC_FP16, "bf16": fengine.TC_BF16}[args.precision]
+    split = _tuned_split(fengine, wl, prec, args)
     plan = fengine.Plan(wl.n_antennas, wl.n_channels, wl.n_taps, wl.chunk_samples,
                         spectra_per_heap=wl.spectra_per_heap, max_delay_samples=wl.max_delay,
-                        precision=prec)
+                        precision=prec, fft_n1=split["fft_n1"], slab_spectra=split["slab_spectra"])
     for a, p, d, r, ph, pr in wl.delays():
         plan.set_delay(a, p, d, r, ph, pr)
     g = wl.gains()
@@ -619,7 +636,10 @@ def main(argv=None):
     kname = {"phase1": f"k_phase1<{wl.n_taps},{N1},{min(512 // N1, N2)}>",
              "phase2": {"fp32": f"k_phase2<{N2}>", "fp16": "k_phase2_tc<1>", "bf16": "k_phase2_tc<2>"}[args.precision]}[dom]
     tr = NCU_TRAFFIC.get(kname)
-    traffic = tr["bytes_per_launch"] if tr and tr.get("src") == _src_hash(kname.split("<")[0]) else None
+    # scaled from the captured launch to this launch by its input samples
+    # (the kernels' DRAM traffic grows in proportion to the samples processed)
+    traffic = (tr["bytes_per_sample"] * spl / slabs if tr and tr.get("src") == _src_hash(kname.split("<")[0])
+               else None)
     step_ms = ms_max / args.steps
     path_alg = 2.25 * spl / (step_ms / 1e3) / 1e9
     path_all = (2.25 + 2 * inter) * spl / (step_ms / 1e3) / 1e9
@@ -631,6 +651,7 @@ def main(argv=None):
         "config": {"workload": wl.description, "name": wl.name, "n_antennas": wl.n_antennas,
                    "n_channels": wl.n_channels, "n_taps": wl.n_taps, "chunk_samples": wl.chunk_samples,
                    "precision": args.precision, "parallelism": f"replicas x{ws}",
+                   "split": {**split, "fft_n1": int(plan.info.fft_n1), "slab_spectra": int(plan.info.slab_spectra)},
                    "l2": f"inputs larger than L2: {h_in.numel() >> 20} MiB packed in + "
                          f"{plan.info.out_bytes >> 20} MiB out per step"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,

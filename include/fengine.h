@@ -184,7 +184,8 @@ fengine_status fengine_process_chunk(fengine_plan_t plan, void *cuda_stream,
  *
  * Times every valid work split of cfg -- fft_n1 in {8, 16, 32, 64} (only
  * N / 1024 for the tensor-core forms) x slab_spectra in {built-in, 32, 64,
- * 128, 256} -- by creating a plan for it and running `calls` calls (after
+ * ..., 2048} (capped at the call's spectra) -- by creating a plan for it and
+ * running `calls` calls (after
  * two warm-up calls) on zero-filled input on cuda_stream, timed with CUDA
  * events, and writes cfg with the fastest split into *tuned. The work does
  * not depend on the sample values. Allocates (and frees) a temporary input

@@ -265,12 +265,13 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
 
     const int ns = pl->n_streams;
     cudaError_t e = cudaSuccess;
-    // Slab of spectra whose FP32 intermediate (all streams) is about 40 MiB:
-    // the slab being written and the one being read fit in the 126 MiB L2
-    // next to the streaming input and output. A multiple of 32 spectra (both
-    // phases' tiles).
+    // Slab of spectra per phase-1 / phase-2 launch pair: built-in, the
+    // spectra whose FP32 intermediate (all streams) is about 256 MiB, a
+    // multiple of 32 (both phases' tiles). Measured on GB300 (fengine_autotune),
+    // launches over more spectra win over keeping a smaller intermediate in
+    // L2: the grids then span several waves of CTAs.
     const size_t per_spec = (size_t)ns * (pl->N1 / 2 + 1) * pl->N2 * sizeof(float2);
-    long long SL = cfg->slab_spectra ? cfg->slab_spectra : (long long)((40u << 20) / per_spec) / 32 * 32;
+    long long SL = cfg->slab_spectra ? cfg->slab_spectra : (long long)((256u << 20) / per_spec) / 32 * 32;
     if (SL < 32) SL = 32;
     const long long M32 = (M + 31) / 32 * 32;
     if (SL > M32) SL = M32;

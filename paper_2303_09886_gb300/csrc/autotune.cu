@@ -1,7 +1,7 @@
 // fengine_autotune: picks the work split of a plan by measurement. The split
 // -- N1 of the four-step DFT (which fixes the phase-1 tile width and the
-// phase-2 FFT length) and the slab of spectra the two-phase pipeline hands
-// over through L2 -- changes how the work is divided, not what is computed,
+// phase-2 FFT length) and the slab of spectra per phase-1 / phase-2 launch
+// pair -- changes how the work is divided, not what is computed,
 // so the fastest split can be chosen by timing each candidate on zero-filled
 // input through the public entry points.
 #include <cuda_runtime.h>
@@ -46,7 +46,7 @@ extern "C" fengine_status fengine_autotune(const fengine_config *cfg, void *cuda
     }
 
     const int n1s[4] = {8, 16, 32, 64};
-    const int sls[5] = {0, 32, 64, 128, 256};
+    const int sls[8] = {0, 32, 64, 128, 256, 512, 1024, 2048};
     float best = -1.0f;
     fengine_config best_cfg = *cfg;
     std::vector<int> seen;   // (n1, resolved slab) pairs already timed
