@@ -46,6 +46,7 @@ struct fengine_plan_s {
     int device = 0;
     int n_ant = 0, n_streams = 0, n = 0, N = 0, T = 0, S = 0, M = 0, N1 = 0, N2 = 0, W = 0, C = 0, R2 = 0;
     int precision = 0;
+    int a_elem = 8;                 // bytes per intermediate element
     long long L = 0, D = 0, H = 0, chunk_bytes = 0, hist_bytes = 0;
     // device state
     float *d_w = nullptr;
@@ -270,7 +271,9 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     // multiple of 32 (both phases' tiles). Measured on GB300 (fengine_autotune),
     // launches over more spectra win over keeping a smaller intermediate in
     // L2: the grids then span several waves of CTAs.
-    const size_t per_spec = (size_t)ns * (pl->N1 / 2 + 1) * pl->N2 * sizeof(float2);
+    // intermediate element: FP32 (re, im), or FP16 (re, im) in the FP16 form
+    pl->a_elem = pl->precision == FENGINE_TC_FP16 ? 4 : 8;
+    const size_t per_spec = (size_t)ns * (pl->N1 / 2 + 1) * pl->N2 * pl->a_elem;
     long long SL = cfg->slab_spectra ? cfg->slab_spectra : (long long)((256u << 20) / per_spec) / 32 * 32;
     if (SL < 32) SL = 32;
     const long long M32 = (M + 31) / 32 * 32;
@@ -555,6 +558,7 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     p1.ctab = pl->d_ctab;
     p1.window_tap = d_window_tap;
     p1.a_spectra = pl->SL;
+    p1.half_out = pl->precision == FENGINE_TC_FP16;
 
     fe::Phase2Params p2{};
     p2.tw2 = pl->d_tw2;
@@ -583,7 +587,7 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
         return cuda_fail(e, "slab fork");
     for (int s = 0; s < pl->n_slabs; s++) {
         const int b = s & 1;
-        float2 *A = pl->d_A + (size_t)b * slab_elems;
+        float2 *A = reinterpret_cast<float2 *>(reinterpret_cast<char *>(pl->d_A) + (size_t)b * slab_elems * pl->a_elem);
         const int qb = s * pl->SL;
         const int qc = (pl->M - qb) < pl->SL ? (pl->M - qb) : pl->SL;
         if (s >= 2 && (e = cudaStreamWaitEvent(pl->sp[0], pl->ev_p2[b], 0)) != cudaSuccess)

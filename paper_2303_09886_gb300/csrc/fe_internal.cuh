@@ -54,6 +54,8 @@ struct Phase1Params {
     const float2 *tw1;        // [(N1/2+1)][N2] exp(-2 pi i k1 t2 / N)
     const int *ctab;          // [stream][M]
     float2 *A;                // out [stream][a_spectra][N1/2+1][N2], spectrum q at row q - q_begin
+                              // (FP16 pairs in 4-byte elements when half_out)
+    int half_out;             // 1: store B as FP16 (re, im) pairs (FP16 tensor-core form)
     int *window_tap;          // optional out [stream][M][N]
     int q_begin, q_count;     // the slab of spectra this launch covers
     int a_spectra;            // spectra per stream in the intermediate buffer
@@ -61,6 +63,7 @@ struct Phase1Params {
 
 struct Phase2Params {
     const float2 *A;          // [stream][a_spectra][N1/2+1][N2], spectrum q at row q - q_begin
+                              // (FP16 pairs in 4-byte elements for the FP16 tensor-core form)
     int q_begin, q_count;     // the slab of spectra this launch covers
     int a_spectra;            // spectra per stream in the intermediate buffer
     const float2 *tw2;        // [N2] exp(-2 pi i q / N2)

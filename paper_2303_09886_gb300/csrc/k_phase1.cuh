@@ -25,6 +25,8 @@
 // t1 in registers, multiplies by the twiddle and stores B to the
 // intermediate.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "fe_device.cuh"
 #include "fe_internal.cuh"
 
@@ -158,7 +160,7 @@ __device__ __forceinline__ void p1_decode(const P1Pending<S> &pd, const P1Stream
     }
 }
 
-template <int T, int N1, int W>
+template <int T, int N1, int W, bool HALF>
 __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) {
     using S = P1Shape<T, N1, W>;
     constexpr int R = S::R, H1 = N1 / 2;
@@ -290,30 +292,52 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
         for (int t1 = 0; t1 < N1; t1++) x[t1] = g[t1 * S::SW];
         float2 X[H1 + 1];
         rdft_reg<N1>(x, X);
-        float2 *out = p.A + ((long long)stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) * N2 + t2_0 + w;
+        const long long o = ((long long)stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) * N2 + t2_0 + w;
         const float2 t0 = tw1_sm[w];   // exp(0), times the plan's scale
-        out[0] = make_float2(X[0].x * t0.x, X[0].x * t0.y);
-#pragma unroll
-        for (int k = 1; k < H1; k++) out[(long long)k * N2] = cmul(X[k], tw1_sm[k * W + w]);
         const float2 th = tw1_sm[H1 * W + w];
-        out[(long long)H1 * N2] = make_float2(X[H1].x * th.x, X[H1].x * th.y);
+        float2 b[H1 + 1];
+        b[0] = make_float2(X[0].x * t0.x, X[0].x * t0.y);
+#pragma unroll
+        for (int k = 1; k < H1; k++) b[k] = cmul(X[k], tw1_sm[k * W + w]);
+        b[H1] = make_float2(X[H1].x * th.x, X[H1].x * th.y);
+        if constexpr (HALF) {
+            // FP16 (re, im) pairs: the rounding the FP16 second stage applies to its operands anyway
+            __half2 *out = reinterpret_cast<__half2 *>(p.A) + o;
+#pragma unroll
+            for (int k = 0; k <= H1; k++) out[(long long)k * N2] = __floats2half2_rn(b[k].x, b[k].y);
+        } else {
+            float2 *out = p.A + o;
+#pragma unroll
+            for (int k = 0; k <= H1; k++) out[(long long)k * N2] = b[k];
+        }
     }
 }
 
-template <int T, int N1, int W>
+template <int T, int N1, int W, bool HALF = false>
 cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t s) {
     using S = P1Shape<T, N1, W>;
     if (p.W != W || p.N2 % W) return cudaErrorInvalidValue;
     const size_t smem = (size_t)S::ROWS * S::ROW * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_phase1<T, N1, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_phase1<T, N1, W, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(p.N2 / W, (p.q_count + kP1Rows - 1) / kP1Rows, n_streams);
-    k_phase1<T, N1, W><<<grid, kP1Threads, smem, s>>>(p);
+    k_phase1<T, N1, W, HALF><<<grid, kP1Threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <int T>
 cudaError_t launch_phase1_n1(int N1, const Phase1Params &p, int n_streams, cudaStream_t s) {
+    if (p.half_out) {
+        // FP16 intermediate: the splits with a 1024-point second stage
+        switch (N1 * 1000 + p.W) {
+            case 8064: return launch_phase1_tw<T, 8, 64, true>(p, n_streams, s);
+            case 16032: return launch_phase1_tw<T, 16, 32, true>(p, n_streams, s);
+            case 32016: return launch_phase1_tw<T, 32, 16, true>(p, n_streams, s);
+            case 64008: return launch_phase1_tw<T, 64, 8, true>(p, n_streams, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (N1 * 1000 + p.W) {
         case 8064: return launch_phase1_tw<T, 8, 64>(p, n_streams, s);
         case 16032: return launch_phase1_tw<T, 16, 32>(p, n_streams, s);

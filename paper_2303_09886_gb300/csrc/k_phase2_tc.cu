@@ -135,11 +135,9 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
     if (r < Rv) {
         for (int pol = 0; pol < 2; pol++) {
             const int stream = ant * 2 + pol;
-            const float2 *src =
-                p.A + ((long long)(stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) + k1) * kTcN2;
-            // contraction 1, one K tile at a time; operand B of tile kt is
-            // B[32 a + b] at a = 8 kt + 2 tq + h, b = 8 nt + g (the next
-            // tile's loads are in flight during this tile's products)
+            const long long base = ((long long)(stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) + k1) * kTcN2;
+            // contraction 1; operand B of K tile kt is B[32 a + b] at
+            // a = 8 kt + 2 tq + h, b = 8 nt + g
             float d1[4][4][4];
 #pragma unroll
             for (int mt = 0; mt < 4; mt++)
@@ -147,40 +145,66 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
                 for (int nt = 0; nt < 4; nt++)
 #pragma unroll
                     for (int x = 0; x < 4; x++) d1[mt][nt][x] = 0.0f;
-            float2 v[4][2];
+            if constexpr (PREC == 1) {
+                // FP16 intermediate: B arrives as the (re, im) FP16 pairs the
+                // products take; all 32 of the lane's operands are loaded at once
+                const unsigned *srch = reinterpret_cast<const unsigned *>(p.A) + base;
+                unsigned vh[4][4][2];
 #pragma unroll
-            for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                for (int h = 0; h < 2; h++) v[nt][h] = __ldg(src + 32 * (2 * tq + h) + 8 * nt + g);
-#pragma unroll
-            for (int kt = 0; kt < 4; kt++) {
-                unsigned bh[4][2], bl[4][2];
-#pragma unroll
-                for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const float2 x = v[nt][h];
-                        bh[nt][h] = pack2<PREC>(x.x, x.y);
-                        if constexpr (LO) bl[nt][h] = pack2<PREC>(x.x - bf16_round(x.x), x.y - bf16_round(x.y));
-                    }
-                if (kt < 3) {
+                for (int kt = 0; kt < 4; kt++)
 #pragma unroll
                     for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-                        for (int h = 0; h < 2; h++)
-                            v[nt][h] = __ldg(src + 32 * (8 * (kt + 1) + 2 * tq + h) + 8 * nt + g);
+                        for (int h = 0; h < 2; h++) vh[kt][nt][h] = __ldg(srch + 32 * (8 * kt + 2 * tq + h) + 8 * nt + g);
+#pragma unroll
+                for (int kt = 0; kt < 4; kt++) {
+#pragma unroll
+                    for (int mt = 0; mt < 4; mt++) {
+                        const uint4 A = a1s[(mt * 4 + kt) * 32 + lane];
+#pragma unroll
+                        for (int nt = 0; nt < 4; nt++) mma16816<PREC>(d1[mt][nt], A, vh[kt][nt][0], vh[kt][nt][1]);
+                    }
                 }
+            } else {
+                // FP32 intermediate (BF16 form: split into hi and lo here), one
+                // K tile at a time, the next tile's loads in flight during
+                // this tile's products
+                const float2 *src = p.A + base;
+                float2 v[4][2];
 #pragma unroll
-                for (int mt = 0; mt < 4; mt++) {
-                    const uint4 A = a1s[(mt * 4 + kt) * 32 + lane];
+                for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-                    for (int nt = 0; nt < 4; nt++) mma16816<PREC>(d1[mt][nt], A, bh[nt][0], bh[nt][1]);
-                    if constexpr (LO) {
-                        const uint4 Al = a1l[(mt * 4 + kt) * 32 + lane];
+                    for (int h = 0; h < 2; h++) v[nt][h] = __ldg(src + 32 * (2 * tq + h) + 8 * nt + g);
 #pragma unroll
-                        for (int nt = 0; nt < 4; nt++) {
-                            mma16816<PREC>(d1[mt][nt], A, bl[nt][0], bl[nt][1]);
-                            mma16816<PREC>(d1[mt][nt], Al, bh[nt][0], bh[nt][1]);
+                for (int kt = 0; kt < 4; kt++) {
+                    unsigned bh[4][2], bl[4][2];
+#pragma unroll
+                    for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            const float2 x = v[nt][h];
+                            bh[nt][h] = pack2<PREC>(x.x, x.y);
+                            if constexpr (LO) bl[nt][h] = pack2<PREC>(x.x - bf16_round(x.x), x.y - bf16_round(x.y));
+                        }
+                    if (kt < 3) {
+#pragma unroll
+                        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                            for (int h = 0; h < 2; h++)
+                                v[nt][h] = __ldg(src + 32 * (8 * (kt + 1) + 2 * tq + h) + 8 * nt + g);
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < 4; mt++) {
+                        const uint4 A = a1s[(mt * 4 + kt) * 32 + lane];
+#pragma unroll
+                        for (int nt = 0; nt < 4; nt++) mma16816<PREC>(d1[mt][nt], A, bh[nt][0], bh[nt][1]);
+                        if constexpr (LO) {
+                            const uint4 Al = a1l[(mt * 4 + kt) * 32 + lane];
+#pragma unroll
+                            for (int nt = 0; nt < 4; nt++) {
+                                mma16816<PREC>(d1[mt][nt], A, bl[nt][0], bl[nt][1]);
+                                mma16816<PREC>(d1[mt][nt], Al, bh[nt][0], bh[nt][1]);
+                            }
                         }
                     }
                 }
