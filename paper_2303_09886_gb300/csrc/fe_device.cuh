@@ -45,10 +45,9 @@ __host__ __device__ constexpr int bitrev(int i) {
     return r;
 }
 
-// exp(-2 pi i q / 64) for q in [0, 32] as compile-time constants (cos and
-// sin of multiples of pi/32, evaluated in FP64 and rounded to FP32; the
-// exact values 0, +-1 are written exactly so multiplications by them fold).
-__host__ __device__ __forceinline__ float2 tw64c(int q) {
+// cos(2 pi q / 64) for q in [0, 32] (FP64 values rounded to FP32; the exact
+// values 0 and +-1 are written exactly so that multiplications by them fold).
+__host__ __device__ constexpr float cos64(int q) {
     constexpr float c[33] = {
         1.0f, 9.951847196e-01f, 9.807852507e-01f, 9.569403529e-01f, 9.238795042e-01f,
         8.819212914e-01f, 8.314695954e-01f, 7.730104327e-01f, 7.071067691e-01f, 6.343932748e-01f,
@@ -57,25 +56,59 @@ __host__ __device__ __forceinline__ float2 tw64c(int q) {
         -3.826834261e-01f, -4.713967443e-01f, -5.555702448e-01f, -6.343932748e-01f, -7.071067691e-01f,
         -7.730104327e-01f, -8.314695954e-01f, -8.819212914e-01f, -9.238795042e-01f, -9.569403529e-01f,
         -9.807852507e-01f, -9.951847196e-01f, -1.0f};
-    // sin(-2 pi q / 64) = -cos(2 pi (16 - q) / 64) = -c[|16 - q|] for q in [0, 32]
-    const int m = q <= 16 ? 16 - q : q - 16;
-    return make_float2(c[q], -c[m]);
+    return c[q];
 }
 
-// Multiply by a compile-time twiddle exp(-2 pi i q / 64), folding q = 0
-// (identity) and q = 16 (-i).
-__device__ __forceinline__ float2 cmul_tw64c(float2 a, int q) {
-    if (q == 0) return a;
-    if (q == 16) return make_float2(a.y, -a.x);
-    return cmul(a, tw64c(q));
+// a * exp(-2 pi i Q / 64) for a compile-time Q in [0, 32]: Q = 0 and
+// Q = 16 (-i) fold to moves; otherwise cos - i sin with sin(2 pi Q / 64) =
+// cos(2 pi |16 - Q| / 64).
+template <int Q>
+__device__ __forceinline__ float2 cmul_w64(float2 a) {
+    static_assert(Q >= 0 && Q <= 32, "twiddle index");
+    if constexpr (Q == 0) {
+        return a;
+    } else if constexpr (Q == 16) {
+        return make_float2(a.y, -a.x);
+    } else {
+        constexpr float c = cos64(Q), s = cos64(Q <= 16 ? 16 - Q : Q - 16);
+        return cmul(a, make_float2(c, -s));
+    }
 }
+
+namespace detail {
+
+// X[K] = E[K] + w^K O[K], X[K + NN/2] = E[K] - w^K O[K] for K = K0 .. NN/2 - 1
+template <int NN, int K>
+__device__ __forceinline__ void dit_combine(float2 (&z)[NN], const float2 (&e)[NN / 2], const float2 (&o)[NN / 2]) {
+    if constexpr (K < NN / 2) {
+        const float2 t = cmul_w64<K * (64 / NN)>(o[K]);
+        z[K] = cadd(e[K], t);
+        z[K + NN / 2] = csub(e[K], t);
+        dit_combine<NN, K + 1>(z, e, o);
+    }
+}
+
+// bins 1 .. NN/4 - 1 of the real DFT from the half-length DFTs E and O
+template <int NN, int K>
+__device__ __forceinline__ void rdit_combine(float2 (&X)[NN / 2 + 1], const float2 (&E)[NN / 4 + 1],
+                                             const float2 (&O)[NN / 4 + 1]) {
+    if constexpr (K < NN / 4) {
+        const float2 t = cmul_w64<K * (64 / NN)>(O[K]);
+        X[K] = cadd(E[K], t);
+        X[NN / 2 - K] = make_float2(E[K].x - t.x, t.y - E[K].y);
+        rdit_combine<NN, K + 1>(X, E, O);
+    }
+}
+
+}  // namespace detail
 
 // In-register real DFT of NN points (NN = 2, 4, ..., 64): bins 0..NN/2 of
 // X[k] = sum_t x[t] exp(-2 pi i k t / NN), radix-2 decimation in time on the
 // real sequence. With E and O the half-length DFTs of the even and odd
 // samples (both real sequences, so E[NN/2 - k] = conj E[k]),
 //   X[k] = E[k] + w^k O[k],  X[NN/2 - k] = conj(E[k] - w^k O[k]),  k <= NN/4,
-// w = exp(-2 pi i / NN); w^(NN/4) = -i and the k = 0 terms are real.
+// w = exp(-2 pi i / NN); w^(NN/4) = -i and the k = 0 terms are real. Every
+// index and twiddle is a compile-time constant.
 template <int NN>
 __device__ __forceinline__ void rdft_reg(const float (&x)[NN], float2 (&X)[NN / 2 + 1]) {
     if constexpr (NN == 2) {
@@ -94,71 +127,26 @@ __device__ __forceinline__ void rdft_reg(const float (&x)[NN], float2 (&X)[NN / 
         rdft_reg<H>(xo, O);
         X[0] = make_float2(E[0].x + O[0].x, 0.0f);
         X[H] = make_float2(E[0].x - O[0].x, 0.0f);
-#pragma unroll
-        for (int k = 1; k < Q; k++) {
-            const float2 t = cmul_tw64c(O[k], k * (64 / NN));
-            X[k] = cadd(E[k], t);
-            X[H - k] = make_float2(E[k].x - t.x, t.y - E[k].y);
-        }
+        detail::rdit_combine<NN, 1>(X, E, O);
         X[Q] = make_float2(E[Q].x, -O[Q].x);
     }
 }
 
-// In-register NN-point complex DFT with compile-time twiddles (NN <= 64),
-// radix-2 decimation in time; natural order in and out.
+// In-register NN-point complex DFT (NN = 1, 2, 4, ..., 64), natural order in
+// and out: recursive radix-2 decimation in time, every index and twiddle a
+// compile-time constant.
 template <int NN>
 __device__ __forceinline__ void fft_regc(float2 (&z)[NN]) {
+    if constexpr (NN > 1) {
+        float2 e[NN / 2], o[NN / 2];
 #pragma unroll
-    for (int i = 0; i < NN; i++) {
-        const int j = bitrev<NN>(i);
-        if (i < j) {
-            float2 t = z[i];
-            z[i] = z[j];
-            z[j] = t;
+        for (int t = 0; t < NN / 2; t++) {
+            e[t] = z[2 * t];
+            o[t] = z[2 * t + 1];
         }
-    }
-#pragma unroll
-    for (int len = 2; len <= NN; len <<= 1) {
-#pragma unroll
-        for (int i = 0; i < NN; i += len) {
-#pragma unroll
-            for (int j = 0; j < len / 2; j++) {
-                const float2 v = cmul_tw64c(z[i + j + len / 2], j * (64 / len));
-                const float2 u = z[i + j];
-                z[i + j] = cadd(u, v);
-                z[i + j + len / 2] = csub(u, v);
-            }
-        }
-    }
-}
-
-// In-register NN-point complex DFT, X[k] = sum_t z[t] exp(-2 pi i k t / NN),
-// radix-2 decimation in time; natural order in and out. tw64[q] holds
-// exp(-2 pi i q / 64) for q in [0, 32], so NN <= 64.
-template <int NN>
-__device__ __forceinline__ void fft_reg(float2 (&z)[NN], const float2 *tw64) {
-#pragma unroll
-    for (int i = 0; i < NN; i++) {
-        const int j = bitrev<NN>(i);
-        if (i < j) {
-            float2 t = z[i];
-            z[i] = z[j];
-            z[j] = t;
-        }
-    }
-#pragma unroll
-    for (int len = 2; len <= NN; len <<= 1) {
-#pragma unroll
-        for (int i = 0; i < NN; i += len) {
-#pragma unroll
-            for (int j = 0; j < len / 2; j++) {
-                const float2 w = tw64[j * (64 / len)];
-                const float2 v = cmul(z[i + j + len / 2], w);
-                const float2 u = z[i + j];
-                z[i + j] = cadd(u, v);
-                z[i + j + len / 2] = csub(u, v);
-            }
-        }
+        fft_regc<NN / 2>(e);
+        fft_regc<NN / 2>(o);
+        detail::dit_combine<NN, 0>(z, e, o);
     }
 }
 

@@ -84,6 +84,10 @@ cudaError_t launch_tail_update(const uint8_t *hist_in, const uint8_t *chunk, uin
                                cudaStream_t s);
 cudaError_t launch_phase1(int T, int N1, const Phase1Params &p, int n_streams, cudaStream_t s);
 cudaError_t launch_phase2(int N2, const Phase2Params &p, int n_ant, cudaStream_t s);
+// FP32 second stage for N2 = 1024 (launch_phase2 routes it there): one warp
+// per sequence, two in-register 32-point DFTs around one shared-memory transpose
+cudaError_t launch_phase2w(const Phase2Params &p, int n_ant, cudaStream_t s);
+size_t phase2w_smem_bytes();
 
 // Tile shapes (host and device agree through these).
 constexpr int kP1Rows = 32;   // spectra per phase-1 CTA

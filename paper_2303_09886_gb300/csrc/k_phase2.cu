@@ -302,7 +302,7 @@ cudaError_t launch_phase2(int N2, const Phase2Params &p, int n_ant, cudaStream_t
         case 128: return launch_p2<128>(p, n_ant, s);
         case 256: return launch_p2<256>(p, n_ant, s);
         case 512: return launch_p2<512>(p, n_ant, s);
-        case 1024: return launch_p2<1024>(p, n_ant, s);
+        case 1024: return launch_phase2w(p, n_ant, s);   // one warp per 1024-point sequence
         default: return cudaErrorInvalidValue;
     }
 }
