@@ -36,21 +36,24 @@ UNIT = "Gsample/s"
 # DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the hash of the kernel sources it was
 # taken on; reported as null once the sources change.
-# DRAM bytes (read + write) of one launch of each slab kernel from an ncu
-# capture (profiles/, 1 antenna x 2 pol x 2^24 samples/pol: one slab launch of
-# 2 x 256 spectra, the same 8.4 M input samples as one slab launch of the
-# 4-antenna workload). ncu flushes the caches before each replay, so these are
-# cold-cache figures. Valid only for the sources they were taken from (src =
-# hash of the kernel's source files).
+# DRAM bytes (read + write) per input sample of each slab kernel, from ncu
+# captures (profiles/) of 1 antenna x 2 pol x 2^24 samples/pol with the whole
+# chunk in one slab (one launch of 2 x 1024 spectra = 33.5 M samples). ncu
+# flushes the caches before each replay (cold cache). The bench scales them to
+# its own launch by the input samples the launch processes. Valid only for the
+# sources they were taken from (src = hash of the kernel's source files).
 KERNEL_SOURCES = {
     "k_phase1": ['k_phase1.cuh', 'k_phase1_t1.cu', 'k_phase1_t2.cu', 'k_phase1_t4.cu', 'k_phase1_t8.cu', 'k_phase1_t16.cu', 'k_phase1_t32.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase2": ['k_phase2.cu', 'fe_device.cuh', 'fe_internal.cuh'],
+    "k_phase2w": ['k_phase2w.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase2_tc": ['k_phase2_tc.cu', 'fe_mma.cuh', 'fe_device.cuh', 'fe_internal.cuh'],
 }
-NCU_TRAFFIC = {   # DRAM bytes per input sample of the launch (captured launch: 8388608 samples)
-    "k_phase1<16,16,32>": {"bytes_per_sample": (12265728 + 18176) / 8388608, "src": "c660b3bf3aa91e1f"},
-    "k_phase2<1024>": {"bytes_per_sample": (37927168 + 256) / 8388608, "src": "14ae78ff12ad7729"},
-    "k_phase2_tc<1>": {"bytes_per_sample": (37964032 + 15104) / 8388608, "src": "b609bd875dcffd25"},
+_CAPTURED = 33554432   # input samples of the captured launch
+NCU_TRAFFIC = {
+    "k_phase1<16,16,32,0>": {"bytes_per_sample": (43747584 + 92332800) / _CAPTURED, "src": "5f71d5ebe94f7be5"},
+    "k_phase1<16,16,32,1>": {"bytes_per_sample": (43742976 + 26004480) / _CAPTURED, "src": "5f71d5ebe94f7be5"},
+    "k_phase2w": {"bytes_per_sample": (151216128 + 16456448) / _CAPTURED, "src": "d952dfc97b634cca"},
+    "k_phase2_tc<1>": {"bytes_per_sample": (75732992 + 9537024) / _CAPTURED, "src": "4d28994ea3e9e4d2"},
 }
 
 
@@ -392,6 +395,9 @@ def run_service(args):
 
 def _tuned_split(fengine, wl, prec, args):
     """The work split of the plan: the autotuner's pick (fengine_autotune) unless --no-autotune."""
+    if args.split:
+        n1, sl = (int(v) for v in args.split.split(","))
+        return {"fft_n1": n1, "slab_spectra": sl, "autotuned": False}
     if args.no_autotune:
         return {"fft_n1": 0, "slab_spectra": 0, "autotuned": False}
     best, table = fengine.autotune(wl.n_antennas, wl.n_channels, wl.n_taps, wl.chunk_samples,
@@ -457,6 +463,7 @@ def main(argv=None):
     ap.add_argument("--load", type=float, default=1.5, help="workload 5: offered load / sustained rate")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision forms")
     ap.add_argument("--no-autotune", action="store_true", help="use the built-in work split instead of the autotuner's")
+    ap.add_argument("--split", default="", help="fixed work split 'N1,SLAB' (fft_n1, slab_spectra) instead of tuning")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="fp32 plain form, or the tensor-core forms (FP16/BF16 operands, FP32 accumulation)")
     args = ap.parse_args(argv)
@@ -622,7 +629,8 @@ def main(argv=None):
 
     # roofline of the dominant kernel (algorithmic bytes per launch / mean launch time)
     N1 = plan.info.fft_n1
-    inter = (N1 // 2 + 1) / N1 * 8.0          # bytes of FP32 intermediate per input sample
+    # bytes of intermediate per input sample (FP32 pairs; FP16 pairs in the FP16 form)
+    inter = (N1 // 2 + 1) / N1 * (4.0 if args.precision == "fp16" else 8.0)
     spl = wl.samples_per_step
     bytes_per_sample = {"phase1": 1.25 + inter, "phase2": inter + 1.0}
     dom = max(("phase1", "phase2"), key=lambda k: stage_ms[k])
@@ -633,8 +641,10 @@ def main(argv=None):
     # algorithmic bytes of one launch (its slab's samples) / its mean duration
     achieved = bytes_per_sample[dom] * (spl / slabs) / (launch_ms / 1e3) / 1e9
     N2 = plan.info.fft_n2
-    kname = {"phase1": f"k_phase1<{wl.n_taps},{N1},{min(512 // N1, N2)}>",
-             "phase2": {"fp32": f"k_phase2<{N2}>", "fp16": "k_phase2_tc<1>", "bf16": "k_phase2_tc<2>"}[args.precision]}[dom]
+    half = 1 if args.precision == "fp16" else 0
+    kname = {"phase1": f"k_phase1<{wl.n_taps},{N1},{min(512 // N1, N2)},{half}>",
+             "phase2": {"fp32": "k_phase2w" if N2 == 1024 else f"k_phase2<{N2}>", "fp16": "k_phase2_tc<1>",
+                        "bf16": "k_phase2_tc<2>"}[args.precision]}[dom]
     tr = NCU_TRAFFIC.get(kname)
     # scaled from the captured launch to this launch by its input samples
     # (the kernels' DRAM traffic grows in proportion to the samples processed)
