@@ -1,5 +1,5 @@
-// Phase 1 of the fused F-engine: 10-bit unpack, coarse delay, PFB FIR (Eq. 1)
-// and the first stage of the four-step real DFT.
+// Phase 1 of the fused F-engine: 10-bit unpack, coarse
+// delay, PFB FIR (Eq. 1) and the first stage of the four-step real DFT.
 //
 // Four-step split of the N-point DFT of one spectrum's filtered samples g:
 //   t = N2 t1 + t2, k = k1 + N1 k2,
@@ -11,19 +11,19 @@
 // {N2 t1 + t2 : t1 < N1, t2 in [t2_0, t2_0 + W)} of one (antenna, pol)
 // stream. Output row r is the FIR over input rows r .. r + T - 1 (input row
 // i holds the samples of spectrum q0 + i; Eq. 1's w[t + N j] weights row
-// r + j). For each run of output rows with one coarse delay (Sec. 3.3: each
-// PFB window uses one consistent delay) it
-//   1. unpacks the run's input rows into shared memory as FP32 (exact for
-//      10-bit integers): four lanes share a row segment (row, t1) of W
-//      samples and decode whole 5-byte groups aligned to the packed stream,
-//      so a segment is stored with its 0-3 sample misalignment;
-//   2. runs the T-tap FIR down each column: each thread owns two columns
-//      (packed FP32x2 FMAs) and a ring of T + 1 input rows in registers, and
-//      emits output rows in pairs (two independent FMA chains), writing g in
-//      place;
-// and finally, for each (output row, t2), does the real N1-point DFT over
-// t1 in registers, multiplies by the twiddle and stores B to the
-// intermediate.
+// r + j); every PFB window uses one coarse delay (Sec. 3.3), so a tile is
+// processed per run of output rows with one delay.
+//
+// Each thread owns two FIR columns and decodes their 10-bit samples itself,
+// straight from the packed stream: sample s occupies bits [10 s, 10 s + 10)
+// (most significant bit first), i.e. bytes 5 s / 4 and 5 s / 4 + 1 at a bit
+// offset 2 (s mod 4) that is the same for every row of a column (a row is N
+// samples, a multiple of 4), and the row's bytes sit 5 N / 4 further on. The
+// FIR keeps T + 1 input rows in a register ring and emits output rows in
+// pairs (packed FP32x2 FMAs, two independent chains); g goes to shared
+// memory, and for each (output row, t2) the real N1-point DFT over t1 runs in
+// registers, is multiplied by the twiddle and stored (FP32 pairs, or FP16
+// pairs for the FP16 form).
 #pragma once
 #include <cuda_fp16.h>
 
@@ -37,19 +37,11 @@ constexpr int kP1Threads = 256;
 template <int T, int N1, int W>
 struct P1Shape {
     static constexpr int R = kP1Rows;
-    static constexpr int NG = (W + 3) / 4 + 1;   // 4-sample groups per row segment
-    static constexpr int SW = 4 * NG;            // shared-memory floats per row segment
-    static constexpr int ROW = N1 * SW;          // floats per buffered row
-    static constexpr int C = N1 * W;             // FIR columns per tile
-    static constexpr int ROWS = R + T - 1;       // input rows of a full tile
-    static constexpr int NI = (NG + 3) / 4;      // groups per lane per segment
-    static constexpr int SPT = 2;                // segments per 4-lane group per batch
+    static constexpr int GW = W + 1;         // shared-memory floats per (row, t1) segment of g
+    static constexpr int ROW = N1 * GW;      // floats per output row
+    static constexpr int C = N1 * W;         // FIR columns per tile
+    static constexpr int ROWS = R + T - 1;   // input rows of a full tile
 };
-
-// A 5-byte group at packed byte b of a 4-byte aligned buffer whose length is
-// a multiple of 4 is read with the two aligned 32-bit words at b & ~3: the
-// group ends at b + 5 <= length, so length - (b & ~3) >= 5 and, being a
-// multiple of 4, >= 8 -- both words are inside the buffer.
 
 // Exact float of the 10-bit two's-complement field in the low bits of x:
 // (field ^ 512) is the offset-binary value in [0, 1024), placed in the
@@ -58,104 +50,61 @@ __device__ __forceinline__ float field10_to_float(unsigned x) {
     return __uint_as_float(((x & 0x3FFu) ^ 0x200u) | 0x4B000000u) - 8389120.0f;
 }
 
-// 4 samples of the 5-byte group whose first byte is byte j of w0 (the group
-// continues into w1): byte permutes build the group's bits 0-31 and 8-39 in
-// big-endian order, and the four 10-bit fields are shifted out of them.
-// All-zero words decode to four zero samples (a zero field is the value 0),
-// which is what a group past the received samples must read as.
-__device__ __forceinline__ float4 decode_group_perm(unsigned w0, unsigned w1, unsigned j) {
-    const unsigned hi = __byte_perm(w0, w1, 0x0123u + j * 0x1111u);   // group bits 0..31
-    const unsigned lo = __byte_perm(w0, w1, 0x1234u + j * 0x1111u);   // group bits 8..39
-    return make_float4(field10_to_float(hi >> 22), field10_to_float(lo >> 20), field10_to_float(lo >> 10),
-                       field10_to_float(lo));
+// The sample whose field starts in byte b[0] at bit offset sh from the top
+// (sh = 2 (s mod 4)): the two bytes as a big-endian 16-bit word, shifted down
+// by 6 - sh.
+__device__ __forceinline__ float sample10(const uint8_t *b, unsigned sh) {
+    const unsigned v = __byte_perm((unsigned)__ldg(b), (unsigned)__ldg(b + 1), 0x0004u);   // b[0] << 8 | b[1]
+    return field10_to_float(v >> (6u - sh));
 }
 
-// Packed words of one chunk's row segments, loaded ahead of their decode.
-template <class S>
-struct P1Pending {
-    unsigned w0[S::SPT][S::NI], w1[S::SPT][S::NI], j[S::SPT], ga[S::SPT];
-    int mode[S::SPT];   // 0 nothing, 1 fast (words loaded), 2 slow (decoded with its own loads)
-    int dst[S::SPT];    // float offset of the segment in the buffer
-};
+// Sample at relative index s (from the first history sample), or 0 past the
+// received samples.
+__device__ __forceinline__ float sample10_at(const uint8_t *hist, const uint8_t *chunk, unsigned s, unsigned H,
+                                             unsigned HL) {
+    if (s >= HL) return 0.0f;
+    const bool h = s < H;
+    const unsigned u = h ? s : s - H;
+    return sample10((h ? hist : chunk) + (u >> 2) * 5u + ((u & 3u) * 5u >> 2), 2u * (s & 3u));
+}
 
-struct P1Stream {
-    const uint8_t *chunk, *hist;
-    unsigned rel0, H, HL;   // relative sample index of (input row 0, t1 0, w 0); history; history + chunk
-};
-
-// Issue the loads of segments seg0 + u * (kP1Threads / 4) + (this lane's
-// slot), u < SPT, of input rows [i0, i_end): segment (i - i0) * N1 + t1.
-// Four lanes share a segment: lane l4 takes groups l4 + 4 k, 20 k bytes
-// apart, so its byte alignment and word offsets are fixed per segment. A
-// warp's 8 segments are permuted so that the two sharing an 8-lane phase of
-// the 16-byte stores are 4 apart in t1 (4 SW floats: no bank conflicts).
-template <class S, int N1>
-__device__ __forceinline__ void p1_load(P1Pending<S> &pd, const P1Stream &st, int seg0, int i0, int i_end, int N,
-                                        int N2) {
-    const int l4 = threadIdx.x & 3, sl = (threadIdx.x >> 2) & 7;
-    const int seg_lane = (threadIdx.x >> 5) * 8 + (sl & 1) * 4 + (sl >> 1);
-    const int nseg = (i_end - i0) * N1;
+// General case of the FIR: a run of output rows [ra, rb) of a tile that
+// touches the history or has several delay runs; samples checked one by one
+// (history / chunk / past the received samples), one row of loads at a time.
+// The window tap of output row r is its first input row, i = r. Kept out of
+// line so that its registers do not weigh on the common path.
+template <int T, class S>
+__device__ __noinline__ void p1_fir_general(const Phase1Params &p, const uint8_t *hist, const uint8_t *chunk,
+                                            unsigned H, unsigned HL, unsigned s0a, unsigned s0b, int ra, int rb,
+                                            float *ga, float *gb, int stream, int q0, int t2_0, int ta, int tb) {
+    const int N = p.N;
+    float2 w2[T];
 #pragma unroll
-    for (int u = 0; u < S::SPT; u++) {
-        const int seg = seg0 + u * (kP1Threads / 4) + seg_lane;
-        const int t1 = seg & (N1 - 1), i = i0 + seg / N1;
-        pd.mode[u] = 0;
-        pd.j[u] = 0u;
-        pd.ga[u] = 0u;
-        pd.dst[u] = i * S::ROW + t1 * S::SW;
-        if (seg < nseg) {
-            // sample indices relative to the first history sample fit 32 bits
-            // (the plan keeps H + L < 2^31)
-            const unsigned ga = (st.rel0 + (unsigned)(N * i + N2 * t1)) & ~3u;   // first group's sample
-            const unsigned ge = ga + 4u * S::NG;                                 // one past the last
-            pd.ga[u] = ga;
-            const bool in_hist = ge <= st.H, in_chunk = ga >= st.H && ge <= st.HL;
-            pd.mode[u] = (in_hist || in_chunk) ? 1 : 2;
-            if (pd.mode[u] == 1) {
-                const unsigned bl = ((in_hist ? ga : ga - st.H) >> 2) * 5u + 5u * l4;
-                const unsigned *wp =
-                    reinterpret_cast<const unsigned *>((in_hist ? st.hist : st.chunk) + (bl & ~3u));
-                pd.j[u] = bl & 3u;
+    for (int j = 0; j < T; j++)
+        w2[j] = make_float2(__ldg(p.w + t2_0 + ta + (long long)N * j), __ldg(p.w + t2_0 + tb + (long long)N * j));
+    unsigned dep = 0u;
+    float2 win[T];
+#pragma unroll 1
+    for (int row = ra; row < rb + T - 1; row++) {
+        const float xa = sample10_at(hist, chunk, s0a + (unsigned)(row * N) + dep, H, HL);
+        const float xb = sample10_at(hist, chunk, s0b + (unsigned)(row * N) + dep, H, HL);
+        asm volatile("" : "+r"(dep) : "f"(xa), "f"(xb));
+        // shift the window: win[j] holds input row (row - T + 1 + j)
 #pragma unroll
-                for (int k = 0; k < S::NI; k++) {
-                    if (l4 + 4 * k < S::NG) {
-                        pd.w0[u][k] = __ldg(wp + 5 * k);
-                        pd.w1[u][k] = __ldg(wp + 5 * k + 1);
-                    }
-                }
-            }
+        for (int j = 0; j < T - 1; j++) win[j] = win[j + 1];
+        win[T - 1] = make_float2(xa, xb);
+        if (p.window_tap && row < rb) {
+            int *tap = p.window_tap + ((long long)stream * p.M + q0 + row) * N + t2_0;
+            tap[ta] = (int)xa;
+            tap[tb] = (int)xb;
         }
-    }
-}
-
-template <class S>
-__device__ __forceinline__ void p1_decode(const P1Pending<S> &pd, const P1Stream &st, float *buf) {
-    const int l4 = threadIdx.x & 3;
+        const int r = row - (T - 1);
+        if (r >= ra) {
+            float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int u = 0; u < S::SPT; u++) {
-        float *dst = buf + pd.dst[u];
-        if (pd.mode[u] == 1) {
-#pragma unroll
-            for (int k = 0; k < S::NI; k++)
-                if (l4 + 4 * k < S::NG)
-                    *reinterpret_cast<float4 *>(dst + 4 * l4 + 16 * k) =
-                        decode_group_perm(pd.w0[u][k], pd.w1[u][k], pd.j[u]);
-        } else if (pd.mode[u] == 2) {
-            // straddles the history/chunk boundary or the end of the received
-            // samples (zeros past it)
-            for (int gi = l4; gi < S::NG; gi += 4) {
-                const unsigned g = pd.ga[u] + 4u * gi;
-                unsigned v0 = 0u, v1 = 0u, j = 0u;
-                if (g < st.HL) {
-                    const bool h = g < st.H;
-                    const unsigned bb = ((h ? g : g - st.H) >> 2) * 5u;
-                    const unsigned *wq = reinterpret_cast<const unsigned *>((h ? st.hist : st.chunk) + (bb & ~3u));
-                    v0 = __ldg(wq);
-                    v1 = __ldg(wq + 1);
-                    j = bb & 3u;
-                }
-                *reinterpret_cast<float4 *>(dst + 4 * gi) = decode_group_perm(v0, v1, j);
-            }
+            for (int j = 0; j < T; j++) acc = __ffma2_rn(w2[j], win[j], acc);
+            ga[r * S::ROW] = acc.x;
+            gb[r * S::ROW] = acc.y;
         }
     }
 }
@@ -164,9 +113,8 @@ template <int T, int N1, int W, bool HALF>
 __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) {
     using S = P1Shape<T, N1, W>;
     constexpr int R = S::R, H1 = N1 / 2;
-    extern __shared__ float xs[];              // [ROWS][N1][SW]
+    extern __shared__ float gs[];              // [R][N1][GW] FIR output g
     __shared__ int c_sm[R];
-    __shared__ int off_sm[R];                  // segment misalignment of each row's run
     __shared__ float2 tw1_sm[(H1 + 1) * W];    // exp(-2 pi i k1 t2 / N) for this tile's t2
 
     const int N = p.N, N2 = p.N2;
@@ -174,11 +122,10 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
     const int t2_0 = blockIdx.x * W;
     const int q0 = p.q_begin + blockIdx.y * R;
     const int Rv = min(R, p.q_begin + p.q_count - q0);
-    P1Stream st;
-    st.chunk = p.chunk + (long long)stream * p.chunk_bytes;
-    st.hist = p.hist + (long long)stream * p.hist_bytes;
-    st.H = (unsigned)p.H;
-    st.HL = (unsigned)(p.H + p.L);
+    const uint8_t *chunk = p.chunk + (long long)stream * p.chunk_bytes;
+    const uint8_t *hist = p.hist + (long long)stream * p.hist_bytes;
+    const unsigned H = (unsigned)p.H, HL = (unsigned)(p.H + p.L);
+    const unsigned RB = (unsigned)N / 4u * 5u;   // packed bytes per row (a multiple of 4: same alignment every row)
     // rel index (from the first history sample) of input row 0, column t = 0, before the delay
     const long long rel_base = (long long)N * (p.m0 + q0) - (p.t_in - p.H) + t2_0;
 
@@ -187,109 +134,100 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
         const int k = i / W, w = i % W;
         tw1_sm[i] = __ldg(p.tw1 + (long long)k * N2 + t2_0 + w);
     }
+
+    // this thread's FIR column pair (c, c + C/2) and its weights
+    const int ca = threadIdx.x, cb = threadIdx.x + S::C / 2;
+    const bool has_pair = ca < S::C / 2;
+    const int ta = N2 * (ca / W) + (ca % W), tb = N2 * (cb / W) + (cb % W);   // column offsets in a row
+    float2 w2[T];
+#pragma unroll
+    for (int j = 0; j < T; j++)
+        w2[j] = has_pair ? make_float2(__ldg(p.w + t2_0 + ta + (long long)N * j), __ldg(p.w + t2_0 + tb + (long long)N * j))
+                         : make_float2(0.0f, 0.0f);
+    float *ga = gs + (ca / W) * S::GW + (ca % W), *gb = gs + (cb / W) * S::GW + (cb % W);
     __syncthreads();
 
-    P1Pending<S> pd;
     int ra = 0;
     while (ra < Rv) {
         const int cd = c_sm[ra];
         int rb = ra + 1;
         while (rb < Rv && c_sm[rb] == cd) rb++;
-        const long long rel0 = rel_base - cd;   // rel of (input row 0, t1 0, w 0) at this delay
-        st.rel0 = (unsigned)rel0;
-        const int off = (int)(rel0 & 3);         // misalignment of every segment of the run
-        const int i_end = rb + T - 1;            // input rows [ra, i_end)
-        // 1. unpack, SPT segments per 4-lane group per batch with all their
-        // loads in flight before the first decode
-        for (int seg0 = 0; seg0 < (i_end - ra) * N1; seg0 += S::SPT * (kP1Threads / 4)) {
-            p1_load<S, N1>(pd, st, seg0, ra, i_end, N, N2);
-            p1_decode<S>(pd, st, xs);
-        }
-        __syncthreads();
-        if (p.window_tap) {
-            // the window tap of output row r is its first input row, i = r
-            for (int e = threadIdx.x; e < (rb - ra) * S::C; e += kP1Threads) {
-                const int row = ra + e / S::C, col = e % S::C;
-                const int t1 = col / W, w = col % W;
-                p.window_tap[((long long)stream * p.M + q0 + row) * N + N2 * t1 + t2_0 + w] =
-                    (int)xs[row * S::ROW + t1 * S::SW + off + w];
+        const long long rel0 = rel_base - cd;   // rel of (input row 0, column 0) at this delay
+        // the whole tile at one delay and inside the chunk: fixed byte pointers per column
+        const long long lo = rel0, hi = rel0 + (long long)N * (R + T - 2) + (long long)N2 * (N1 - 1) + W;
+        if (has_pair && ra == 0 && rb == R && lo >= (long long)H && hi <= (long long)HL && !p.window_tap) {
+            const unsigned sa = (unsigned)(rel0 + ta) - H, sb = (unsigned)(rel0 + tb) - H;
+            const uint8_t *pa = chunk + (sa >> 2) * 5u + ((sa & 3u) * 5u >> 2);
+            const uint8_t *pb = chunk + (sb >> 2) * 5u + ((sb & 3u) * 5u >> 2);
+            const unsigned sha = 6u - 2u * (sa & 3u), shb = 6u - 2u * (sb & 3u);
+            // the packed bytes of rows row + 1 .. row + PF are in flight while row
+            // is filtered; the loads of a row take an (always zero) offset that
+            // the compiler must treat as produced by the previous row's decode,
+            // which keeps it from hoisting every row's loads (and registers) up front
+            constexpr int PF = 6, NR = R + T - 1;
+            unsigned dep = 0u;
+            unsigned ba[PF][2], bb[PF][2];
+#pragma unroll
+            for (int i = 0; i < PF; i++) {
+                ba[i][0] = __ldg(pa + i * RB);
+                ba[i][1] = __ldg(pa + i * RB + 1);
+                bb[i][0] = __ldg(pb + i * RB);
+                bb[i][1] = __ldg(pb + i * RB + 1);
             }
-            __syncthreads();   // the FIR below overwrites these slots in place
-        }
-        // 2. FIR down each column, g written over the row it starts at
-        if (ra == 0 && rb == R) {
-            // one delay for the whole tile: no predicates, two columns per
-            // thread (c and c + C/2) through packed FP32x2 FMAs
-            for (int pc = threadIdx.x; pc < S::C / 2; pc += kP1Threads) {
-                const int ca = pc, cb = pc + S::C / 2;
-                const int ta = N2 * (ca / W) + t2_0 + ca % W, tb = N2 * (cb / W) + t2_0 + cb % W;
-                float *xa = xs + (ca / W) * S::SW + off + ca % W;
-                float *xb = xs + (cb / W) * S::SW + off + cb % W;
-                // outputs in pairs (r, r + 1), two independent FMA chains, from a
-                // ring of T + 1 input rows
-                float2 w2[T], win[T + 1];
+            // outputs in pairs (r, r + 1), two independent FMA chains, from a
+            // ring of T + 1 input rows
+            float2 win[T + 1];
 #pragma unroll
-                for (int j = 0; j < T; j++)
-                    w2[j] = make_float2(__ldg(p.w + ta + (long long)N * j), __ldg(p.w + tb + (long long)N * j));
+            for (int row = 0; row < NR; row++) {
+                const int u = row % PF;
+                const float xa = field10_to_float(__byte_perm(ba[u][0], ba[u][1], 0x0004u) >> sha);
+                const float xb = field10_to_float(__byte_perm(bb[u][0], bb[u][1], 0x0004u) >> shb);
+                win[row % (T + 1)] = make_float2(xa, xb);
+                asm volatile("" : "+r"(dep) : "f"(xa), "f"(xb));
+                if (row + PF < NR) {
+                    const unsigned off = (row + PF) * RB + dep;
+                    ba[u][0] = __ldg(pa + off);
+                    ba[u][1] = __ldg(pa + off + 1);
+                    bb[u][0] = __ldg(pb + off);
+                    bb[u][1] = __ldg(pb + off + 1);
+                }
+                const int r = row - T;   // pair (r, r + 1) is complete once row r + T is in
+                if (r >= 0 && (r & 1) == 0) {
+                    float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
 #pragma unroll
-                for (int row = 0; row < R + T - 1; row++) {
-                    win[row % (T + 1)] = make_float2(xa[row * S::ROW], xb[row * S::ROW]);
-                    const int r = row - T;      // pair (r, r + 1) is complete once row r + T is in
-                    if (r >= 0 && (r & 1) == 0) {
-                        float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
-#pragma unroll
-                        for (int j = 0; j < T; j++) {
-                            acc0 = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc0);
-                            acc1 = __ffma2_rn(w2[j], win[(r + 1 + j) % (T + 1)], acc1);
-                        }
-                        xa[r * S::ROW] = acc0.x;
-                        xb[r * S::ROW] = acc0.y;
-                        xa[(r + 1) * S::ROW] = acc1.x;
-                        xb[(r + 1) * S::ROW] = acc1.y;
+                    for (int j = 0; j < T; j++) {
+                        acc0 = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc0);
+                        acc1 = __ffma2_rn(w2[j], win[(r + 1 + j) % (T + 1)], acc1);
                     }
-                }
-                if constexpr ((R & 1) != 0) {
-                    // R odd: the last output row has no partner
-                    constexpr int r = R - 1;
-                    float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-                    for (int j = 0; j < T; j++) acc = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc);
-                    xa[r * S::ROW] = acc.x;
-                    xb[r * S::ROW] = acc.y;
+                    ga[r * S::ROW] = acc0.x;
+                    gb[r * S::ROW] = acc0.y;
+                    ga[(r + 1) * S::ROW] = acc1.x;
+                    gb[(r + 1) * S::ROW] = acc1.y;
                 }
             }
-        } else
-        for (int col = threadIdx.x; col < S::C; col += kP1Threads) {
-            const int t1 = col / W, w = col % W;
-            const int t = N2 * t1 + t2_0 + w;
-            float *x = xs + t1 * S::SW + off + w;
-            float wr[T], win[T];
+            if constexpr ((R & 1) != 0) {
+                constexpr int r = R - 1;
+                float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int j = 0; j < T; j++) wr[j] = __ldg(p.w + t + (long long)N * j);
-#pragma unroll
-            for (int row = 0; row < R + T - 1; row++) {
-                if (row >= ra && row < rb + T - 1) win[row % T] = x[row * S::ROW];
-                const int r = row - (T - 1);
-                if (r >= ra && r < rb) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < T; j++) acc = fmaf(wr[j], win[(r + j) % T], acc);
-                    x[r * S::ROW] = acc;
-                }
+                for (int j = 0; j < T; j++) acc = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc);
+                ga[r * S::ROW] = acc.x;
+                gb[r * S::ROW] = acc.y;
             }
+        } else if (has_pair) {
+            p1_fir_general<T, S>(p, hist, chunk, H, HL, (unsigned)(rel0 + ta), (unsigned)(rel0 + tb), ra, rb, ga, gb,
+                                 stream, q0, t2_0, ta, tb);
         }
-        for (int r = ra + (int)threadIdx.x; r < rb; r += kP1Threads) off_sm[r] = off;
-        __syncthreads();
         ra = rb;
     }
+    __syncthreads();
 
-    // 3. real N1-point DFT over t1, twiddle, store B[k1][t2]
+    // real N1-point DFT over t1, twiddle, store B[k1][t2]
     for (int e = threadIdx.x; e < Rv * W; e += kP1Threads) {
         const int r = e / W, w = e % W;
-        const float *g = xs + r * S::ROW + off_sm[r] + w;
+        const float *g = gs + r * S::ROW + w;
         float x[N1];
 #pragma unroll
-        for (int t1 = 0; t1 < N1; t1++) x[t1] = g[t1 * S::SW];
+        for (int t1 = 0; t1 < N1; t1++) x[t1] = g[t1 * S::GW];
         float2 X[H1 + 1];
         rdft_reg<N1>(x, X);
         const long long o = ((long long)stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) * N2 + t2_0 + w;
@@ -317,7 +255,7 @@ template <int T, int N1, int W, bool HALF = false>
 cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t s) {
     using S = P1Shape<T, N1, W>;
     if (p.W != W || p.N2 % W) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)S::ROWS * S::ROW * sizeof(float);
+    const size_t smem = (size_t)S::R * S::ROW * sizeof(float);
     cudaError_t e =
         cudaFuncSetAttribute(k_phase1<T, N1, W, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
