@@ -1,5 +1,5 @@
-// Phase 1 of the fused F-engine: 10-bit unpack, coarse
-// delay, PFB FIR (Eq. 1) and the first stage of the four-step real DFT.
+// Phase 1 of the fused F-engine: 10-bit unpack, coarse delay, PFB FIR
+// (Eq. 1) and the first stage of the four-step real DFT.
 //
 // Four-step split of the N-point DFT of one spectrum's filtered samples g:
 //   t = N2 t1 + t2, k = k1 + N1 k2,
