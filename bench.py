@@ -126,6 +126,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _max_over_ranks(x: float, ws: int, device: str) -> float:
+    """The largest x over all ranks: the job takes as long as its slowest rank."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_throughput(samples_per_step: int, steps: int, ms: float, ws: int) -> float:
+    """Whole-job Gsample/s: every rank (one independent replica per GPU)
+    processes samples_per_step per step; ms is the slowest rank's time."""
+    return ws * samples_per_step * steps / (ms / 1e3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -543,12 +560,8 @@ def main(argv=None):
     ms = e0.elapsed_time(e1)
     stage_ms, calls = plan.stage_times()
     plan.set_profiling(False)
-    ms_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = ws * wl.samples_per_step * args.steps / (ms_max / 1e3) / 1e9
+    ms_max = _max_over_ranks(ms, ws, "cuda")
+    value = _job_throughput(wl.samples_per_step, args.steps, ms_max, ws)
 
     # end to end through the public API with host buffers: H2D of the packed
     # chunk from pinned memory, the call, D2H of the 8-bit output, every step
@@ -603,12 +616,8 @@ def main(argv=None):
         run_e2e(k2)
         e3.record(stream)
         torch.cuda.synchronize()
-        ems = e2.elapsed_time(e3)
-        if ws > 1:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": ws * wl.samples_per_step * k2 / (ems / 1e3) / 1e9, "unit": UNIT,
+        ems = _max_over_ranks(e2.elapsed_time(e3), ws, "cuda")
+        e2e = {"value": _job_throughput(wl.samples_per_step, k2, ems, ws), "unit": UNIT,
                "h2d_bytes_per_step": int(h_in.numel()), "d2h_bytes_per_step": int(h_outs[0].numel()),
                "steps": k2, "pipelined": "H2D of step k+1 and D2H of step k-1 overlap step k"}
     # the other precision forms on the same input, same timing (context for
