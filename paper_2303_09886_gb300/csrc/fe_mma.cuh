@@ -18,7 +18,13 @@ __device__ __forceinline__ unsigned pack2(float lo, float hi) {
     }
 }
 
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+// x rounded to the operand type (round to nearest even); x - prec_round(x)
+// is the remainder that a second, "lo" operand carries.
+template <int PREC>
+__device__ __forceinline__ float prec_round(float x) {
+    if constexpr (PREC == 1) return __half2float(__float2half_rn(x));
+    else return __bfloat162float(__float2bfloat16_rn(x));
+}
 
 template <int PREC>
 __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {

@@ -26,10 +26,21 @@
 // twiddle table carries 2^-5 (contraction 1 grows values by at most 32),
 // and the rotation tables carry the inverse of both.
 //
-// BF16 form: every operand x is split into hi = bf16(x) and lo =
-// bf16(x - hi), and each product is hi.hi + hi.lo + lo.hi.
+// Split operands: an operand x is carried as hi = round(x) and lo =
+// round(x - hi) in the operand type, and a product as hi.hi + hi.lo + lo.hi,
+// which leaves an error of the order of the type's precision squared. A
+// strong tone makes one class sequence far larger than its neighbours in
+// the spectrum, and a single rounding of the DFT matrices or of the data
+// between the contractions puts an error of a few 1e-4 of the tone's
+// amplitude into every channel of the class: several 8-bit LSB next to a
+// tone that saturates. So both forms split the DFT matrices and the data
+// between the contractions. The FP16 form's input B is already an FP16
+// value (the intermediate is stored in FP16) and needs no split:
+// contraction 1 takes 2 products there, contraction 2 takes 3. The BF16
+// form splits its FP32 input as well (3 and 3).
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "fe_device.cuh"
 #include "fe_internal.cuh"
@@ -57,9 +68,9 @@ __device__ __forceinline__ int stage_slot(int k2) { return k2 + 8 * (k2 >> 5); }
 
 }  // namespace
 
-// shared memory: tables (hi; lo for BF16) + P/Q + gains + staging + row info
-size_t phase2_tc_smem_bytes(int precision) {
-    const int nl = precision == 2 ? 2 : 1;
+// shared memory: tables (hi and lo) + P/Q + gains + staging + row info
+size_t phase2_tc_smem_bytes(int) {
+    const int nl = 2;
     const size_t pq = (sizeof(float2) * 2 * kTcR * kPQ + 15) / 16 * 16;
     return sizeof(uint4) * 512 * (1 + 2 * nl) + pq + sizeof(float2) * 2 * kGainLd +
            sizeof(unsigned) * kStgLd * kTcR + (sizeof(long long) + sizeof(int)) * kTcR;
@@ -67,13 +78,12 @@ size_t phase2_tc_smem_bytes(int precision) {
 
 template <int PREC>
 __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(const Phase2Params p) {
-    constexpr bool LO = PREC == 2;
     extern __shared__ uint4 smu[];
     // plan table order: a1 [4 mt][4 kt][32], b2 [4 kt2][4 ntp][32], tw [4 mt][4 nt][32], a1 lo, b2 lo
     const uint4 *a1s = smu, *b2s = smu + 512;
     const float4 *tws = reinterpret_cast<const float4 *>(smu + 1024);
     const uint4 *a1l = smu + 1536, *b2l = smu + 2048;
-    float2 *pq = reinterpret_cast<float2 *>(smu + (LO ? 2560 : 1536));   // [2 kTcR][kPQ]
+    float2 *pq = reinterpret_cast<float2 *>(smu + 2560);                  // [2 kTcR][kPQ]
     float2 *gsm = pq + (2 * kTcR * kPQ + 1) / 2 * 2;                     // [2][kGainLd]
     unsigned *stg = reinterpret_cast<unsigned *>(gsm + 2 * kGainLd);     // [kTcR][kStgLd]
     long long *rowoff = reinterpret_cast<long long *>(stg + kStgLd * kTcR);
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
     const bool upper = (k1 != 0 && k1 != H1);
     const int nslot = upper ? kTcN2 : kTcN2 / 2;
 
-    for (int i = threadIdx.x; i < (LO ? 2560 : 1536); i += kTcThreads) smu[i] = __ldg(p.tc + i);
+    for (int i = threadIdx.x; i < 2560; i += kTcThreads) smu[i] = __ldg(p.tc + i);
     // rotation factors of each (pol, spectrum) sequence, angles over pi:
     //   P[c] = u exp(i pi (phi/pi - 2 delta (k1 + N1 c) / N)),
     //   Q[d] = exp(-i pi 2 delta 32 N1 d / N),  qu = exp(i pi (2 phi/pi - 2 delta)),
@@ -136,45 +146,40 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
         for (int pol = 0; pol < 2; pol++) {
             const int stream = ant * 2 + pol;
             const long long base = ((long long)(stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) + k1) * kTcN2;
-            // contraction 1; operand B of K tile kt is B[32 a + b] at
-            // a = 8 kt + 2 tq + h, b = 8 nt + g
-            float d1[4][4][4];
+            const float2 *pqs = pq + (pol * kTcR + r) * kPQ;
+            const float2 qu = pqs[64];
+            float2 *pre = p.prequant ? p.prequant + ((long long)stream * M + q0 + r) * n : nullptr;
+            // lane parts of the gain slot and staging slot of k2 = g + 32 tq + 16 mp + 8 h + 128 nt2
+            const float2 *gp = gsm + pol * kGainLd + g + 36 * tq;
+            unsigned short *sp = stg16 + 2 * (r * kStgLd + g + 40 * tq) + pol;
+            // Rows c = 16 mp + (0 .. 15) of Y' need only m tiles 2 mp and
+            // 2 mp + 1 of contraction 1, and give rows c of F: both
+            // contractions and the epilogue run per mp, so that only half of
+            // the first accumulator is live at a time.
 #pragma unroll
-            for (int mt = 0; mt < 4; mt++)
+            for (int mp = 0; mp < 2; mp++) {
+                // the lane's operands B of contraction 1, all four K tiles at once:
+                // K tile kt takes B[32 a + b] at a = 8 kt + 2 tq + h, b = 8 nt + g.
+                // FP16 form: the intermediate holds the (re, im) FP16 pairs the
+                // products take; BF16 form: FP32 pairs, split into hi and lo below.
+                using In = std::conditional_t<PREC == 1, unsigned, float2>;
+                In v[4][4][2];
+                {
+                    const In *src = reinterpret_cast<const In *>(p.A) + base;
 #pragma unroll
-                for (int nt = 0; nt < 4; nt++)
+                    for (int kt = 0; kt < 4; kt++)
 #pragma unroll
-                    for (int x = 0; x < 4; x++) d1[mt][nt][x] = 0.0f;
-            if constexpr (PREC == 1) {
-                // FP16 intermediate: B arrives as the (re, im) FP16 pairs the
-                // products take; all 32 of the lane's operands are loaded at once
-                const unsigned *srch = reinterpret_cast<const unsigned *>(p.A) + base;
-                unsigned vh[4][4][2];
+                        for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-                for (int kt = 0; kt < 4; kt++)
+                            for (int h = 0; h < 2; h++) v[kt][nt][h] = __ldg(src + 32 * (8 * kt + 2 * tq + h) + 8 * nt + g);
+                }
+                float d1[2][4][4];
+#pragma unroll
+                for (int i = 0; i < 2; i++)
 #pragma unroll
                     for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-                        for (int h = 0; h < 2; h++) vh[kt][nt][h] = __ldg(srch + 32 * (8 * kt + 2 * tq + h) + 8 * nt + g);
-#pragma unroll
-                for (int kt = 0; kt < 4; kt++) {
-#pragma unroll
-                    for (int mt = 0; mt < 4; mt++) {
-                        const uint4 A = a1s[(mt * 4 + kt) * 32 + lane];
-#pragma unroll
-                        for (int nt = 0; nt < 4; nt++) mma16816<PREC>(d1[mt][nt], A, vh[kt][nt][0], vh[kt][nt][1]);
-                    }
-                }
-            } else {
-                // FP32 intermediate (BF16 form: split into hi and lo here), one
-                // K tile at a time, the next tile's loads in flight during
-                // this tile's products
-                const float2 *src = p.A + base;
-                float2 v[4][2];
-#pragma unroll
-                for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                    for (int h = 0; h < 2; h++) v[nt][h] = __ldg(src + 32 * (2 * tq + h) + 8 * nt + g);
+                        for (int x = 0; x < 4; x++) d1[i][nt][x] = 0.0f;
 #pragma unroll
                 for (int kt = 0; kt < 4; kt++) {
                     unsigned bh[4][2], bl[4][2];
@@ -182,63 +187,46 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
                     for (int nt = 0; nt < 4; nt++)
 #pragma unroll
                         for (int h = 0; h < 2; h++) {
-                            const float2 x = v[nt][h];
-                            bh[nt][h] = pack2<PREC>(x.x, x.y);
-                            if constexpr (LO) bl[nt][h] = pack2<PREC>(x.x - bf16_round(x.x), x.y - bf16_round(x.y));
-                        }
-                    if (kt < 3) {
-#pragma unroll
-                        for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                            for (int h = 0; h < 2; h++)
-                                v[nt][h] = __ldg(src + 32 * (8 * (kt + 1) + 2 * tq + h) + 8 * nt + g);
-                    }
-#pragma unroll
-                    for (int mt = 0; mt < 4; mt++) {
-                        const uint4 A = a1s[(mt * 4 + kt) * 32 + lane];
-#pragma unroll
-                        for (int nt = 0; nt < 4; nt++) mma16816<PREC>(d1[mt][nt], A, bh[nt][0], bh[nt][1]);
-                        if constexpr (LO) {
-                            const uint4 Al = a1l[(mt * 4 + kt) * 32 + lane];
-#pragma unroll
-                            for (int nt = 0; nt < 4; nt++) {
-                                mma16816<PREC>(d1[mt][nt], A, bl[nt][0], bl[nt][1]);
-                                mma16816<PREC>(d1[mt][nt], Al, bh[nt][0], bh[nt][1]);
+                            if constexpr (PREC == 1) {
+                                bh[nt][h] = v[kt][nt][h];
+                            } else {
+                                const float2 x = v[kt][nt][h];
+                                bh[nt][h] = pack2<PREC>(x.x, x.y);
+                                bl[nt][h] = pack2<PREC>(x.x - prec_round<PREC>(x.x), x.y - prec_round<PREC>(x.y));
                             }
                         }
+#pragma unroll
+                    for (int i = 0; i < 2; i++) {
+                        const int mt = 2 * mp + i;
+                        const uint4 A = a1s[(mt * 4 + kt) * 32 + lane], Al = a1l[(mt * 4 + kt) * 32 + lane];
+#pragma unroll
+                        for (int nt = 0; nt < 4; nt++) {
+                            mma16816<PREC>(d1[i][nt], A, bh[nt][0], bh[nt][1]);
+                            mma16816<PREC>(d1[i][nt], Al, bh[nt][0], bh[nt][1]);
+                            if constexpr (PREC == 2) mma16816<PREC>(d1[i][nt], A, bl[nt][0], bl[nt][1]);
+                        }
                     }
                 }
-            }
-            // twiddle; lane (g, tq) then holds operand A of contraction 2 for
-            // m tile mp (rows c = 16 mp + g, + 8) and K tile kt2 (b = 8 kt2 + 2 tq, + 1):
-            // a0 = Y'[c][b], a1 = Y'[c + 8][b], a2 = Y'[c][b + 1], a3 = Y'[c + 8][b + 1]
-            unsigned ah[2][4][4], al[2][4][4];
+                // twiddle; lane (g, tq) then holds operand A of contraction 2
+                // for K tile kt2 (b = 8 kt2 + 2 tq, + 1) and rows c = 16 mp + g, + 8:
+                // a0 = Y'[c][b], a1 = Y'[c + 8][b], a2 = Y'[c][b + 1], a3 = Y'[c + 8][b + 1]
+                unsigned ah[4][4], al[4][4];
 #pragma unroll
-            for (int mt = 0; mt < 4; mt++) {
-                const int mp = mt >> 1, i = mt & 1;
+                for (int i = 0; i < 2; i++) {
+                    const int mt = 2 * mp + i;
 #pragma unroll
-                for (int nt = 0; nt < 4; nt++) {
-                    const float4 t = tws[(mt * 4 + nt) * 32 + lane];
-                    const float2 y0 = cmul(make_float2(d1[mt][nt][0], d1[mt][nt][2]), make_float2(t.x, t.y));
-                    const float2 y1 = cmul(make_float2(d1[mt][nt][1], d1[mt][nt][3]), make_float2(t.z, t.w));
-                    ah[mp][nt][i] = pack2<PREC>(y0.x, y0.y);
-                    ah[mp][nt][2 + i] = pack2<PREC>(y1.x, y1.y);
-                    if constexpr (LO) {
-                        al[mp][nt][i] = pack2<PREC>(y0.x - bf16_round(y0.x), y0.y - bf16_round(y0.y));
-                        al[mp][nt][2 + i] = pack2<PREC>(y1.x - bf16_round(y1.x), y1.y - bf16_round(y1.y));
+                    for (int nt = 0; nt < 4; nt++) {
+                        const float4 t = tws[(mt * 4 + nt) * 32 + lane];
+                        const float2 y0 = cmul(make_float2(d1[i][nt][0], d1[i][nt][2]), make_float2(t.x, t.y));
+                        const float2 y1 = cmul(make_float2(d1[i][nt][1], d1[i][nt][3]), make_float2(t.z, t.w));
+                        ah[nt][i] = pack2<PREC>(y0.x, y0.y);
+                        ah[nt][2 + i] = pack2<PREC>(y1.x, y1.y);
+                        al[nt][i] = pack2<PREC>(y0.x - prec_round<PREC>(y0.x), y0.y - prec_round<PREC>(y0.y));
+                        al[nt][2 + i] = pack2<PREC>(y1.x - prec_round<PREC>(y1.x), y1.y - prec_round<PREC>(y1.y));
                     }
                 }
-            }
-            const float2 *pqs = pq + (pol * kTcR + r) * kPQ;
-            const float2 qu = pqs[64];
-            float2 *pre = p.prequant ? p.prequant + ((long long)stream * M + q0 + r) * n : nullptr;
-            // lane parts of the gain slot and staging slot of k2 = g + 32 tq + 16 mp + 8 h + 128 nt2
-            const float2 *gp = gsm + pol * kGainLd + g + 36 * tq;
-            unsigned short *sp = stg16 + 2 * (r * kStgLd + g + 40 * tq) + pol;
-            // contraction 2 and the epilogue, per m tile and per half of the
-            // output columns (d < 16: lower-half channels, d >= 16: upper)
-#pragma unroll
-            for (int mp = 0; mp < 2; mp++) {
+                // contraction 2 and the epilogue per half of the output
+                // columns (d < 16: lower-half channels, d >= 16: upper)
 #pragma unroll
                 for (int half = 0; half < 2; half++) {
                     if (half == 1 && !upper) break;
@@ -253,15 +241,13 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
                         for (int jp = 0; jp < 2; jp++) {
                             const int ntp = 2 * half + jp;
                             const uint4 B = b2s[(kt2 * 4 + ntp) * 32 + lane];
-                            mma16816<PREC>(d2[2 * jp], ah[mp][kt2], B.x, B.y);
-                            mma16816<PREC>(d2[2 * jp + 1], ah[mp][kt2], B.z, B.w);
-                            if constexpr (LO) {
-                                const uint4 Bl = b2l[(kt2 * 4 + ntp) * 32 + lane];
-                                mma16816<PREC>(d2[2 * jp], ah[mp][kt2], Bl.x, Bl.y);
-                                mma16816<PREC>(d2[2 * jp + 1], ah[mp][kt2], Bl.z, Bl.w);
-                                mma16816<PREC>(d2[2 * jp], al[mp][kt2], B.x, B.y);
-                                mma16816<PREC>(d2[2 * jp + 1], al[mp][kt2], B.z, B.w);
-                            }
+                            const uint4 Bl = b2l[(kt2 * 4 + ntp) * 32 + lane];
+                            mma16816<PREC>(d2[2 * jp], ah[kt2], B.x, B.y);
+                            mma16816<PREC>(d2[2 * jp + 1], ah[kt2], B.z, B.w);
+                            mma16816<PREC>(d2[2 * jp], ah[kt2], Bl.x, Bl.y);
+                            mma16816<PREC>(d2[2 * jp + 1], ah[kt2], Bl.z, Bl.w);
+                            mma16816<PREC>(d2[2 * jp], al[kt2], B.x, B.y);
+                            mma16816<PREC>(d2[2 * jp + 1], al[kt2], B.z, B.w);
                         }
                     }
                     // rotation, gain, requantisation into the staging cells
@@ -349,13 +335,14 @@ double b2_value(int k, int n) {
 }
 
 // Two matrix entries as one 32-bit operand register (first entry in the low
-// half); part 0 is the rounded value, part 1 the BF16 remainder.
+// half); part 0 is the rounded value, part 1 the rounded remainder.
 unsigned pack_pair(double v0, double v1, int precision, int part) {
     unsigned short h[2];
     const double v[2] = {v0, v1};
     for (int i = 0; i < 2; i++) {
         if (precision == 1) {
-            const __half x = __float2half_rn((float)v[i]);
+            __half x = __float2half_rn((float)v[i]);
+            if (part) x = __float2half_rn((float)(v[i] - (double)__half2float(x)));
             std::memcpy(&h[i], &x, 2);
         } else {
             __nv_bfloat16 x = __float2bfloat16_rn((float)v[i]);
@@ -370,7 +357,7 @@ unsigned pack_pair(double v0, double v1, int precision, int part) {
 
 void build_phase2_tc_tables(int precision, uint4 *out) {
     std::memset(out, 0, sizeof(uint4) * kPhase2TcTableLen);
-    for (int part = 0; part < (precision == 2 ? 2 : 1); part++) {
+    for (int part = 0; part < 2; part++) {
         uint4 *a1 = out + (part ? 1536 : 0), *b2 = out + (part ? 2048 : 512);
         for (int lane = 0; lane < 32; lane++) {
             const int g = lane >> 2, q = lane & 3;
