@@ -152,27 +152,31 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
             // lane parts of the gain slot and staging slot of k2 = g + 32 tq + 16 mp + 8 h + 128 nt2
             const float2 *gp = gsm + pol * kGainLd + g + 36 * tq;
             unsigned short *sp = stg16 + 2 * (r * kStgLd + g + 40 * tq) + pol;
+            // The lane's operands B of contraction 1, all four K tiles: K tile
+            // kt takes B[32 a + b] at a = 8 kt + 2 tq + h, b = 8 nt + g. FP16
+            // form: the intermediate holds the (re, im) FP16 pairs the products
+            // take, and they are loaded again for the second row half (128
+            // registers a thread leave no room to keep them); BF16 form: FP32
+            // pairs, split into hi and lo below, loaded once.
+            using In = std::conditional_t<PREC == 1, unsigned, float2>;
+            In v[4][4][2];
+            const In *src = reinterpret_cast<const In *>(p.A) + base;
+            auto load_b = [&](In (&vv)[4][4][2]) {
+#pragma unroll
+                for (int kt = 0; kt < 4; kt++)
+#pragma unroll
+                    for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                        for (int h = 0; h < 2; h++) vv[kt][nt][h] = __ldg(src + 32 * (8 * kt + 2 * tq + h) + 8 * nt + g);
+            };
+            if constexpr (PREC == 2) load_b(v);
             // Rows c = 16 mp + (0 .. 15) of Y' need only m tiles 2 mp and
             // 2 mp + 1 of contraction 1, and give rows c of F: both
             // contractions and the epilogue run per mp, so that only half of
             // the first accumulator is live at a time.
 #pragma unroll
             for (int mp = 0; mp < 2; mp++) {
-                // the lane's operands B of contraction 1, all four K tiles at once:
-                // K tile kt takes B[32 a + b] at a = 8 kt + 2 tq + h, b = 8 nt + g.
-                // FP16 form: the intermediate holds the (re, im) FP16 pairs the
-                // products take; BF16 form: FP32 pairs, split into hi and lo below.
-                using In = std::conditional_t<PREC == 1, unsigned, float2>;
-                In v[4][4][2];
-                {
-                    const In *src = reinterpret_cast<const In *>(p.A) + base;
-#pragma unroll
-                    for (int kt = 0; kt < 4; kt++)
-#pragma unroll
-                        for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                            for (int h = 0; h < 2; h++) v[kt][nt][h] = __ldg(src + 32 * (8 * kt + 2 * tq + h) + 8 * nt + g);
-                }
+                if constexpr (PREC == 1) load_b(v);
                 float d1[2][4][4];
 #pragma unroll
                 for (int i = 0; i < 2; i++)
