@@ -7,17 +7,23 @@
 //   Y[c][b]     = sum_a exp(-2 pi i c a / 32) B[32 a + b]
 //   Y'[c][b]    = exp(-2 pi i c b / 1024) Y[c][b]
 //   F[c + 32 d] = sum_b Y'[c][b] exp(-2 pi i d b / 32).
-// Lane b loads B[32 a + b] for every a (coalesced), does the first 32-point
-// DFT in registers, applies the twiddle, and writes Y'[.][b] into the warp's
-// padded shared-memory tile; after one transpose lane c holds Y'[c][.] and
-// does the second 32-point DFT in registers, leaving F[c + 32 d] for every d.
-// One shared-memory round trip per point instead of one per radix pass.
+// The sequence arrives in the warp's shared-memory buffer by cp.async; lane
+// b reads B[32 a + b] for every a, does the first 32-point DFT in registers,
+// applies the twiddle, and writes Y'[.][b] back into the buffer (XOR
+// swizzle); after that transpose lane c holds Y'[c][.] and does the second
+// 32-point DFT in registers, leaving F[c + 32 d] for every d. One
+// shared-memory round trip per point instead of one per radix pass.
 //
-// A CTA owns one first-stage class k1 and 4 consecutive spectra; warp w
-// computes spectrum w / 2, polarisation w % 2. Channel mapping, rotation
-// split and upper-half conjugation are those of the other second stages:
+// A work item is one first-stage class k1 and 4 consecutive spectra of one
+// antenna; warp w computes spectrum w / 2, polarisation w % 2. The kernel is
+// persistent (a contiguous range of items per CTA) so that each warp's next
+// sequence is in flight while the current one is finished. Channel mapping,
+// rotation split and upper-half conjugation are those of the other second
+// stages:
 // slot k2 is channel k1 + N1 k2 for k2 < 512, and for k2 >= 512 (classes
 // k1 = 1 .. N1/2 - 1 only) the conjugate of channel N - (k1 + N1 k2).
+#include <algorithm>
+
 #include "fe_device.cuh"
 #include "fe_internal.cuh"
 
@@ -26,9 +32,8 @@ namespace fe {
 namespace {
 
 constexpr int kWThreads = 256;
-constexpr int kWR = 4;        // spectra per CTA (two warps each)
+constexpr int kWR = 4;        // spectra per work item (two warps each)
 constexpr int kWN2 = 1024;
-constexpr int kTLd = 33;      // transpose tile row stride in float2 (conflict-free both ways)
 constexpr int kWPQ = 65;      // per sequence: P[32], Q[32], qu
 
 // 32-bit word of output cell (slot k2, spectrum r) in the staging buffer: the
@@ -36,144 +41,207 @@ constexpr int kWPQ = 65;      // per sequence: P[32], Q[32], qu
 // store (consecutive k2) and of a corner-turn read hit 32 banks.
 __device__ __forceinline__ int stg_word(int k2, int r) { return k2 * kWR + (r ^ ((k2 >> 3) & 3)); }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// A work item is (antenna, class k1, group of kWR consecutive spectra), in
+// that order; item -> its fields.
+struct WItem {
+    int ant, k1, q0;
+};
+__device__ __forceinline__ WItem witem(const Phase2Params &p, int it, int H1, int G) {
+    const int per_ant = (H1 + 1) * G;
+    WItem w;
+    w.ant = it / per_ant;
+    const int rem = it - w.ant * per_ant;
+    w.k1 = rem / G;
+    w.q0 = p.q_begin + (rem - w.k1 * G) * kWR;
+    return w;
+}
+
 }  // namespace
 
 size_t phase2w_smem_bytes() {
-    return sizeof(float2) * (8 * 32 * kTLd)    // transpose tiles (afterwards: the staging)
-           + sizeof(float2) * 2 * kWN2         // gains of the CTA's slots
-           + sizeof(float2) * 2 * kWR * kWPQ   // rotation factors
+    return sizeof(float2) * 8 * kWN2              // per-warp sequence buffers (also the transpose tiles)
+           + sizeof(unsigned) * kWN2 * kWR        // output staging
+           + sizeof(float2) * 2 * kWN2            // gains of the item's slots
+           + sizeof(float2) * 2 * kWR * kWPQ      // rotation factors
+           + sizeof(float2) * 32 * 32             // twiddles exp(-2 pi i c b / 1024), [c][b]
            + (sizeof(long long) + sizeof(int)) * kWR;
 }
 
-__global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p) {
+// Persistent: each CTA takes a contiguous range of work items. Warp w owns
+// sequence (spectrum w / 2, polarisation w % 2) of every item; its 8 KB
+// sequence arrives in its shared-memory buffer by cp.async, and the copy of
+// the next item's sequence is issued as soon as the buffer has been read
+// (after the transpose), so it runs under this item's second DFT, epilogue
+// and corner turn.
+__global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, int n_ant) {
     extern __shared__ float2 smw[];
-    float2 *tbuf = smw;                                            // [8][32][kTLd]
-    unsigned *stg = reinterpret_cast<unsigned *>(smw);             // [kWN2][kWR], after the FFTs
-    float2 *gsm = smw + 8 * 32 * kTLd;                             // [2][kWN2]
-    float2 *pq = gsm + 2 * kWN2;                                   // [2 kWR][kWPQ]
-    long long *rowoff = reinterpret_cast<long long *>(pq + 2 * kWR * kWPQ);
+    float2 *sbuf = smw;                                                   // [8][kWN2]
+    unsigned *stg = reinterpret_cast<unsigned *>(smw + 8 * kWN2);         // [kWN2][kWR]
+    float2 *gsm = reinterpret_cast<float2 *>(stg + kWN2 * kWR);           // [2][kWN2]
+    float2 *pq = gsm + 2 * kWN2;                                          // [2 kWR][kWPQ]
+    float2 *twm = pq + 2 * kWR * kWPQ;                                    // [32 c][32 b]
+    long long *rowoff = reinterpret_cast<long long *>(twm + 32 * 32);
     int *rowstride = reinterpret_cast<int *>(rowoff + kWR);
 
-    const int k1 = blockIdx.x, ant = blockIdx.z;
-    const int q0 = p.q_begin + blockIdx.y * kWR;
-    const int M = p.M, Rv = min(kWR, p.q_begin + p.q_count - q0);
-    const int N1 = p.N1, H1 = N1 / 2, N = p.N, n = N / 2, S_ = p.S;
-    const bool upper = (k1 != 0 && k1 != H1);
-    const int nslot = upper ? kWN2 : kWN2 / 2;
+    const int M = p.M, N1 = p.N1, H1 = N1 / 2, N = p.N, n = N / 2, S_ = p.S;
+    const int G = (p.q_count + kWR - 1) / kWR;
+    const int n_items = n_ant * (H1 + 1) * G;
+    const int per = (n_items + gridDim.x - 1) / gridDim.x;
+    const int it0 = blockIdx.x * per, it1 = min(n_items, it0 + per);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = warp >> 1, pol = warp & 1, stream = ant * 2 + pol;
-    const bool active = r < Rv;
+    const int r = warp >> 1, pol = warp & 1;
+    float2 *mybuf = sbuf + warp * kWN2;
 
-    // this warp's sequence: lane b takes B[32 a + b] (loads issued before the set-up)
-    float2 z[32];
-    if (active) {
-        const float2 *src =
-            p.A + ((long long)(stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) + k1) * kWN2 + lane;
+    // this warp's sequence of item it into its buffer (lane: 16-byte chunks lane + 32 i)
+    auto fetch = [&](int it) {
+        const WItem w = witem(p, it, H1, G);
+        if (w.q0 + r < p.q_begin + p.q_count) {
+            const float2 *src =
+                p.A + ((long long)((w.ant * 2 + pol) * p.a_spectra + (w.q0 - p.q_begin) + r) * (H1 + 1) + w.k1) * kWN2;
 #pragma unroll
-        for (int a = 0; a < 32; a++) z[a] = __ldg(src + 32 * a);
-    }
-
-    // rotation factors of each (pol, spectrum) sequence, angles over pi:
-    //   P[c] = exp(i pi (phi/pi - 2 delta (k1 + N1 c) / N)),
-    //   Q[d] = exp(-i pi 2 delta 32 N1 d / N),  qu = exp(i pi (2 phi/pi - 2 delta)),
-    // so that channel k1 + N1 k2 (k2 = c + 32 d) is P[c] Q[d] F[k2] and the
-    // upper-half channel N - (k1 + N1 k2) is qu conj(P[c] Q[d] F[k2]).
-    const float inv = 2.0f / (float)N;
-    for (int e = threadIdx.x; e < 2 * kWR * kWPQ; e += kWThreads) {
-        const int sq = e / kWPQ, j = e - sq * kWPQ;
-        const int ps = sq / kWR, rs = sq % kWR;
-        if (rs >= Rv) continue;
-        const float2 f = p.ftab[(long long)(ant * 2 + ps) * M + q0 + rs];   // (delta, phi / pi)
-        const int c = j & 31;
-        float ang;
-        if (j < 32) ang = f.y - f.x * (float)(k1 + N1 * c) * inv;
-        else if (j < 64) ang = -f.x * (float)(32 * N1 * c) * inv;
-        else ang = 2.0f * f.y - 2.0f * f.x;
-        float sn, cs;
-        sincospif(ang, &sn, &cs);
-        pq[e] = make_float2(cs, sn);
-    }
-    for (int e = threadIdx.x; e < 2 * kWN2; e += kWThreads) {
-        const int ps = e / kWN2, k2 = e % kWN2;
-        const int kc = k1 + N1 * k2;
-        const int k = k2 >= kWN2 / 2 ? N - kc : kc;
-        gsm[e] = (k >= 0 && k < n) ? __ldg(p.gains + (long long)(ant * 2 + ps) * n + k) : make_float2(0.f, 0.f);
-    }
-    if ((int)threadIdx.x < Rv) {
-        const int q = q0 + threadIdx.x;
-        const int h = q / S_, s = q - h * S_;
-        const int Sh = min(S_, M - h * S_);
-        rowoff[threadIdx.x] = (long long)h * S_ * n * 4 + s * 4;
-        rowstride[threadIdx.x] = Sh * 4;
-    }
-    __syncthreads();
-
-    if (active) {
-        fft_regc<32>(z);                                  // z[c] = Y[c][lane]
-#pragma unroll
-        for (int c = 1; c < 32; c++) z[c] = cmul(z[c], __ldg(p.tw2 + ((c * lane) & (kWN2 - 1))));
-        float2 *tb = tbuf + warp * 32 * kTLd;
-#pragma unroll
-        for (int c = 0; c < 32; c++) tb[c * kTLd + lane] = z[c];
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < 32; b++) z[b] = tb[lane * kTLd + b];
-        fft_regc<32>(z);                                  // z[d] = F[lane + 32 d]
-    }
-    __syncthreads();   // every tile read: the tiles become the staging buffer
-
-    if (active) {
-        const float2 *pqs = pq + (pol * kWR + r) * kWPQ;
-        const float2 P = pqs[lane], qu = pqs[64];
-        const float2 Pu = cmul(qu, cconj(P));
-        const float2 *gp = gsm + pol * kWN2;
-        unsigned short *stg16 = reinterpret_cast<unsigned short *>(stg);
-        float2 *pre = p.prequant ? p.prequant + ((long long)stream * M + q0 + r) * n : nullptr;
-        // lower half (d < 16): channel k1 + N1 k2
-#pragma unroll
-        for (int d = 0; d < 16; d++) {
-            const int k2 = lane + 32 * d;
-            const float2 y = cmul(gp[k2], cmul(cmul(P, pqs[32 + d]), z[d]));
-            if (pre) pre[k1 + N1 * k2] = y;
-            stg16[2 * stg_word(k2, r) + pol] =
-                (unsigned short)__byte_perm((unsigned)quant8(y.x), (unsigned)quant8(y.y), 0x0040u);
+            for (int i = 0; i < 16; i++) cp_async16(mybuf + 2 * (lane + 32 * i), src + 2 * (lane + 32 * i));
         }
-        if (upper) {
-            // upper half (d >= 16): channel N - (k1 + N1 k2)
+        cp_async_commit();
+    };
+    if (it0 < it1) fetch(it0);
+    // the twiddle of (c, b) at [c][b]: a warp's 32 lanes (b) read 32 consecutive entries
+    for (int e = threadIdx.x; e < 32 * 32; e += kWThreads) twm[e] = __ldg(p.tw2 + (((e >> 5) * (e & 31)) & (kWN2 - 1)));
+
+    int cur = -1;   // (ant, k1) of the gains in gsm
+    for (int it = it0; it < it1; it++) {
+        const WItem w = witem(p, it, H1, G);
+        const int ant = w.ant, k1 = w.k1, q0 = w.q0;
+        const int Rv = min(kWR, p.q_begin + p.q_count - q0);
+        const bool upper = (k1 != 0 && k1 != H1);
+        const int nslot = upper ? kWN2 : kWN2 / 2;
+        const bool active = r < Rv;
+        const int stream = ant * 2 + pol;
+
+        __syncthreads();   // the previous item's corner turn is done with stg, rowoff and the tables
+        // rotation factors of each (pol, spectrum) sequence, angles over pi:
+        //   P[c] = exp(i pi (phi/pi - 2 delta (k1 + N1 c) / N)),
+        //   Q[d] = exp(-i pi 2 delta 32 N1 d / N),  qu = exp(i pi (2 phi/pi - 2 delta)),
+        // so that channel k1 + N1 k2 (k2 = c + 32 d) is P[c] Q[d] F[k2] and the
+        // upper-half channel N - (k1 + N1 k2) is qu conj(P[c] Q[d] F[k2]).
+        const float inv = 2.0f / (float)N;
+        for (int e = threadIdx.x; e < 2 * kWR * kWPQ; e += kWThreads) {
+            const int sq = e / kWPQ, j = e - sq * kWPQ;
+            const int ps = sq / kWR, rs = sq % kWR;
+            if (rs >= Rv) continue;
+            const float2 f = p.ftab[(long long)(ant * 2 + ps) * M + q0 + rs];   // (delta, phi / pi)
+            const int c = j & 31;
+            float ang;
+            if (j < 32) ang = f.y - f.x * (float)(k1 + N1 * c) * inv;
+            else if (j < 64) ang = -f.x * (float)(32 * N1 * c) * inv;
+            else ang = 2.0f * f.y - 2.0f * f.x;
+            float sn, cs;
+            sincospif(ang, &sn, &cs);
+            pq[e] = make_float2(cs, sn);
+        }
+        if (ant * 1024 + k1 != cur) {
+            cur = ant * 1024 + k1;
+            for (int e = threadIdx.x; e < 2 * kWN2; e += kWThreads) {
+                const int ps = e / kWN2, k2 = e % kWN2;
+                const int kc = k1 + N1 * k2;
+                const int k = k2 >= kWN2 / 2 ? N - kc : kc;
+                gsm[e] = (k >= 0 && k < n) ? __ldg(p.gains + (long long)(ant * 2 + ps) * n + k) : make_float2(0.f, 0.f);
+            }
+        }
+        if ((int)threadIdx.x < Rv) {
+            const int q = q0 + threadIdx.x;
+            const int h = q / S_, s = q - h * S_;
+            const int Sh = min(S_, M - h * S_);
+            rowoff[threadIdx.x] = (long long)h * S_ * n * 4 + s * 4;
+            rowstride[threadIdx.x] = Sh * 4;
+        }
+
+        // With t2 = 32 a + b and k2 = c + 32 d: lane b takes B[32 a + b] for
+        // every a, does the first 32-point DFT, applies the twiddle and writes
+        // Y'[c][b] back to the buffer at c * 32 + (b ^ c) (conflict-free both
+        // ways); after the transpose lane c holds Y'[c][.].
+        cp_async_wait_all();
+        __syncwarp();
+        float2 z[32];
+        if (active) {
 #pragma unroll
-            for (int d = 16; d < 32; d++) {
+            for (int a = 0; a < 32; a++) z[a] = mybuf[32 * a + lane];
+            __syncwarp();
+            fft_regc<32>(z);                                  // z[c] = Y[c][lane]
+#pragma unroll
+            for (int c = 1; c < 32; c++) z[c] = cmul(z[c], twm[32 * c + lane]);
+#pragma unroll
+            for (int c = 0; c < 32; c++) mybuf[32 * c + (lane ^ c)] = z[c];
+            __syncwarp();
+#pragma unroll
+            for (int b = 0; b < 32; b++) z[b] = mybuf[32 * lane + (b ^ lane)];
+        }
+        __syncwarp();
+        if (it + 1 < it1) fetch(it + 1);                      // the buffer is free again
+        __syncthreads();                                      // tables and row info ready
+
+        if (active) {
+            fft_regc<32>(z);                                  // z[d] = F[lane + 32 d]
+            const float2 *pqs = pq + (pol * kWR + r) * kWPQ;
+            const float2 P = pqs[lane], qu = pqs[64];
+            const float2 Pu = cmul(qu, cconj(P));
+            const float2 *gp = gsm + pol * kWN2;
+            unsigned short *stg16 = reinterpret_cast<unsigned short *>(stg);
+            float2 *pre = p.prequant ? p.prequant + ((long long)stream * M + q0 + r) * n : nullptr;
+            // lower half (d < 16): channel k1 + N1 k2
+#pragma unroll
+            for (int d = 0; d < 16; d++) {
                 const int k2 = lane + 32 * d;
-                const float2 y = cmul(gp[k2], cmul(cmul(Pu, cconj(pqs[32 + d])), cconj(z[d])));
-                if (pre) pre[N - (k1 + N1 * k2)] = y;
+                const float2 y = cmul(gp[k2], cmul(cmul(P, pqs[32 + d]), z[d]));
+                if (pre) pre[k1 + N1 * k2] = y;
                 stg16[2 * stg_word(k2, r) + pol] =
                     (unsigned short)__byte_perm((unsigned)quant8(y.x), (unsigned)quant8(y.y), 0x0040u);
             }
+            if (upper) {
+                // upper half (d >= 16): channel N - (k1 + N1 k2)
+#pragma unroll
+                for (int d = 16; d < 32; d++) {
+                    const int k2 = lane + 32 * d;
+                    const float2 y = cmul(gp[k2], cmul(cmul(Pu, cconj(pqs[32 + d])), cconj(z[d])));
+                    if (pre) pre[N - (k1 + N1 * k2)] = y;
+                    stg16[2 * stg_word(k2, r) + pol] =
+                        (unsigned short)__byte_perm((unsigned)quant8(y.x), (unsigned)quant8(y.y), 0x0040u);
+                }
+            }
         }
-    }
-    __syncthreads();
+        __syncthreads();
 
-    // corner turn: cell (slot k2, spectrum r) -> heap row of channel k; four
-    // spectra of a slot with one 16-byte store when they share a heap and the
-    // row is 16-byte aligned
-    int8_t *out = p.out + (long long)ant * M * n * 4;
-    const bool vec = Rv == kWR && S_ % 4 == 0 && rowstride[0] % 16 == 0;
-    if (vec) {
-        for (int k2 = threadIdx.x; k2 < nslot; k2 += kWThreads) {
-            const int kc = k1 + N1 * k2;
-            const int k = k2 >= kWN2 / 2 ? N - kc : kc;
-            const uint4 v = make_uint4(stg[stg_word(k2, 0)], stg[stg_word(k2, 1)], stg[stg_word(k2, 2)],
-                                       stg[stg_word(k2, 3)]);
-            *reinterpret_cast<uint4 *>(out + rowoff[0] + (long long)k * rowstride[0]) = v;
-        }
-    } else {
-        for (int e = threadIdx.x; e < nslot * kWR; e += kWThreads) {
-            const int k2 = e / kWR, rr = e % kWR;
-            if (rr >= Rv) continue;
-            const int kc = k1 + N1 * k2;
-            const int k = k2 >= kWN2 / 2 ? N - kc : kc;
-            *reinterpret_cast<unsigned *>(out + rowoff[rr] + (long long)k * rowstride[rr]) = stg[stg_word(k2, rr)];
+        // corner turn: cell (slot k2, spectrum r) -> heap row of channel k; four
+        // spectra of a slot with one 16-byte store when they share a heap and the
+        // row is 16-byte aligned
+        int8_t *out = p.out + (long long)ant * M * n * 4;
+        const bool vec = Rv == kWR && S_ % 4 == 0 && rowstride[0] % 16 == 0;
+        if (vec) {
+            for (int k2 = threadIdx.x; k2 < nslot; k2 += kWThreads) {
+                const int kc = k1 + N1 * k2;
+                const int k = k2 >= kWN2 / 2 ? N - kc : kc;
+                const uint4 v = make_uint4(stg[stg_word(k2, 0)], stg[stg_word(k2, 1)], stg[stg_word(k2, 2)],
+                                           stg[stg_word(k2, 3)]);
+                *reinterpret_cast<uint4 *>(out + rowoff[0] + (long long)k * rowstride[0]) = v;
+            }
+        } else {
+            for (int e = threadIdx.x; e < nslot * kWR; e += kWThreads) {
+                const int k2 = e / kWR, rr = e % kWR;
+                if (rr >= Rv) continue;
+                const int kc = k1 + N1 * k2;
+                const int k = k2 >= kWN2 / 2 ? N - kc : kc;
+                *reinterpret_cast<unsigned *>(out + rowoff[rr] + (long long)k * rowstride[rr]) =
+                    stg[stg_word(k2, rr)];
+            }
         }
     }
+    cp_async_wait_all();   // nothing is left in flight when the CTA exits
 }
 
 cudaError_t launch_phase2w(const Phase2Params &p, int n_ant, cudaStream_t s) {
@@ -181,8 +249,15 @@ cudaError_t launch_phase2w(const Phase2Params &p, int n_ant, cudaStream_t s) {
     const size_t smem = phase2w_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_phase2w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(p.N1 / 2 + 1, (p.q_count + kWR - 1) / kWR, n_ant);
-    k_phase2w<<<grid, kWThreads, smem, s>>>(p);
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase2w, kWThreads, smem)) != cudaSuccess)
+        return e;
+    const long long items = (long long)n_ant * (p.N1 / 2 + 1) * ((p.q_count + kWR - 1) / kWR);
+    if (items <= 0) return cudaSuccess;
+    const int ctas = (int)std::min<long long>(items, (long long)sms * std::max(per_sm, 1));
+    k_phase2w<<<ctas, kWThreads, smem, s>>>(p, n_ant);
     return cudaGetLastError();
 }
 
