@@ -57,6 +57,26 @@ def test_config2_shape_random_delays_and_gains():
         _report("cfg2-shape", compare_call(s, c, M, S, n, T, delays, gains))
 
 
+def test_persistent_second_stage_with_several_items_per_cta():
+    """The FP32 1024-point second stage is persistent (at most two CTAs per
+    SM, each taking every gridDim-th work item of 4 spectra x 2 pols of one
+    class k1). n = 4096 (N1 = 8: 5 classes) with 3 antennas and 257 spectra
+    per call gives 3 x 5 x 65 = 975 items, more than the resident CTAs, so
+    CTAs run several items with the next item's sequences prefetched, and
+    the last group of each class is ragged (1 spectrum)."""
+    n, T, M = 4096, 16, 257
+    L = 2 * n * M
+    g = np.random.default_rng(11)
+    s = streams(synth.SEED_BASE + 12, 3, 2 * L, 30.0, tones=[(0.3173, 80.0, 0.2)])
+    delays = [[[Seg(delay=float(g.uniform(0, 60)), rate=3e-9, phase=float(g.uniform(0, 6.28)))] for _ in range(2)]
+              for _ in range(3)]
+    gains = synth.random_gains(13, 6, n).reshape(3, 2, n)
+    gains = [[gains[a, p] for p in range(2)] for a in range(3)]
+    res, M2, S = run_gpu(s, n, T, L, 2, delays, gains, S=64, D=64, taps=False)
+    for c in res:
+        _report("persistent second stage, 975 items", compare_call(s, c, M2, S, n, T, delays, gains))
+
+
 @pytest.mark.parametrize("n,T,M", [(32768, 4, 12), (16384, 8, 20), (4096, 16, 33), (2048, 32, 9)])
 def test_other_fft_splits(n, T, M):
     L = 2 * n * M
