@@ -55,10 +55,15 @@ typedef enum {
 
 /* Precision forms. The reduced-precision forms run the N2 = 1024-point
  * second DFT stage as two 32-point DFT contractions on tensor cores (FP32
- * accumulation; BF16 operands split into hi + lo parts); they need a split
- * with N2 = 1024, i.e. n_channels >= 4096 (FENGINE_EUNSUPPORTED otherwise).
+ * accumulation). The DFT matrices and the data between the contractions are
+ * carried as hi + lo operand pairs (and the BF16 form's FP32 input too), so
+ * that a strong tone does not leave errors of more than a fraction of an
+ * 8-bit LSB in the other channels of its class; the FP16 form stores the
+ * intermediate between the two phases as FP16 pairs. They need a split with
+ * N2 = 1024, i.e. n_channels >= 4096 (FENGINE_EUNSUPPORTED otherwise).
  * Pre-quantisation spectra stay within 2e-3 relative RMS of the FP64
- * oracle (measured: FP16 3.7e-4, BF16 5.2e-6). */
+ * oracle (measured: FP16 2.1-2.3e-4, BF16 4.6-5.2e-6), 8-bit outputs within
+ * 1 LSB. */
 typedef enum {
     FENGINE_FP32 = 0,    /* FP32 FIR and FFT on CUDA cores */
     FENGINE_TC_FP16 = 1, /* reduced-precision form (FP16 operands, FP32 accumulation) */
