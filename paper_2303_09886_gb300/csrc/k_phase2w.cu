@@ -71,7 +71,7 @@ size_t phase2w_smem_bytes() {
            + sizeof(float2) * 2 * kWN2            // gains of the item's slots
            + sizeof(float2) * 2 * kWR * kWPQ      // rotation factors
            + sizeof(float2) * 32 * 32             // twiddles exp(-2 pi i c b / 1024), [c][b]
-           + (sizeof(long long) + sizeof(int)) * kWR;
+           + (sizeof(long long) + sizeof(int)) * 2 * kWR;   // row info, two items
 }
 
 // Persistent: each CTA takes a contiguous range of work items. Warp w owns
@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
     float2 *gsm = reinterpret_cast<float2 *>(stg + kWN2 * kWR);           // [2][kWN2]
     float2 *pq = gsm + 2 * kWN2;                                          // [2 kWR][kWPQ]
     float2 *twm = pq + 2 * kWR * kWPQ;                                    // [32 c][32 b]
-    long long *rowoff = reinterpret_cast<long long *>(twm + 32 * 32);
-    int *rowstride = reinterpret_cast<int *>(rowoff + kWR);
+    long long *rowoff_all = reinterpret_cast<long long *>(twm + 32 * 32);   // [2][kWR]
+    int *rowstride_all = reinterpret_cast<int *>(rowoff_all + 2 * kWR);       // [2][kWR]
 
     const int M = p.M, N1 = p.N1, H1 = N1 / 2, N = p.N, n = N / 2, S_ = p.S;
     const int G = (p.q_count + kWR - 1) / kWR;
@@ -113,9 +113,14 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
     if (it0 < it1) fetch(it0);
     // the twiddle of (c, b) at [c][b]: a warp's 32 lanes (b) read 32 consecutive entries
     for (int e = threadIdx.x; e < 32 * 32; e += kWThreads) twm[e] = __ldg(p.tw2 + (((e >> 5) * (e & 31)) & (kWN2 - 1)));
+    __syncthreads();   // the twiddles are read before the first item's barrier
 
     int cur = -1;   // (ant, k1) of the gains in gsm
     for (int it = it0; it < it1; it++) {
+        // row info alternates between two slots: the previous item's corner
+        // turn may still read its slot while this item's is written
+        long long *rowoff = rowoff_all + ((it - it0) & 1) * kWR;
+        int *rowstride = rowstride_all + ((it - it0) & 1) * kWR;
         const WItem w = witem(p, it, H1, G);
         const int ant = w.ant, k1 = w.k1, q0 = w.q0;
         const int Rv = min(kWR, p.q_begin + p.q_count - q0);
@@ -124,7 +129,9 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
         const bool active = r < Rv;
         const int stream = ant * 2 + pol;
 
-        __syncthreads();   // the previous item's corner turn is done with stg, rowoff and the tables
+        // No barrier here: the tables (pq, gsm) were last read by the previous
+        // item's epilogue, before its final barrier; stg is written only after
+        // the next barrier, which every thread reaches after its corner turn.
         // rotation factors of each (pol, spectrum) sequence, angles over pi:
         //   P[c] = exp(i pi (phi/pi - 2 delta (k1 + N1 c) / N)),
         //   Q[d] = exp(-i pi 2 delta 32 N1 d / N),  qu = exp(i pi (2 phi/pi - 2 delta)),
