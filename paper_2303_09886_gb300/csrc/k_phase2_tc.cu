@@ -77,7 +77,7 @@ size_t phase2_tc_smem_bytes(int) {
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(const Phase2Params p) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_phase2_tc(const Phase2Params p) {
     extern __shared__ uint4 smu[];
     // plan table order: a1 [4 mt][4 kt][32], b2 [4 kt2][4 ntp][32], tw [4 mt][4 nt][32], a1 lo, b2 lo
     const uint4 *a1s = smu, *b2s = smu + 512;
@@ -152,31 +152,29 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
             // lane parts of the gain slot and staging slot of k2 = g + 32 tq + 16 mp + 8 h + 128 nt2
             const float2 *gp = gsm + pol * kGainLd + g + 36 * tq;
             unsigned short *sp = stg16 + 2 * (r * kStgLd + g + 40 * tq) + pol;
-            // The lane's operands B of contraction 1, all four K tiles: K tile
-            // kt takes B[32 a + b] at a = 8 kt + 2 tq + h, b = 8 nt + g. FP16
-            // form: the intermediate holds the (re, im) FP16 pairs the products
-            // take, and they are loaded again for the second row half (128
-            // registers a thread leave no room to keep them); BF16 form: FP32
-            // pairs, split into hi and lo below, loaded once.
+            // The lane's operands B of contraction 1: K tile kt takes B[32 a + b]
+            // at a = 8 kt + 2 tq + h, b = 8 nt + g. FP16 form: the intermediate
+            // holds the (re, im) FP16 pairs the products take; all four K tiles
+            // are loaded per row half (128 registers a thread leave no room to
+            // keep them across both). BF16 form: FP32 pairs, one K tile at a
+            // time (below).
             using In = std::conditional_t<PREC == 1, unsigned, float2>;
-            In v[4][4][2];
             const In *src = reinterpret_cast<const In *>(p.A) + base;
-            auto load_b = [&](In (&vv)[4][4][2]) {
-#pragma unroll
-                for (int kt = 0; kt < 4; kt++)
-#pragma unroll
-                    for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                        for (int h = 0; h < 2; h++) vv[kt][nt][h] = __ldg(src + 32 * (8 * kt + 2 * tq + h) + 8 * nt + g);
-            };
-            if constexpr (PREC == 2) load_b(v);
+            [[maybe_unused]] unsigned v[4][4][2];
             // Rows c = 16 mp + (0 .. 15) of Y' need only m tiles 2 mp and
             // 2 mp + 1 of contraction 1, and give rows c of F: both
             // contractions and the epilogue run per mp, so that only half of
             // the first accumulator is live at a time.
 #pragma unroll
             for (int mp = 0; mp < 2; mp++) {
-                if constexpr (PREC == 1) load_b(v);
+                if constexpr (PREC == 1) {
+#pragma unroll
+                    for (int kt = 0; kt < 4; kt++)
+#pragma unroll
+                        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                            for (int h = 0; h < 2; h++) v[kt][nt][h] = __ldg(src + 32 * (8 * kt + 2 * tq + h) + 8 * nt + g);
+                }
                 float d1[2][4][4];
 #pragma unroll
                 for (int i = 0; i < 2; i++)
@@ -184,30 +182,53 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 2 ? 1 : 2) k_phase2_tc(con
                     for (int nt = 0; nt < 4; nt++)
 #pragma unroll
                         for (int x = 0; x < 4; x++) d1[i][nt][x] = 0.0f;
+                if constexpr (PREC == 1) {
 #pragma unroll
-                for (int kt = 0; kt < 4; kt++) {
-                    unsigned bh[4][2], bl[4][2];
+                    for (int kt = 0; kt < 4; kt++) {
 #pragma unroll
-                    for (int nt = 0; nt < 4; nt++)
+                        for (int i = 0; i < 2; i++) {
+                            const int mt = 2 * mp + i;
+                            const uint4 A = a1s[(mt * 4 + kt) * 32 + lane], Al = a1l[(mt * 4 + kt) * 32 + lane];
 #pragma unroll
-                        for (int h = 0; h < 2; h++) {
-                            if constexpr (PREC == 1) {
-                                bh[nt][h] = v[kt][nt][h];
-                            } else {
-                                const float2 x = v[kt][nt][h];
+                            for (int nt = 0; nt < 4; nt++) {
+                                mma16816<PREC>(d1[i][nt], A, v[kt][nt][0], v[kt][nt][1]);
+                                mma16816<PREC>(d1[i][nt], Al, v[kt][nt][0], v[kt][nt][1]);
+                            }
+                        }
+                    }
+                } else {
+                    // FP32 pairs one K tile at a time (the next tile's loads in
+                    // flight), split into hi and lo here: 3 products
+                    float2 vk[2][4][2];
+                    auto load_kt = [&](int kt, float2 (&dst)[4][2]) {
+#pragma unroll
+                        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                            for (int h = 0; h < 2; h++) dst[nt][h] = __ldg(src + 32 * (8 * kt + 2 * tq + h) + 8 * nt + g);
+                    };
+                    load_kt(0, vk[0]);
+#pragma unroll
+                    for (int kt = 0; kt < 4; kt++) {
+                        if (kt < 3) load_kt(kt + 1, vk[(kt + 1) & 1]);
+                        unsigned bh[4][2], bl[4][2];
+#pragma unroll
+                        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                const float2 x = vk[kt & 1][nt][h];
                                 bh[nt][h] = pack2<PREC>(x.x, x.y);
                                 bl[nt][h] = pack2<PREC>(x.x - prec_round<PREC>(x.x), x.y - prec_round<PREC>(x.y));
                             }
-                        }
 #pragma unroll
-                    for (int i = 0; i < 2; i++) {
-                        const int mt = 2 * mp + i;
-                        const uint4 A = a1s[(mt * 4 + kt) * 32 + lane], Al = a1l[(mt * 4 + kt) * 32 + lane];
+                        for (int i = 0; i < 2; i++) {
+                            const int mt = 2 * mp + i;
+                            const uint4 A = a1s[(mt * 4 + kt) * 32 + lane], Al = a1l[(mt * 4 + kt) * 32 + lane];
 #pragma unroll
-                        for (int nt = 0; nt < 4; nt++) {
-                            mma16816<PREC>(d1[i][nt], A, bh[nt][0], bh[nt][1]);
-                            mma16816<PREC>(d1[i][nt], Al, bh[nt][0], bh[nt][1]);
-                            if constexpr (PREC == 2) mma16816<PREC>(d1[i][nt], A, bl[nt][0], bl[nt][1]);
+                            for (int nt = 0; nt < 4; nt++) {
+                                mma16816<PREC>(d1[i][nt], A, bh[nt][0], bh[nt][1]);
+                                mma16816<PREC>(d1[i][nt], Al, bh[nt][0], bh[nt][1]);
+                                mma16816<PREC>(d1[i][nt], A, bl[nt][0], bl[nt][1]);
+                            }
                         }
                     }
                 }
