@@ -55,7 +55,7 @@ NCU_TRAFFIC = {
     "k_phase1<16,64,8,0>": {"bytes_per_sample": (44158464 + 89049344) / _CAPTURED, "src": "13910250eed63552"},
     "k_phase2w": {"bytes_per_sample": (166702080 + 19888640) / _CAPTURED, "src": "37b541bbe4acac32"},
     "k_phase2<256>": {"bytes_per_sample": (138605824 + 13872896) / _CAPTURED, "src": "d220de853820a978"},
-    "k_phase2_tc<1>": {"bytes_per_sample": (75761920 + 9490176) / _CAPTURED, "src": "42f0c33654a9bcc3"},
+    "k_phase2_tc<1>": {"bytes_per_sample": (75749888 + 9130240) / _CAPTURED, "src": "f50b2f86ddfef24f"},
     "k_phase2_tc<2>": {"bytes_per_sample": (151278336 + 19053056) / _CAPTURED, "src": "f50b2f86ddfef24f"},
 }
 
