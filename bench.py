@@ -50,13 +50,13 @@ KERNEL_SOURCES = {
 }
 _CAPTURED = 33554432   # input samples of the captured launch
 NCU_TRAFFIC = {
-    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44408832 + 95248128) / _CAPTURED, "src": "13910250eed63552"},
-    "k_phase1<16,16,32,1>": {"bytes_per_sample": (43936768 + 27555840) / _CAPTURED, "src": "13910250eed63552"},
-    "k_phase1<16,64,8,0>": {"bytes_per_sample": (44158464 + 89049344) / _CAPTURED, "src": "13910250eed63552"},
-    "k_phase2w": {"bytes_per_sample": (166702080 + 19888640) / _CAPTURED, "src": "37b541bbe4acac32"},
-    "k_phase2<256>": {"bytes_per_sample": (138605824 + 13872896) / _CAPTURED, "src": "d220de853820a978"},
-    "k_phase2_tc<1>": {"bytes_per_sample": (75749888 + 9130240) / _CAPTURED, "src": "f50b2f86ddfef24f"},
-    "k_phase2_tc<2>": {"bytes_per_sample": (151278336 + 19053056) / _CAPTURED, "src": "f50b2f86ddfef24f"},
+    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44408832 + 95248128) / _CAPTURED, "src": "11552148f7285605"},
+    "k_phase1<16,16,32,1>": {"bytes_per_sample": (43936768 + 27555840) / _CAPTURED, "src": "11552148f7285605"},
+    "k_phase1<16,64,8,0>": {"bytes_per_sample": (44158464 + 89049344) / _CAPTURED, "src": "11552148f7285605"},
+    "k_phase2w": {"bytes_per_sample": (166702080 + 19888640) / _CAPTURED, "src": "25eaca44b1835be4"},
+    "k_phase2<256>": {"bytes_per_sample": (138605824 + 13872896) / _CAPTURED, "src": "4b85a31bd47bd8c3"},
+    "k_phase2_tc<1>": {"bytes_per_sample": (75749888 + 9130240) / _CAPTURED, "src": "2bb83c4f67d0b965"},
+    "k_phase2_tc<2>": {"bytes_per_sample": (151278336 + 19053056) / _CAPTURED, "src": "2bb83c4f67d0b965"},
 }
 
 

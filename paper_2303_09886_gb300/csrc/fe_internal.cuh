@@ -4,8 +4,10 @@
 //   k_delay_table   FP64 delay/phase model per spectrum -> coarse c, fine delta, phase
 //   k_phase1<T,N1>  unpack + coarse delay + PFB FIR (Eq. 1) + first FFT stage
 //                   (real N1-point DFT over t1, twiddle by exp(-2 pi i k1 t2 / N))
-//   k_phase2<N2>    N2-point FFT over t2 + fine-delay rotation + gain +
-//                   requantise + channel-major corner turn (FP32 form), or
+//   k_phase2w       1024-point FFT over t2 + fine-delay rotation + gain +
+//                   requantise + channel-major corner turn (FP32 form,
+//                   persistent, one warp per sequence), or
+//   k_phase2<N2>    the same for N2 < 1024 (FP32 form), or
 //   k_phase2_tc     the same with the 1024-point FFT as two 32-point DFT
 //                   contractions on tensor cores (FP16 / BF16 forms)
 //   k_tail_update   keep the last H packed samples of every stream
@@ -105,8 +107,9 @@ size_t phase2_smem_bytes(int N2, int R2);
 
 // Reduced-precision second stage (N2 = 1024 only): two 32-point DFT
 // contractions on tensor cores. The tables hold the DFT matrices as per-lane
-// mma fragments and the 32 x 32 twiddle (times 2^-5); kPhase2TcTableLen
-// uint4 entries, built on the host for precision 1 (FP16) or 2 (BF16).
+// mma fragments (hi and lo parts) and the 32 x 32 twiddle (times 2^-5);
+// kPhase2TcTableLen uint4 entries, built on the host for precision 1 (FP16)
+// or 2 (BF16).
 constexpr int kPhase2TcTableLen = 2560;
 void build_phase2_tc_tables(int precision, uint4 *out);
 size_t phase2_tc_smem_bytes(int precision);
