@@ -74,7 +74,8 @@ size_t phase2w_smem_bytes() {
            + (sizeof(long long) + sizeof(int)) * 2 * kWR;   // row info, two items
 }
 
-// Persistent: each CTA takes a contiguous range of work items. Warp w owns
+// Persistent: each CTA takes a contiguous range of work items of equal work.
+// Warp w owns
 // sequence (spectrum w / 2, polarisation w % 2) of every item; its 8 KB
 // sequence arrives in its shared-memory buffer by cp.async, and the copy of
 // the next item's sequence is issued as soon as the buffer has been read
@@ -93,8 +94,31 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
     const int M = p.M, N1 = p.N1, H1 = N1 / 2, N = p.N, n = N / 2, S_ = p.S;
     const int G = (p.q_count + kWR - 1) / kWR;
     const int n_items = n_ant * (H1 + 1) * G;
-    const int per = (n_items + gridDim.x - 1) / gridDim.x;
-    const int it0 = blockIdx.x * per, it1 = min(n_items, it0 + per);
+    // Contiguous ranges of equal work: classes k1 = 0 and N1/2 keep only the
+    // lower half of their slots (half the epilogue and corner turn), so their
+    // items count 4 units against 5 for the others; CTA b takes the items
+    // whose work starts in [b W / gridDim.x, (b + 1) W / gridDim.x).
+    constexpr int wL = 4, wF = 5;
+    const int Wa = G * (2 * wL + (H1 - 1) * wF);   // work of one antenna
+    auto first_item = [&](long long x) {          // first item whose work starts at >= x
+        const int ant = (int)(x / Wa);
+        const int y = (int)(x - (long long)ant * Wa);
+        int k1, g;
+        if (y < wL * G) {
+            k1 = 0;
+            g = (y + wL - 1) / wL;
+        } else if (y < (wL + (H1 - 1) * wF) * G) {
+            const int y1 = y - wL * G;
+            k1 = 1 + y1 / (wF * G);
+            g = (y1 - (k1 - 1) * wF * G + wF - 1) / wF;
+        } else {
+            k1 = H1;
+            g = (y - (wL + (H1 - 1) * wF) * G + wL - 1) / wL;
+        }
+        return min(n_items, ant * (H1 + 1) * G + k1 * G + g);
+    };
+    const long long Wt = (long long)n_ant * Wa;
+    const int it0 = first_item(Wt * blockIdx.x / gridDim.x), it1 = first_item(Wt * (blockIdx.x + 1) / gridDim.x);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = warp >> 1, pol = warp & 1;
     float2 *mybuf = sbuf + warp * kWN2;
