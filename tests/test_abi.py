@@ -104,3 +104,31 @@ def test_autotune_rejects_bad_arguments_before_any_device_call(lib):
     n = ctypes.c_int32(-1)
     assert lib.fengine_autotune(ctypes.byref(c), None, 0, ctypes.byref(tuned), None, 0, ctypes.byref(n)) == 1
     assert lib.fengine_autotune(None, None, 3, ctypes.byref(tuned), None, 0, ctypes.byref(n)) == 1
+
+
+def test_batch_and_service_refuse_bad_arguments_before_any_device_call(lib):
+    EINVAL = 1
+    vp = ctypes.c_void_p
+    h = vp()
+    # batch: pool size 1..64, an out pointer, a live handle, non-negative counts
+    for n_pool in (0, -1, 65):
+        assert lib.fengine_batch_create(n_pool, ctypes.byref(h)) == EINVAL
+    assert lib.fengine_batch_create(8, None) == EINVAL
+    assert lib.fengine_batch_destroy(None) == EINVAL
+    first = ctypes.c_int64()
+    assert lib.fengine_batch_process(None, None, None, 0, ctypes.byref(first)) == EINVAL
+    # service: 1..64 streams and a positive budget, live handles everywhere
+    fengine._service_signatures(lib)
+    for n_streams, budget in ((0, 1 << 30), (65, 1 << 30), (4, 0), (4, -1)):
+        cfg = fengine.ServiceConfig(n_streams, budget)
+        assert lib.fengine_service_create(ctypes.byref(cfg), ctypes.byref(h)) == EINVAL
+    assert lib.fengine_service_create(None, ctypes.byref(h)) == EINVAL
+    assert lib.fengine_service_create(ctypes.byref(fengine.ServiceConfig(4, 1 << 30)), None) == EINVAL
+    ticket = ctypes.c_int64()
+    assert lib.fengine_service_submit(None, None, None, 0, None, ctypes.byref(ticket)) == EINVAL
+    assert lib.fengine_service_set_delay(None, None, 0, 0, 0, 0, 1.0, 0.0, 0.0, 0.0) == EINVAL
+    assert lib.fengine_service_set_gains(None, None, 0, 0, None) == EINVAL
+    lat = ctypes.c_double()
+    assert lib.fengine_service_wait(None, 0, 10, ctypes.byref(lat)) == EINVAL
+    assert lib.fengine_service_get_stats(None, None) == EINVAL
+    assert lib.fengine_service_destroy(None) == EINVAL
