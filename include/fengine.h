@@ -105,7 +105,7 @@ typedef struct {
     int64_t out_bytes;            /* bytes of d_out per call: n_antennas * M * n * 4 */
     size_t device_bytes;          /* device memory the plan holds */
     size_t scratch_bytes;         /* part of device_bytes used as per-call scratch */
-    int32_t slab_spectra;         /* spectra per slab of the L2-resident two-phase pipeline */
+    int32_t slab_spectra;         /* spectra per slab of the two-phase pipeline (one launch pair) */
     int32_t slabs_per_chunk;      /* slabs (phase-1 + phase-2 launch pairs) per call */
 } fengine_info;
 
