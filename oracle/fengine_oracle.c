@@ -25,7 +25,7 @@
  *      corner turn within each 256-spectrum heap (Sec. 2.2, Sec. 3.6):
  *      orc_quantise / orc_corner_turn.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent (this oracle's and the library's choices):
  *   R1 bit order: sample i occupies bits [10i, 10i+10) of the chunk bit
  *      stream, most significant bit first (bit 0 = MSB of byte 0); the field
  *      is two's complement.
@@ -40,6 +40,14 @@
  *   R6 fine delay: Y[k] = G[k] exp(i (phi - 2 pi delta k / N)) X[k].
  *   R7 quantiser: round half away from zero, saturate to [-127, 127].
  *   R8 samples before the first sample of a stream are zero.
+ *   R12 a gain update, like a delay update, applies to spectra whose
+ *      timestamp t0 is at or after its t_apply.
+ *   R13 lost data (Sec. 3.7): a digitiser heap is 4096 samples (Sec. 2.2)
+ *      starting at a multiple of 4096; heaps no chunk delivered (before a
+ *      stream's first chunk, or flagged missing) are missing.
+ * Steps 7-8 (lost data, Sec. 3.7): orc_window_usable / orc_spectrum_flags /
+ * orc_heap_flags; gain sets that change at spectrum timestamps:
+ * orc_segment_select.
  */
 #include <math.h>
 #include <stdint.h>
@@ -316,4 +324,90 @@ void orc_corner_turn(const int8_t *q_pol0, const int8_t *q_pol1, int64_t M,
                     out[off] = qp[p][2 * (m * n + k) + c];
                 }
     }
+}
+
+/* ------------------------------------------------------------ lost data */
+
+/* floor(a / b) for b > 0, also for negative a. */
+static int64_t floor_div(int64_t a, int64_t b)
+{
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0)
+        q -= 1;
+    return q;
+}
+
+/* Lost data (Sec. 3.7): the receiver flags which digitiser heaps arrived;
+ * a heap holds heap_len consecutive samples of one polarisation (4096,
+ * Sec. 2.2), heap h holding samples [h heap_len, (h + 1) heap_len).
+ * received[i] describes heap heap_first + i for i < n_heaps; every heap
+ * outside that range counts as missing (so do samples before a stream's
+ * first chunk). A window [start, start + len) is usable iff every heap it
+ * touches was received. Returns 1 (usable) or 0. */
+int orc_window_usable(const uint8_t *received, int64_t heap_first, int64_t n_heaps,
+                      int64_t heap_len, int64_t start, int64_t len)
+{
+    int64_t h0 = floor_div(start, heap_len);
+    int64_t h1 = floor_div(start + len - 1, heap_len);
+    for (int64_t h = h0; h <= h1; h++) {
+        if (h < heap_first || h >= heap_first + n_heaps)
+            return 0;
+        if (!received[h - heap_first])
+            return 0;
+    }
+    return 1;
+}
+
+/* Sec. 3.7: the output spectrum m is flagged unusable if the window of input
+ * samples of its PFB, [t0 - c, t0 - c + N T) with t0 = N m and c the coarse
+ * delay of the delay model (orc_delay_eval), has any missing data.
+ * usable[i] (i < m_count) is 1 or 0 for spectrum m_first + i. */
+void orc_spectrum_flags(const uint8_t *received, int64_t heap_first, int64_t n_heaps,
+                        int64_t heap_len, int N, int T, int32_t n_seg,
+                        const int64_t *t_apply, const int64_t *t_ref, const double *d0,
+                        const double *rate, const double *phi0, const double *phi_rate,
+                        int64_t m_first, int64_t m_count, uint8_t *usable)
+{
+    for (int64_t i = 0; i < m_count; i++) {
+        int64_t t0 = (int64_t)N * (m_first + i);
+        int64_t c;
+        double delta, phi;
+        orc_delay_eval(n_seg, t_apply, t_ref, d0, rate, phi0, phi_rate, t0, &c, &delta, &phi);
+        usable[i] = (uint8_t)orc_window_usable(received, heap_first, n_heaps, heap_len,
+                                                t0 - c, (int64_t)N * T);
+    }
+}
+
+/* Sec. 3.7 with Sec. 2.1 (an output heap carries both polarisations of an
+ * antenna): output heap h of a call, spectra h S .. h S + S_h - 1 with
+ * S_h = min(S, M - h S) (the heap layout of orc_corner_turn), is transmitted
+ * (heap_ok[h] = 1) only if all of its spectra are usable in both
+ * polarisations; otherwise heap_ok[h] = 0. */
+void orc_heap_flags(const uint8_t *usable_pol0, const uint8_t *usable_pol1, int64_t M, int S,
+                    uint8_t *heap_ok)
+{
+    int64_t n_heaps = (M + S - 1) / S;
+    for (int64_t h = 0; h < n_heaps; h++) {
+        int ok = 1;
+        for (int64_t m = h * S; m < M && m < (h + 1) * S; m++)
+            if (!usable_pol0[m] || !usable_pol1[m])
+                ok = 0;
+        heap_ok[h] = (uint8_t)ok;
+    }
+}
+
+/* --------------------------------------------------------- gain updates */
+
+/* Bandpass gains change at spectrum timestamps like the delay model (Sec. 2.1
+ * step 5 gives the per-channel correction; the time it applies from is this
+ * library's reading R12): gain set s applies to spectra with timestamp
+ * t0 >= t_apply[s], sets sorted by t_apply, a timestamp before every set uses
+ * set 0. Returns the index of the set that spectrum timestamp t0 uses. */
+int32_t orc_segment_select(int32_t n_seg, const int64_t *t_apply, int64_t t0)
+{
+    int32_t s = 0;
+    for (int32_t k = 0; k < n_seg; k++)
+        if (t_apply[k] <= t0)
+            s = k;
+    return s;
 }

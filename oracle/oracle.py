@@ -71,6 +71,18 @@ def _load():
             lib.orc_corner_turn.argtypes = [_I8P, _I8P, ctypes.c_int64, ctypes.c_int,
                                             ctypes.c_int, _I8P]
             lib.orc_corner_turn.restype = None
+            lib.orc_window_usable.argtypes = [_U8P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.c_int64, ctypes.c_int64]
+            lib.orc_window_usable.restype = ctypes.c_int
+            lib.orc_spectrum_flags.argtypes = [_U8P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_int32, _I64P, _I64P,
+                                               _F64P, _F64P, _F64P, _F64P, ctypes.c_int64, ctypes.c_int64,
+                                               _U8P]
+            lib.orc_spectrum_flags.restype = None
+            lib.orc_heap_flags.argtypes = [_U8P, _U8P, ctypes.c_int64, ctypes.c_int, _U8P]
+            lib.orc_heap_flags.restype = None
+            lib.orc_segment_select.argtypes = [ctypes.c_int32, _I64P, ctypes.c_int64]
+            lib.orc_segment_select.restype = ctypes.c_int32
             _lib = lib
     return _lib
 
@@ -159,14 +171,39 @@ def fir(samples: np.ndarray, first: int, N: int, T: int, w: np.ndarray, t0: int,
     return g
 
 
+def segment_select(t_applies, t0: int) -> int:
+    """Index of the gain (or delay) set that spectrum timestamp t0 uses: the
+    last set whose t_apply <= t0, set 0 before every set (reading R12)."""
+    ta = np.ascontiguousarray(t_applies, dtype=np.int64)
+    return int(_load().orc_segment_select(ta.size, _p(ta, _I64P), int(t0)))
+
+
 def channelize(samples: np.ndarray, first: int, N: int, T: int, w: np.ndarray,
-               delay: DelayModel, gains: np.ndarray, m_first: int, m_count: int,
+               delay: DelayModel, gains, m_first: int, m_count: int,
                want_q: bool = True):
     """Whole hot path for one (antenna, pol) stream.
 
+    gains: n complex values, or a list of (t_apply, n complex values) gain
+    sets sorted by t_apply (spectrum t0 uses the set segment_select picks).
     Returns (prequant complex128 [m_count, n], q int8 [m_count, n, 2] or None,
     coarse int64 [m_count]).
     """
+    if isinstance(gains, (list, tuple)) and gains and isinstance(gains[0], tuple):
+        # runs of consecutive spectra with one gain set, each a plain call
+        t_app = [g[0] for g in gains]
+        sel = [segment_select(t_app, N * (m_first + i)) for i in range(m_count)]
+        parts = []
+        i = 0
+        while i < m_count:
+            j = i
+            while j < m_count and sel[j] == sel[i]:
+                j += 1
+            parts.append(channelize(samples, first, N, T, w, delay, gains[sel[i]][1], m_first + i, j - i,
+                                    want_q))
+            i = j
+        return (np.concatenate([p[0] for p in parts]),
+                np.concatenate([p[1] for p in parts]) if want_q else None,
+                np.concatenate([p[2] for p in parts]))
     n = N // 2
     s = np.ascontiguousarray(samples, dtype=np.int32)
     w = np.ascontiguousarray(w, dtype=np.float64)
@@ -195,4 +232,43 @@ def corner_turn(q_pol0: np.ndarray, q_pol1: np.ndarray, S: int) -> np.ndarray:
     M, n = q0.shape[0], q0.shape[1]
     out = np.empty(M * n * 4, np.int8)
     _load().orc_corner_turn(_p(q0, _I8P), _p(q1, _I8P), M, n, S, _p(out, _I8P))
+    return out
+
+
+# ------------------------------------------------------------- lost data
+
+HEAP_SAMPLES = 4096   # samples per digitiser heap (Sec. 2.2)
+
+
+def window_usable(received: np.ndarray, heap_first: int, start: int, length: int,
+                  heap_len: int = HEAP_SAMPLES) -> bool:
+    """Sec. 3.7: True iff every heap that [start, start + length) touches was
+    received (heaps outside received's range are missing)."""
+    r = np.ascontiguousarray(received, dtype=np.uint8)
+    return bool(_load().orc_window_usable(_p(r, _U8P), int(heap_first), r.size, int(heap_len),
+                                          int(start), int(length)))
+
+
+def spectrum_flags(received: np.ndarray, heap_first: int, N: int, T: int, delay: DelayModel,
+                   m_first: int, m_count: int, heap_len: int = HEAP_SAMPLES) -> np.ndarray:
+    """Sec. 3.7: uint8 [m_count], 1 where spectrum m's PFB window has no
+    missing sample, 0 where it is flagged unusable."""
+    r = np.ascontiguousarray(received, dtype=np.uint8)
+    ta, tr, d0, rt, p0, pr = delay.arrays()
+    out = np.empty(m_count, np.uint8)
+    _load().orc_spectrum_flags(_p(r, _U8P), int(heap_first), r.size, int(heap_len), N, T,
+                               len(delay.segments), _p(ta, _I64P), _p(tr, _I64P), _p(d0, _F64P),
+                               _p(rt, _F64P), _p(p0, _F64P), _p(pr, _F64P), int(m_first), int(m_count),
+                               _p(out, _U8P))
+    return out
+
+
+def heap_flags(usable_pol0: np.ndarray, usable_pol1: np.ndarray, S: int) -> np.ndarray:
+    """Sec. 3.7: uint8 per output heap of S spectra (both polarisations),
+    1 = transmitted, 0 = holds an unusable spectrum and is not transmitted."""
+    u0 = np.ascontiguousarray(usable_pol0, np.uint8)
+    u1 = np.ascontiguousarray(usable_pol1, np.uint8)
+    M = u0.size
+    out = np.empty((M + S - 1) // S, np.uint8)
+    _load().orc_heap_flags(_p(u0, _U8P), _p(u1, _U8P), M, S, _p(out, _U8P))
     return out

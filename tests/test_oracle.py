@@ -295,3 +295,98 @@ def test_corner_turn_golden():
             q0[m, k] = (10 * m + 2 * k + 1, 10 * m + 2 * k + 2)
     out = O.corner_turn(q0, -q0, S)
     np.testing.assert_array_equal(out, expect)
+
+
+# -------------------------------------------------------------- lost data
+
+def _golden_lost():
+    with open(os.path.join(GOLDEN, "lost_data_small.txt")) as fh:
+        return [l.strip() for l in fh if l.strip() and not l.startswith("#")]
+
+
+def test_lost_data_golden():
+    rec = [np.ones(20, np.uint8), np.ones(20, np.uint8)]
+    rec[0][5] = 0
+    rec[1][9] = 0
+    usable = {}
+    for line in _golden_lost():
+        head, tail = line.split(";")
+        expect = [int(v) for v in tail.split()]
+        if head.startswith("heaps"):
+            got = O.heap_flags(usable[(0, 0)], usable[(1, 0)], 4)
+            np.testing.assert_array_equal(got, np.array(expect, np.uint8))
+            continue
+        pol, c = (int(v) for v in head.split())
+        f = O.spectrum_flags(rec[pol], 0, 2048, 4, O.DelayModel.constant(float(c)), 0, 20)
+        usable[(pol, c)] = f
+        np.testing.assert_array_equal(np.where(f == 0)[0], np.array(expect))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_lost_data_brute_force_per_sample(seed):
+    # sample-by-sample definition on tiny streams: a spectrum is usable iff no
+    # sample of its window lies in a missing heap (or before the stream)
+    g = np.random.default_rng(seed)
+    heap = int(g.choice([16, 32, 64]))
+    N, T = int(g.choice([8, 16, 32])), int(g.choice([1, 2, 4]))
+    n_heaps = 24
+    rec = (g.random(n_heaps) > 0.25).astype(np.uint8)
+    first = int(g.integers(0, 3))          # heaps before `first` are missing
+    d = float(g.uniform(-40, 40))
+    rate = float(g.choice([0.0, 0.01]))
+    dm = O.DelayModel.constant(d, rate=rate)
+    M = (n_heaps * heap) // N
+    f = O.spectrum_flags(rec[first:], first, N, T, dm, 0, M, heap_len=heap)
+    ok_sample = np.zeros(n_heaps * heap + 4096, bool)
+    for h in range(first, n_heaps):
+        ok_sample[h * heap:(h + 1) * heap] = bool(rec[h])
+    for m in range(M):
+        c, _, _ = dm.eval(N * m)
+        idx = N * m - c + np.arange(N * T)
+        expect = bool(np.all(idx >= 0) and np.all(ok_sample[np.clip(idx, 0, None)]))
+        assert bool(f[m]) == expect, (seed, m)
+
+
+def test_heap_flags_partial_last_heap():
+    u0 = np.array([1, 1, 1, 1, 1, 1, 1, 0], np.uint8)    # last (partial) heap: spectrum 7 unusable
+    u1 = np.array([1, 0, 1, 1, 1, 1, 1, 1], np.uint8)
+    np.testing.assert_array_equal(O.heap_flags(u0, u1, 3), [0, 1, 0])
+    np.testing.assert_array_equal(O.heap_flags(u1, u1, 3), [0, 1, 1])
+
+
+# ----------------------------------------------------------- gain updates
+
+def test_gain_set_applies_from_t_apply():
+    # a second gain set equal to twice the first, applied from spectrum 5 on:
+    # spectra 0..4 keep the first set, 5.. are exactly doubled (power-of-two
+    # scaling is exact), and the switch is at t0 >= t_apply, not after it
+    N, T = 64, 4
+    g = np.random.default_rng(3)
+    s = g.integers(-300, 300, 4096).astype(np.int32)
+    w = O.pfb_weights(N, T)
+    G0 = g.uniform(0.5, 2, N // 2) * np.exp(2j * np.pi * g.random(N // 2))
+    dm = O.DelayModel.constant(3.25, phase=0.4)
+    base, _, _ = O.channelize(s, 0, N, T, w, dm, G0, 4, 12)
+    sched, _, _ = O.channelize(s, 0, N, T, w, dm, [(-(2 ** 62), G0), (N * 5, 2 * G0)], 4, 12)
+    np.testing.assert_array_equal(sched[:1], base[:1])            # m = 4 < 5
+    np.testing.assert_array_equal(sched[1:], 2 * base[1:])         # m >= 5
+    assert O.segment_select([-(2 ** 62), N * 5], N * 5) == 1
+    assert O.segment_select([-(2 ** 62), N * 5], N * 5 - 1) == 0
+    assert O.segment_select([100, 200], 50) == 0                  # before every set: set 0
+
+
+# --------------------------------------------------------- negative delays
+
+@pytest.mark.parametrize("c", [1, 7, 300])
+def test_negative_integer_delay_is_a_shift_the_other_way(c):
+    # Sec. 3.3 allows negative delays: delay -c on stream s equals delay 0 on
+    # the stream advanced by c samples (s'[i] = s[i + c]), exactly
+    N, T = 128, 4
+    g = np.random.default_rng(c)
+    s = g.integers(-512, 512, 40 * N).astype(np.int32)
+    w = O.pfb_weights(N, T)
+    neg, qn, cn = O.channelize(s, 0, N, T, w, O.DelayModel.constant(-float(c), phase=0.2), np.ones(N // 2), 2, 20)
+    adv, qa, _ = O.channelize(s[c:], 0, N, T, w, O.DelayModel.constant(0.0, phase=0.2), np.ones(N // 2), 2, 20)
+    assert np.all(cn == -c)
+    np.testing.assert_array_equal(neg, adv)
+    np.testing.assert_array_equal(qn, qa)
