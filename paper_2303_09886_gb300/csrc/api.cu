@@ -51,8 +51,12 @@ struct fengine_plan_s {
     // device state
     float *d_w = nullptr;
     float2 *d_tw1 = nullptr, *d_tw2 = nullptr, *d_gains = nullptr, *d_ftab = nullptr, *d_A = nullptr;
-    uint4 *d_tc = nullptr;        // tensor-core second-stage tables (reduced-precision forms)
-    float tc_unscale = 1.0f;
+    // reduced-precision forms: tensor-core phase-1 operand blocks and per-column epilogue scales
+    uint16_t *d_bmat = nullptr;
+    float *d_oscale = nullptr;
+    float tc_unscale = 1.0f;        // inverse of the FP16 intermediate's scale
+    bool tc1 = false;               // phase 1 on tensor cores
+    int tc_splits = 1;              // tensor-core phase-1 item ranges per column group (per slab)
     uint8_t *d_hist[2] = {nullptr, nullptr};
     int cur = 0;
     DelaySeg *d_seg = nullptr;
@@ -96,7 +100,8 @@ void release(fengine_plan_s *pl) {
     cudaFree(pl->d_w);
     cudaFree(pl->d_tw1);
     cudaFree(pl->d_tw2);
-    cudaFree(pl->d_tc);
+    cudaFree(pl->d_bmat);
+    cudaFree(pl->d_oscale);
     cudaFree(pl->d_gains);
     cudaFree(pl->d_ftab);
     cudaFree(pl->d_A);
@@ -225,20 +230,27 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     if (S < 1 || S > M) return fail(FENGINE_EINVAL, "spectra_per_heap must be in [1, L/2n]");
     if (cfg->precision != FENGINE_FP32 && cfg->precision != FENGINE_TC_FP16 && cfg->precision != FENGINE_TC_BF16)
         return fail(FENGINE_EINVAL, "unknown precision");
-    // four-step split: N1 from the config or the built-in max(8, N / 1024);
-    // the phase-1 tiles exist for N1 = 8 (W = min(64, N2)) and N1 = 16, 32,
-    // 64 (W = 512 / N1 <= N2), the phase-2 kernels for N2 <= 1024
-    const int N1 = cfg->fft_n1 ? cfg->fft_n1 : (int)(N / 1024 > 8 ? N / 1024 : 8);
-    if (!(N1 == 8 || N1 == 16 || N1 == 32 || N1 == 64) || N % N1 || N / N1 > 1024 || N / N1 < 4 ||
-        (N1 > 8 && N / N1 < 512 / N1))
+    // four-step split. FP32 form: N1 from the config or the built-in
+    // max(8, N / 1024); its phase-1 tiles exist for N1 = 8 (W = min(64, N2))
+    // and N1 = 16, 32, 64 (W = 512 / N1 <= N2), the phase-2 kernels for
+    // N2 <= 1024. Tensor-core forms: N1 = 8 R (fe::phase1_tc_R), the only split.
+    const bool tc1 = cfg->precision != FENGINE_FP32;
+    int N1 = cfg->fft_n1 ? cfg->fft_n1 : (int)(N / 1024 > 8 ? N / 1024 : 8);
+    if (tc1) {
+        if (!fe::phase1_tc_supported((int)N, T, cfg->precision))
+            return fail(FENGINE_EUNSUPPORTED, "the tensor-core forms need 32 <= n_channels <= 32768 (and n_taps <= 16 "
+                                              "for n_channels >= 32768, or for n_channels = 16384 in BF16)");
+        const int n1_tc = 8 * fe::phase1_tc_R((int)N);
+        if (cfg->fft_n1 && cfg->fft_n1 != n1_tc)
+            return fail(FENGINE_EINVAL, "the tensor-core forms use fft_n1 = " + std::to_string(n1_tc) + " (or 0)");
+        N1 = n1_tc;
+    } else if (!(N1 == 8 || N1 == 16 || N1 == 32 || N1 == 64) || N % N1 || N / N1 > 1024 || N / N1 < 4 ||
+               (N1 > 8 && N / N1 < 512 / N1)) {
         return fail(FENGINE_EINVAL, "fft_n1 must be 8, 16, 32 or 64 with N / fft_n1 <= 1024 (and >= 512 / fft_n1 "
                                     "for fft_n1 > 8)");
+    }
     if (cfg->slab_spectra < 0 || cfg->slab_spectra % 32)
         return fail(FENGINE_EINVAL, "slab_spectra must be 0 or a positive multiple of 32");
-    if (cfg->precision != FENGINE_FP32 && N / N1 != 1024)
-        return fail(FENGINE_EUNSUPPORTED,
-                    "the tensor-core forms need a 1024-point second stage (n_channels >= 4096, "
-                    "fft_n1 = 2 n_channels / 1024)");
 
     fengine_plan_s *pl = new (std::nothrow) fengine_plan_s();
     if (!pl) return fail(FENGINE_ENOMEM, "host allocation");
@@ -254,6 +266,7 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     pl->D = cfg->max_delay_samples;
     pl->precision = cfg->precision;
     pl->N1 = N1;
+    pl->tc1 = tc1;
     pl->N2 = (int)(N / pl->N1);
     pl->W = fe::phase1_W(pl->N1, pl->N2);
     pl->C = pl->N1 * pl->W;
@@ -333,42 +346,39 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
             release(pl);
             return fail(FENGINE_EINVAL, "weights must be finite");
         }
-    // The reduced-precision second stage reads B[k1][t2] scaled by a power
-    // of two s1 with |s1 B| <= 2^15 (inside FP16): |g| <= 512 max_t sum_j |w|
-    // and the real N1-point first stage grows it by at most N1. The scale is
-    // folded into the first-stage twiddle (exact), the second stage's own
-    // twiddle carries 2^-5 and its rotation 32 / s1 undoes both.
-    float s1 = 1.0f;
-    {
-        double wmax = 0.0;
-        for (long long t = 0; t < N; t++) {
-            double a = 0.0;
-            for (int j = 0; j < T; j++) a += std::fabs((double)w[t + N * j]);
-            wmax = a > wmax ? a : wmax;
-        }
-        const double bound = (double)pl->N1 * 512.0 * (wmax > 0.0 ? wmax : 1.0);
-        s1 = (float)std::ldexp(1.0, (int)std::floor(std::log2(32768.0 / bound)));
-    }
-    const float tw1_scale = s1;
-    std::vector<uint4> tc;
-    if (pl->precision != FENGINE_FP32) {
-        pl->tc_unscale = 32.0f / s1;
-        tc.resize(fe::kPhase2TcTableLen);
-        fe::build_phase2_tc_tables(pl->precision, tc.data());
-        if ((e = dalloc(pl, &pl->d_tc, sizeof(uint4) * tc.size())) != cudaSuccess ||
-            (e = cudaMemcpy(pl->d_tc, tc.data(), sizeof(uint4) * tc.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    // Reduced-precision forms: the tensor-core phase 1's operand blocks
+    // (weights x DFT x twiddle, a power-of-two scale per output column) and
+    // epilogue scales; the FP16 form stores the second-stage input scaled by
+    // a power of two s_int that keeps it inside FP16, undone in phase 2.
+    if (tc1) {
+        std::vector<uint16_t> bmat;
+        std::vector<float> osc;
+        float s_int = 1.0f;
+        fe::build_phase1_tc_tables((int)N, T, pl->precision, w.data(), bmat, osc, s_int);
+        pl->tc_unscale = 1.0f / s_int;
+        if ((e = dalloc(pl, &pl->d_bmat, sizeof(uint16_t) * bmat.size())) != cudaSuccess ||
+            (e = dalloc(pl, &pl->d_oscale, sizeof(float) * osc.size())) != cudaSuccess ||
+            (e = cudaMemcpy(pl->d_bmat, bmat.data(), sizeof(uint16_t) * bmat.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess ||
+            (e = cudaMemcpy(pl->d_oscale, osc.data(), sizeof(float) * osc.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
             release(pl);
-            return cuda_fail(e, "tensor-core tables");
+            return cuda_fail(e, "tensor-core operand blocks");
         }
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // column groups x item ranges: about eight CTAs per SM over a slab
+        const int R = fe::phase1_tc_R((int)N), n_cg = pl->N2 / (8 / R);
+        const long long items = (long long)pl->n_streams * ((pl->SL + 127) / 128);
+        long long sp = ((long long)8 * (sms > 0 ? sms : 148) + n_cg - 1) / n_cg;
+        if (sp > items) sp = items;
+        pl->tc_splits = (int)(sp < 1 ? 1 : sp);
     }
     // twiddles, evaluated in FP64 with exact integer phase reduction
     std::vector<float2> tw1((size_t)(pl->N1 / 2 + 1) * pl->N2), tw2(pl->N2);
     for (int k1 = 0; k1 <= pl->N1 / 2; k1++)
-        for (int t2 = 0; t2 < pl->N2; t2++) {
-            float2 v = unit_root((long long)k1 * t2, N);
-            if (pl->precision != FENGINE_FP32) v = make_float2(v.x * tw1_scale, v.y * tw1_scale);
-            tw1[(size_t)k1 * pl->N2 + t2] = v;
-        }
+        for (int t2 = 0; t2 < pl->N2; t2++) tw1[(size_t)k1 * pl->N2 + t2] = unit_root((long long)k1 * t2, N);
     for (int q = 0; q < pl->N2; q++) tw2[q] = unit_root(q, pl->N2);
     pl->segs.assign(ns, std::vector<DelaySeg>{DelaySeg{-(1LL << 62), 0, 0.0, 0.0, 0.0, 0.0}});
     pl->gains.assign((size_t)ns * n, make_float2(1.0f, 0.0f));
@@ -558,7 +568,7 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     p1.ctab = pl->d_ctab;
     p1.window_tap = d_window_tap;
     p1.a_spectra = pl->SL;
-    p1.half_out = pl->precision == FENGINE_TC_FP16;
+    p1.half_out = 0;
 
     fe::Phase2Params p2{};
     p2.tw2 = pl->d_tw2;
@@ -572,9 +582,29 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     p2.out = d_out;
     p2.prequant = reinterpret_cast<float2 *>(d_prequant);
     p2.a_spectra = pl->SL;
-    p2.precision = pl->precision;
-    p2.tc = pl->d_tc;
+    p2.half_in = pl->precision == FENGINE_TC_FP16;   // every form's second stage runs on CUDA cores
     p2.tc_unscale = pl->tc_unscale;
+
+    fe::Phase1TcParams pt{};
+    pt.chunk = d_packed;
+    pt.hist = pl->d_hist[pl->cur];
+    pt.chunk_bytes = pl->chunk_bytes;
+    pt.hist_bytes = pl->hist_bytes;
+    pt.H = pl->H;
+    pt.L = pl->L;
+    pt.N = pl->N;
+    pt.N2 = pl->N2;
+    pt.M = pl->M;
+    pt.m0 = m0;
+    pt.t_in = first_sample;
+    pt.a_spectra = pl->SL;
+    pt.n_streams = pl->n_streams;
+    pt.splits = pl->tc_splits;
+    pt.bmat = pl->d_bmat;
+    pt.oscale = pl->d_oscale;
+    pt.ctab = pl->d_ctab;
+    pt.window_tap = d_window_tap;
+    pt.err = pl->d_err;
 
     // Slab pipeline: slab s uses intermediate buffer s % 2; phase 1 runs on
     // internal stream 0, phase 2 on internal stream 1, so phase 1 of slab
@@ -595,8 +625,12 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
         p1.A = A;
         p1.q_begin = qb;
         p1.q_count = qc;
+        pt.A = A;
+        pt.q_begin = qb;
+        pt.q_count = qc;
         prof_begin(pl, 1, pl->sp[0]);
-        if ((e = fe::launch_phase1(pl->T, pl->N1, p1, pl->n_streams, pl->sp[0])) != cudaSuccess)
+        if ((e = pl->tc1 ? fe::launch_phase1_tc(pl->T, pl->precision, pt, pl->sp[0])
+                         : fe::launch_phase1(pl->T, pl->N1, p1, pl->n_streams, pl->sp[0])) != cudaSuccess)
             return cuda_fail(e, "phase-1 launch");
         prof_end(pl, pl->sp[0]);
         if ((e = cudaEventRecord(pl->ev_p1[b], pl->sp[0])) != cudaSuccess ||
@@ -606,8 +640,7 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
         p2.q_begin = qb;
         p2.q_count = qc;
         prof_begin(pl, 2, pl->sp[1]);
-        if ((e = pl->precision != FENGINE_FP32 ? fe::launch_phase2_tc(p2, pl->n_ant, pl->sp[1])
-                                               : fe::launch_phase2(pl->N2, p2, pl->n_ant, pl->sp[1])) != cudaSuccess)
+        if ((e = fe::launch_phase2(pl->N2, p2, pl->n_ant, pl->sp[1])) != cudaSuccess)
             return cuda_fail(e, "phase-2 launch");
         prof_end(pl, pl->sp[1]);
         if ((e = cudaEventRecord(pl->ev_p2[b], pl->sp[1])) != cudaSuccess)

@@ -13,9 +13,14 @@
 namespace {
 
 bool split_ok(long long N, int N1, int precision) {
+    if (precision != FENGINE_FP32) {
+        // tensor-core phase 1: radix 8 R with R physical columns per output
+        // column, the only split (N2 = N / N1 <= 1024)
+        const long long P = N / 8;
+        return N1 == 8 * (P > 1024 ? P / 1024 : 1);
+    }
     if (N % N1 || N / N1 > 1024 || N / N1 < 4) return false;
-    if (N1 > 8 && N / N1 < 512 / N1) return false;
-    return precision == FENGINE_FP32 || N / N1 == 1024;
+    return !(N1 > 8 && N / N1 < 512 / N1);
 }
 
 }  // namespace

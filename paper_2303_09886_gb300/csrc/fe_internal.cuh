@@ -7,9 +7,11 @@
 //   k_phase2w       1024-point FFT over t2 + fine-delay rotation + gain +
 //                   requantise + channel-major corner turn (FP32 form,
 //                   persistent, one warp per sequence), or
-//   k_phase2<N2>    the same for N2 < 1024 (FP32 form), or
-//   k_phase2_tc     the same with the 1024-point FFT as two 32-point DFT
-//                   contractions on tensor cores (FP16 / BF16 forms)
+//   k_phase2<N2>    the same for N2 < 1024
+// In the reduced-precision forms phase 1 is k_phase1_tc (tcgen05 tensor
+// cores: unpack + coarse delay + FIR + first DFT stage with its twiddle in one
+// contraction); the second stage reads its FP16 (FP16 form) or FP32 (BF16
+// form) output.
 //   k_tail_update   keep the last H packed samples of every stream
 // with the four-step split t = N2 t1 + t2, k = k1 + N1 k2 of the 2n-point
 // real DFT (the exp(-2 pi i k1 t2 / N) cross term is the twiddle).
@@ -17,6 +19,8 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include <vector>
 
 namespace fe {
 
@@ -74,9 +78,8 @@ struct Phase2Params {
     int N, N1, M, S, R2;      // FFT length, first-stage size, spectra/call, spectra/heap, spectra/CTA
     int8_t *out;              // [ant][heap][n][S_h][pol][2]
     float2 *prequant;         // optional [stream][M][n]
-    int precision;            // 0 FP32 CUDA cores, 1 FP16 / 2 BF16 tensor-core second stage
-    const uint4 *tc;          // tensor-core tables (build_phase2_tc_tables), precision != 0
-    float tc_unscale;         // inverse of the scale the reduced-precision path carries
+    int half_in;              // 1: A holds FP16 (re, im) pairs (tensor-core phase 1, FP16 form)
+    float tc_unscale;         // inverse of the power-of-two scale of an FP16 A (1 otherwise)
 };
 
 // Launchers (return cudaGetLastError() of the launch).
@@ -105,14 +108,34 @@ inline int phase2_R2(int N2) {
 }
 size_t phase2_smem_bytes(int N2, int R2);
 
-// Reduced-precision second stage (N2 = 1024 only): two 32-point DFT
-// contractions on tensor cores. The tables hold the DFT matrices as per-lane
-// mma fragments (hi and lo parts) and the 32 x 32 twiddle (times 2^-5);
-// kPhase2TcTableLen uint4 entries, built on the host for precision 1 (FP16)
-// or 2 (BF16).
-constexpr int kPhase2TcTableLen = 2560;
-void build_phase2_tc_tables(int precision, uint4 *out);
-size_t phase2_tc_smem_bytes(int precision);
-cudaError_t launch_phase2_tc(const Phase2Params &p, int n_ant, cudaStream_t s);
+// Phase 1 of the reduced-precision forms on tcgen05 tensor cores
+// (k_phase1_tc.cu): first-stage radix N1 = 8 R with R = phase1_tc_R(N), so
+// N2 = N / N1 <= 1024; the output is the second-stage input
+// [stream][a_spectra][N1/2 + 1][N2] as FP16 pairs (FP16 form, scaled by
+// s_int) or FP32 pairs (BF16 form).
+struct Phase1TcParams {
+    const uint8_t *chunk;     // [stream][chunk_bytes]
+    const uint8_t *hist;      // [stream][hist_bytes], samples [t_in - H, t_in)
+    long long chunk_bytes, hist_bytes;
+    long long H, L;           // history samples, chunk samples
+    int N, N2;                // FFT length, second-stage size
+    int M;                    // spectra per call
+    long long m0, t_in;       // first spectrum of the call, first sample of the chunk
+    int q_begin, q_count;     // the slab of spectra this launch covers
+    int a_spectra;            // spectra per stream in the intermediate buffer
+    int n_streams, splits;    // item ranges per column group (grid = column groups x splits)
+    const uint16_t *bmat;     // operand blocks, build_phase1_tc_tables
+    const float *oscale;      // [N2] epilogue scale per output column
+    const int *ctab;          // [stream][M] coarse delays
+    void *A;                  // out: second-stage input
+    int *window_tap;          // optional out [stream][M][N]
+    int *err;                 // set to 2 if a bounded wait gave up
+};
+int phase1_tc_R(int N);
+bool phase1_tc_supported(int N, int T, int precision);
+size_t phase1_tc_smem_bytes(int R, int T, int precision);
+void build_phase1_tc_tables(int N, int T, int precision, const float *w, std::vector<uint16_t> &bmat,
+                            std::vector<float> &oscale, float &s_int);
+cudaError_t launch_phase1_tc(int T, int precision, const Phase1TcParams &p, cudaStream_t s);
 
 }  // namespace fe

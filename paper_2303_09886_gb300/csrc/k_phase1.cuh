@@ -266,16 +266,7 @@ cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t 
 
 template <int T>
 cudaError_t launch_phase1_n1(int N1, const Phase1Params &p, int n_streams, cudaStream_t s) {
-    if (p.half_out) {
-        // FP16 intermediate: the splits with a 1024-point second stage
-        switch (N1 * 1000 + p.W) {
-            case 8064: return launch_phase1_tw<T, 8, 64, true>(p, n_streams, s);
-            case 16032: return launch_phase1_tw<T, 16, 32, true>(p, n_streams, s);
-            case 32016: return launch_phase1_tw<T, 32, 16, true>(p, n_streams, s);
-            case 64008: return launch_phase1_tw<T, 64, 8, true>(p, n_streams, s);
-            default: return cudaErrorInvalidValue;
-        }
-    }
+    if (p.half_out) return cudaErrorInvalidValue;   // FP16 output: unused by the FP32 form
     switch (N1 * 1000 + p.W) {
         case 8064: return launch_phase1_tw<T, 8, 64>(p, n_streams, s);
         case 16032: return launch_phase1_tw<T, 16, 32>(p, n_streams, s);

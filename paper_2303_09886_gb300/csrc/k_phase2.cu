@@ -24,6 +24,8 @@
 //
 // The CTA writes, for each of its channels, R2 consecutive spectra x 2 pols
 // x (re, im) = 4 R2 contiguous bytes of one heap row.
+#include <cuda_fp16.h>
+
 #include "fe_device.cuh"
 #include "fe_internal.cuh"
 
@@ -154,7 +156,7 @@ __device__ __forceinline__ int dif_pos(int k2) {
 
 }  // namespace
 
-template <int N2>
+template <int N2, bool HALF_IN>
 __global__ void __launch_bounds__(kP2Threads, 3) k_phase2(const Phase2Params p) {
     using S = P2Shape<N2>;
     constexpr int R2 = S::R2, LD = S::LD;
@@ -184,10 +186,18 @@ __global__ void __launch_bounds__(kP2Threads, 3) k_phase2(const Phase2Params p) 
             const int sq = e / (N2 / 2), t2 = 2 * (e % (N2 / 2));
             const int pol = sq / R2, r = sq % R2;
             v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (e < R2 * N2 && r < Rv)
-                v[u] = __ldg(reinterpret_cast<const float4 *>(
-                    p.A + (((long long)(ant * 2 + pol) * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) + k1) * N2 +
-                    t2));
+            const long long o =
+                (((long long)(ant * 2 + pol) * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) + k1) * N2 + t2;
+            if (e < R2 * N2 && r < Rv) {
+                if constexpr (HALF_IN) {
+                    const uint2 h = __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const uint32_t *>(p.A) + o));
+                    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&h.x));
+                    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&h.y));
+                    v[u] = make_float4(a.x, a.y, b.x, b.y);
+                } else {
+                    v[u] = __ldg(reinterpret_cast<const float4 *>(p.A + o));
+                }
+            }
         }
 #pragma unroll
         for (int u = 0; u < PER; u++) {
@@ -210,7 +220,9 @@ __global__ void __launch_bounds__(kP2Threads, 3) k_phase2(const Phase2Params p) 
         if (which < S::HI) {
             const float kk = (float)(k1 + N1 * S::LO * which);
             sincospif(f.y - f.x * kk * inv, &sn, &cs);
-            thi[sq * HP + which] = make_float2(cs, sn);
+            // with the inverse of the FP16 intermediate's scale (a power of two)
+            const float us = HALF_IN ? p.tc_unscale : 1.0f;
+            thi[sq * HP + which] = make_float2(cs * us, sn * us);
         } else if (which < S::HI + S::LO) {
             const int b = which - S::HI;
             sincospif(-f.x * (float)(N1 * b) * inv, &sn, &cs);
@@ -278,17 +290,22 @@ size_t phase2_smem_bytes(int N2, int R2) {
            (sizeof(long long) + sizeof(int)) * R2;
 }
 
-template <int N2>
-static cudaError_t launch_p2(const Phase2Params &p, int n_ant, cudaStream_t s) {
+template <int N2, bool HALF_IN>
+static cudaError_t launch_p2h(const Phase2Params &p, int n_ant, cudaStream_t s) {
     const int R2 = P2Shape<N2>::R2;
     if (p.R2 != R2) return cudaErrorInvalidValue;
     const size_t smem = phase2_smem_bytes(N2, R2);
-    cudaError_t e = cudaFuncSetAttribute(k_phase2<N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_phase2<N2, HALF_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(p.N1 / 2 + 1, (p.q_count + R2 - 1) / R2, n_ant);
-    k_phase2<N2><<<grid, kP2Threads, smem, s>>>(p);
+    k_phase2<N2, HALF_IN><<<grid, kP2Threads, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int N2>
+static cudaError_t launch_p2(const Phase2Params &p, int n_ant, cudaStream_t s) {
+    return p.half_in ? launch_p2h<N2, true>(p, n_ant, s) : launch_p2h<N2, false>(p, n_ant, s);
 }
 
 cudaError_t launch_phase2(int N2, const Phase2Params &p, int n_ant, cudaStream_t s) {

@@ -24,6 +24,8 @@
 // k1 = 1 .. N1/2 - 1 only) the conjugate of channel N - (k1 + N1 k2).
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "fe_device.cuh"
 #include "fe_internal.cuh"
 
@@ -81,6 +83,7 @@ size_t phase2w_smem_bytes() {
 // the next item's sequence is issued as soon as the buffer has been read
 // (after the transpose), so it runs under this item's second DFT, epilogue
 // and corner turn.
+template <bool HALF_IN>
 __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, int n_ant) {
     extern __shared__ float2 smw[];
     float2 *sbuf = smw;                                                   // [8][kWN2]
@@ -124,13 +127,22 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
     float2 *mybuf = sbuf + warp * kWN2;
 
     // this warp's sequence of item it into its buffer (lane: 16-byte chunks lane + 32 i)
+    // (FP16 pairs: 4 KB in the first half of the buffer)
     auto fetch = [&](int it) {
         const WItem w = witem(p, it, H1, G);
         if (w.q0 + r < p.q_begin + p.q_count) {
-            const float2 *src =
-                p.A + ((long long)((w.ant * 2 + pol) * p.a_spectra + (w.q0 - p.q_begin) + r) * (H1 + 1) + w.k1) * kWN2;
+            const long long e0 =
+                ((long long)((w.ant * 2 + pol) * p.a_spectra + (w.q0 - p.q_begin) + r) * (H1 + 1) + w.k1) * kWN2;
+            if constexpr (HALF_IN) {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(p.A) + e0;
+                uint32_t *dst = reinterpret_cast<uint32_t *>(mybuf);
 #pragma unroll
-            for (int i = 0; i < 16; i++) cp_async16(mybuf + 2 * (lane + 32 * i), src + 2 * (lane + 32 * i));
+                for (int i = 0; i < 8; i++) cp_async16(dst + 4 * (lane + 32 * i), src + 4 * (lane + 32 * i));
+            } else {
+                const float2 *src = p.A + e0;
+#pragma unroll
+                for (int i = 0; i < 16; i++) cp_async16(mybuf + 2 * (lane + 32 * i), src + 2 * (lane + 32 * i));
+            }
         }
         cp_async_commit();
     };
@@ -174,7 +186,9 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
             else ang = 2.0f * f.y - 2.0f * f.x;
             float sn, cs;
             sincospif(ang, &sn, &cs);
-            pq[e] = make_float2(cs, sn);
+            // P carries the inverse of the FP16 intermediate's scale (a power of two)
+            const float u = (HALF_IN && j < 32) ? p.tc_unscale : 1.0f;
+            pq[e] = make_float2(cs * u, sn * u);
         }
         if (ant * 1024 + k1 != cur) {
             cur = ant * 1024 + k1;
@@ -201,8 +215,14 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
         __syncwarp();
         float2 z[32];
         if (active) {
+            if constexpr (HALF_IN) {
+                const __half2 *hb = reinterpret_cast<const __half2 *>(mybuf);
 #pragma unroll
-            for (int a = 0; a < 32; a++) z[a] = mybuf[32 * a + lane];
+                for (int a = 0; a < 32; a++) z[a] = __half22float2(hb[32 * a + lane]);
+            } else {
+#pragma unroll
+                for (int a = 0; a < 32; a++) z[a] = mybuf[32 * a + lane];
+            }
             __syncwarp();
             fft_regc<32>(z);                                  // z[c] = Y[c][lane]
 #pragma unroll
@@ -275,21 +295,28 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
     cp_async_wait_all();   // nothing is left in flight when the CTA exits
 }
 
-cudaError_t launch_phase2w(const Phase2Params &p, int n_ant, cudaStream_t s) {
-    if (p.N / p.N1 != kWN2) return cudaErrorInvalidValue;
+template <bool HALF_IN>
+static cudaError_t launch_w(const Phase2Params &p, int n_ant, cudaStream_t s) {
     const size_t smem = phase2w_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_phase2w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_phase2w<HALF_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase2w, kWThreads, smem)) != cudaSuccess)
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase2w<HALF_IN>, kWThreads, smem)) !=
+            cudaSuccess)
         return e;
     const long long items = (long long)n_ant * (p.N1 / 2 + 1) * ((p.q_count + kWR - 1) / kWR);
     if (items <= 0) return cudaSuccess;
     const int ctas = (int)std::min<long long>(items, (long long)sms * std::max(per_sm, 1));
-    k_phase2w<<<ctas, kWThreads, smem, s>>>(p, n_ant);
+    k_phase2w<HALF_IN><<<ctas, kWThreads, smem, s>>>(p, n_ant);
     return cudaGetLastError();
+}
+
+cudaError_t launch_phase2w(const Phase2Params &p, int n_ant, cudaStream_t s) {
+    if (p.N / p.N1 != kWN2) return cudaErrorInvalidValue;
+    return p.half_in ? launch_w<true>(p, n_ant, s) : launch_w<false>(p, n_ant, s);
 }
 
 }  // namespace fe

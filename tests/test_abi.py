@@ -74,8 +74,9 @@ def test_quantiser_matches_oracle_on_every_tie_and_neighbour(lib):
     (dict(chunk_samples=1000), 1), (dict(spectra_per_heap=10 ** 6), 1),
     (dict(max_delay_samples=-1), 1), (dict(n_antennas=0), 1),
     (dict(fft_n1=12), 1), (dict(fft_n1=128), 1), (dict(fft_n1=2), 1), (dict(slab_spectra=33), 1),
-    (dict(slab_spectra=-32), 1), (dict(precision=1), 7), (dict(precision=2, n_channels=2048), 7),
-    (dict(precision=1, n_channels=8192, fft_n1=32, chunk_samples=16384 * 4), 7)])
+    (dict(slab_spectra=-32), 1), (dict(precision=1, n_channels=16, chunk_samples=32 * 8), 7),
+    (dict(precision=2, n_channels=16, chunk_samples=32 * 8), 7),
+    (dict(precision=1, n_channels=8192, fft_n1=32, chunk_samples=16384 * 4), 1)])
 def test_plan_config_validation_before_any_device_call(lib, kw, status):
     cfg = dict(n_antennas=1, n_pols=2, n_channels=1024, n_taps=16, chunk_samples=2048 * 8,
                spectra_per_heap=0, precision=0, max_delay_samples=0, weights=None, fft_n1=0, slab_spectra=0)

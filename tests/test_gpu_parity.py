@@ -135,11 +135,11 @@ def test_identity_weights_give_the_plain_dft_of_the_window():
 @pytest.mark.parametrize("precision,spectra,heap", [(fengine.TC_FP16, 40, 16), (fengine.TC_BF16, 40, 16),
                                                     (fengine.TC_FP16, 37, 12), (fengine.TC_BF16, 37, 12)])
 def test_reduced_precision_forms(precision, spectra, heap):
-    """Tensor-core DFT stages (FP16 / BF16 operands, FP32 accumulation):
-    pre-quantisation relative RMS <= 2e-3 against the FP64 oracle, 8-bit
-    output within 1 LSB; 8192 channels, 16 taps, random delays and gains.
-    37 spectra per call leave a ragged last tile of the second stage, and
-    heaps of 12 spectra split its 8-spectrum tiles across heap rows."""
+    """Tensor-core FIR + first DFT stage (FP16 / BF16 operands, FP32
+    accumulation): pre-quantisation relative RMS <= 2e-3 against the FP64
+    oracle, 8-bit output within 1 LSB; 8192 channels, 16 taps, random delays
+    and gains. 37 spectra per call leave a ragged last tile, and heaps of 12
+    spectra split the second stage's 4-spectrum items across heap rows."""
     from tests.fe_harness import REL_RMS_REDUCED
     n, T, L = 8192, 16, 16384 * spectra
     g = np.random.default_rng(15)
@@ -157,7 +157,7 @@ def test_reduced_precision_forms(precision, spectra, heap):
 
 def test_reduced_precision_rejects_unsupported_shapes():
     with pytest.raises(fengine.FEngineError) as e:
-        fengine.Plan(1, 1024, 16, 2048 * 8, precision=fengine.TC_FP16)
+        fengine.Plan(1, 16, 16, 32 * 8, precision=fengine.TC_FP16)
     assert e.value.status == 7
 
 
