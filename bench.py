@@ -46,7 +46,7 @@ KERNEL_SOURCES = {
     "k_phase1": ['k_phase1.cuh', 'k_phase1_t1.cu', 'k_phase1_t2.cu', 'k_phase1_t4.cu', 'k_phase1_t8.cu', 'k_phase1_t16.cu', 'k_phase1_t32.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase2": ['k_phase2.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase2w": ['k_phase2w.cu', 'fe_device.cuh', 'fe_internal.cuh'],
-    "k_phase2_tc": ['k_phase2_tc.cu', 'fe_mma.cuh', 'fe_device.cuh', 'fe_internal.cuh'],
+    "k_phase1_tc": ['k_phase1_tc.cu', 'fe_device.cuh', 'fe_internal.cuh'],
 }
 _CAPTURED = 33554432   # input samples of the captured launch
 NCU_TRAFFIC = {
@@ -55,8 +55,6 @@ NCU_TRAFFIC = {
     "k_phase1<16,64,8,0>": {"bytes_per_sample": (44158464 + 89049344) / _CAPTURED, "src": "11552148f7285605"},
     "k_phase2w": {"bytes_per_sample": (166702080 + 19888640) / _CAPTURED, "src": "25eaca44b1835be4"},
     "k_phase2<256>": {"bytes_per_sample": (138605824 + 13872896) / _CAPTURED, "src": "4b85a31bd47bd8c3"},
-    "k_phase2_tc<1>": {"bytes_per_sample": (75749888 + 9130240) / _CAPTURED, "src": "2bb83c4f67d0b965"},
-    "k_phase2_tc<2>": {"bytes_per_sample": (151278336 + 19053056) / _CAPTURED, "src": "2bb83c4f67d0b965"},
 }
 
 
@@ -654,9 +652,11 @@ def main(argv=None):
     achieved = bytes_per_sample[dom] * (spl / slabs) / (launch_ms / 1e3) / 1e9
     N2 = plan.info.fft_n2
     half = 1 if args.precision == "fp16" else 0
-    kname = {"phase1": f"k_phase1<{wl.n_taps},{N1},{min(512 // N1, N2)},{half}>",
-             "phase2": {"fp32": "k_phase2w" if N2 == 1024 else f"k_phase2<{N2}>", "fp16": "k_phase2_tc<1>",
-                        "bf16": "k_phase2_tc<2>"}[args.precision]}[dom]
+    R_tc = N1 // 8
+    kname = {"phase1": (f"k_phase1<{wl.n_taps},{N1},{min(512 // N1, N2)},0>" if args.precision == "fp32"
+                        else f"k_phase1_tc<{R_tc},{wl.n_taps},{1 if args.precision == 'fp16' else 2}>"),
+             "phase2": ("k_phase2w" if N2 == 1024 else f"k_phase2<{N2}>")
+             + ("" if args.precision != "fp16" else "<half>")}[dom]
     tr = NCU_TRAFFIC.get(kname)
     # scaled from the captured launch to this launch by its input samples
     # (the kernels' DRAM traffic grows in proportion to the samples processed)

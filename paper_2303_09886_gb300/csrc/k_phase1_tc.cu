@@ -254,6 +254,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
 
     // ---- pass generation (every thread computes the same sequence) ----
     int it = it_begin, ra = -1, rows = 0, st = 0, q0 = 0, uniform = 0;
+    // coarse delay of row tid of an item, loaded one item ahead
+    auto item_delay = [&](int item) -> int {
+        const int s2 = item / n_tiles, qq = p.q_begin + (item % n_tiles) * kTcRows;
+        return (item < it_end && qq + tid < p.q_begin + p.q_count && tid < kTcRows)
+                   ? __ldg(p.ctab + (long long)s2 * p.M + qq + tid)
+                   : 0;
+    };
+    int c_pref = item_delay(it);
     auto next_pass = [&](Pass &ps) -> bool {
         for (;;) {
             if (ra < 0) {
@@ -261,8 +269,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
                 st = it / n_tiles;
                 q0 = p.q_begin + (it % n_tiles) * kTcRows;
                 rows = min(kTcRows, p.q_begin + p.q_count - q0);
+                const int c_this = c_pref;
+                c_pref = item_delay(it + 1);
                 __syncthreads();   // the previous item's delays are no longer read
-                if (tid < rows) c_sm[tid] = __ldg(p.ctab + (long long)st * p.M + q0 + tid);
+                if (tid < rows) c_sm[tid] = c_this;
                 __syncthreads();
                 uniform = __syncthreads_and(tid >= rows || c_sm[tid] == c_sm[0]);
                 ra = 0;
@@ -286,35 +296,74 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
     };
 
     // ---- decode of one pass into data buffer b ----
-    auto decode = [&](const Pass &ps, int b) {
-        uint16_t *xb = xsm + (size_t)(b % NXB) * NPL * kTcPhys * XL;
-        // position (from the first history sample) of row v = 0 at column t = 0
-        const long long base = (long long)p.N * (p.m0 + ps.q0) - (p.t_in - H) - ps.c;
+    // Fast path (the pass's samples all inside the chunk): a thread takes
+    // (run j, rows v and v + 1) items, a run being CW consecutive columns of
+    // one row; its packed words are loaded into registers by fetch() one
+    // step ahead (under the previous pass's epilogue), and decode() converts
+    // them into 16-bit samples in shared memory.
+    constexpr int NIT = R * (XL / 2);                              // items per pass
+    constexpr int MAXI = (NIT + kTcThreads - 1) / kTcThreads;      // items per thread
+    constexpr int NW = (30 + 10 * CW) / 32 + 1;                    // words covering a run at any bit offset
+    constexpr int PFI = MAXI * 2 * NW <= 40 ? MAXI : 40 / (2 * NW);   // items prefetched into registers
+    uint32_t rw[PFI][2][NW];
+    // position (from the first history sample) of row v = 0 at column t = 0
+    auto pass_base = [&](const Pass &ps) -> long long {
+        return (long long)p.N * (p.m0 + ps.q0) - (p.t_in - H) - ps.c;
+    };
+    auto is_fast = [&](const Pass &ps) -> bool {
+        const long long base = pass_base(ps);
         const long long lo = base + cg * CW, hi = base + cg * CW + (long long)N2 * (R - 1) + CW +
                                                   (long long)P * (XL - 1);
-        const bool fast = lo >= H && hi < HL - 16 && !p.window_tap;
+        return lo >= H && hi < HL - 16 && !p.window_tap;
+    };
+    // bit position (from the chunk start) of the first bit of item e's row rr
+    auto item_bit = [&](long long base, int e, int rr) -> long long {
+        const int j = e / (XL / 2), v = 2 * (e - j * (XL / 2));
+        return 10 * (base - H + cg * CW + (long long)N2 * j + (long long)P * (v + rr));
+    };
+    auto fetch = [&](const Pass &ps, bool fast) {
+        if (!fast) return;
+        const uint32_t *w32 = reinterpret_cast<const uint32_t *>(p.chunk + (long long)ps.st * p.chunk_bytes);
+        const long long base = pass_base(ps);
+#pragma unroll
+        for (int i = 0; i < PFI; i++) {
+            const int e = tid + i * kTcThreads;
+            if (e < NIT) {
+#pragma unroll
+                for (int rr = 0; rr < 2; rr++) {
+                    const uint32_t *wp = w32 + (item_bit(base, e, rr) >> 5);
+#pragma unroll
+                    for (int k = 0; k < NW; k++) rw[i][rr][k] = __ldg(wp + k);
+                }
+            }
+        }
+    };
+    auto decode = [&](const Pass &ps, int b, bool fast) {
+        uint16_t *xb = xsm + (size_t)(b % NXB) * NPL * kTcPhys * XL;
+        const long long base = pass_base(ps);
         if (fast) {
-            // a thread takes two rows (v, v + 1) of one run of CW consecutive columns
-            const uint8_t *chunk = p.chunk + (long long)ps.st * p.chunk_bytes;
-            const uint32_t *w32 = reinterpret_cast<const uint32_t *>(chunk);
-            constexpr int NW = (30 + 10 * CW) / 32 + 1;   // words covering a run at any bit offset
-            for (int e = tid; e < R * (XL / 2); e += kTcThreads) {
+            const uint32_t *w32 = reinterpret_cast<const uint32_t *>(p.chunk + (long long)ps.st * p.chunk_bytes);
+#pragma unroll
+            for (int i = 0; i < MAXI; i++) {
+                const int e = tid + i * kTcThreads;
+                if (e >= NIT) break;
                 const int j = e / (XL / 2), v = 2 * (e - j * (XL / 2));
                 uint32_t f[2][CW];
 #pragma unroll
                 for (int rr = 0; rr < 2; rr++) {
-                    const long long pos = base - H + cg * CW + (long long)N2 * j + (long long)P * (v + rr);
-                    const long long bit = 10 * pos;
-                    const uint32_t *wp = w32 + (bit >> 5);
+                    const long long bit = item_bit(base, e, rr);
                     const int off = (int)(bit & 31);
                     // big-endian words, then shifted so that bit 0 is the run's first bit:
                     // field c sits at the compile-time bit 10 c
                     uint32_t w[NW + 1], a[NW];
 #pragma unroll
-                    for (int i = 0; i < NW; i++) w[i] = __byte_perm(__ldg(wp + i), 0u, 0x0123u);
+                    for (int k = 0; k < NW; k++) {
+                        const uint32_t raw = i < PFI ? rw[i < PFI ? i : 0][rr][k] : __ldg(w32 + (bit >> 5) + k);
+                        w[k] = __byte_perm(raw, 0u, 0x0123u);
+                    }
                     w[NW] = 0u;
 #pragma unroll
-                    for (int i = 0; i < NW; i++) a[i] = __funnelshift_l(w[i + 1], w[i], (unsigned)off);
+                    for (int k = 0; k < NW; k++) a[k] = __funnelshift_l(w[k + 1], w[k], (unsigned)off);
 #pragma unroll
                     for (int c = 0; c < CW; c++) {
                         const int bb = 10 * c;
@@ -324,14 +373,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
                 }
 #pragma unroll
                 for (int c = 0; c < CW; c++) {
-                    const int i = j * CW + c;
+                    const int i2 = j * CW + c;
                     if constexpr (PREC == 2) {
                         uint32_t h, l;
                         ints_to_bf16x2(field_value(f[0][c]), field_value(f[1][c]), h, l);
-                        *reinterpret_cast<uint32_t *>(xb + (size_t)i * XL + v) = h;
-                        *reinterpret_cast<uint32_t *>(xb + (size_t)(kTcPhys + i) * XL + v) = l;
+                        *reinterpret_cast<uint32_t *>(xb + (size_t)i2 * XL + v) = h;
+                        *reinterpret_cast<uint32_t *>(xb + (size_t)(kTcPhys + i2) * XL + v) = l;
                     } else {
-                        *reinterpret_cast<uint32_t *>(xb + (size_t)i * XL + v) = fields_to_half2(f[0][c], f[1][c]);
+                        *reinterpret_cast<uint32_t *>(xb + (size_t)i2 * XL + v) = fields_to_half2(f[0][c], f[1][c]);
                     }
                 }
             }
@@ -444,12 +493,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
     };
 
     // ---- the pipeline ----
-    Pass cur{}, prev{};
+    Pass cur{}, prev{}, nxt{};
     bool have_prev = false;
     int b = 0;
     uint32_t parity = 0u;   // bit k: next phase parity of mbar[k]
     bool aborted = false;
-    while (next_pass(cur)) {
+    bool have_cur = next_pass(cur);
+    bool fast_cur = have_cur && is_fast(cur);
+    if (have_cur) fetch(cur, fast_cur);
+    while (have_cur) {
         if (NXB == 1 && have_prev) {
             // one decode buffer: the previous pass's MMAs must have read it
             // (the epilogue's wait below returns at once for this phase)
@@ -458,7 +510,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
                 atomicExch(p.err, 2);
             }
         }
-        decode(cur, b);
+        decode(cur, b, fast_cur);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
         __syncthreads();
@@ -469,6 +521,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
         }
         if (tid == 0) issue(b);
         __syncwarp();
+        // the next pass's packed words are in flight during this epilogue
+        const bool have_nxt = next_pass(nxt);
+        const bool fast_nxt = have_nxt && is_fast(nxt);
+        if (have_nxt) fetch(nxt, fast_nxt);
         if (have_prev) {
             const int pb = b ^ 1;
             const bool ok = mbar_wait(smem_addr(&mbar[pb]), (parity >> pb) & 1u);
@@ -484,6 +540,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
         prev = cur;
         have_prev = true;
         b ^= 1;
+        cur = nxt;
+        have_cur = have_nxt;
+        fast_cur = fast_nxt;
     }
     if (have_prev && !aborted) {
         const int pb = b ^ 1;
