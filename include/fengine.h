@@ -38,8 +38,10 @@
 extern "C" {
 #endif
 
-#define FENGINE_ABI_VERSION 2
+#define FENGINE_ABI_VERSION 3
 #define FENGINE_MAX_DELAY_SEGMENTS 16
+#define FENGINE_MAX_GAIN_SETS 4        /* gain sets per stream pending at once */
+#define FENGINE_HEAP_SAMPLES 4096      /* samples per digitiser heap (Sec. 2.2) */
 
 typedef enum {
     FENGINE_OK = 0,
@@ -50,28 +52,29 @@ typedef enum {
     FENGINE_EBUSY = 5,        /* no free slot / over the memory budget */
     FENGINE_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
     FENGINE_EUNSUPPORTED = 7, /* valid request this build does not implement */
-    FENGINE_EDELAY = 8        /* a coarse delay of this call leaves [0, max_delay] */
+    FENGINE_EDELAY = 8        /* a coarse delay of this call leaves [min_delay, max_delay] */
 } fengine_status;
 
-/* Precision forms. The reduced-precision forms run the N2 = 1024-point
- * second DFT stage as two 32-point DFT contractions on tensor cores (FP32
- * accumulation). The DFT matrices and the data between the contractions are
- * carried as hi + lo operand pairs (and the BF16 form's FP32 input too), so
- * that a strong tone does not leave errors of more than a fraction of an
- * 8-bit LSB in the other channels of its class; the FP16 form stores the
- * intermediate between the two phases as FP16 pairs. They need a split with
- * N2 = 1024, i.e. n_channels >= 4096 (FENGINE_EUNSUPPORTED otherwise).
- * Pre-quantisation spectra stay within 2e-3 relative RMS of the FP64
- * oracle (measured: FP16 2.1-2.3e-4, BF16 4.6-5.2e-6), 8-bit outputs within
- * 1 LSB. */
+/* Precision forms. The reduced-precision forms run the unpack, the coarse
+ * delay, the PFB FIR (Eq. 1) and the first DFT stage (radix 8 R, with its
+ * twiddle) as one contraction per FIR column on the tensor cores (tcgen05,
+ * FP32 accumulation in tensor memory): the 10-bit samples are exact in FP16;
+ * the weights x DFT operand is scaled by a power of two per output column.
+ * The BF16 form carries samples and operand as hi + lo BF16 pairs (three
+ * products per step). The second DFT stage, delay, gain and requantisation
+ * run on CUDA cores in FP32, reading FP16 (FP16 form) or FP32 (BF16 form)
+ * pairs. n_channels >= 32 (FENGINE_EUNSUPPORTED otherwise). Pre-quantisation
+ * spectra stay within 2e-3 relative RMS of the FP64 oracle (measured: FP16
+ * 3-4e-4, BF16 3-4e-6), 8-bit outputs within 1 LSB. */
 typedef enum {
     FENGINE_FP32 = 0,    /* FP32 FIR and FFT on CUDA cores */
-    FENGINE_TC_FP16 = 1, /* reduced-precision form (FP16 operands, FP32 accumulation) */
-    FENGINE_TC_BF16 = 2  /* reduced-precision form (BF16 operands, FP32 accumulation) */
+    FENGINE_TC_FP16 = 1, /* FIR + first DFT stage on tensor cores, FP16 operands, FP32 accumulation */
+    FENGINE_TC_BF16 = 2  /* FIR + first DFT stage on tensor cores, BF16 hi + lo operands */
 } fengine_precision;
 
 /* Plan configuration (Sec. 2.1: channels and taps; Sec. 3.1: chunks;
- * Sec. 3.3: coarse delay range; Sec. 2.2: 256 spectra per output heap). */
+ * Sec. 3.3: coarse delay range, which may include negative delays;
+ * Sec. 2.2: 256 spectra per output heap). */
 typedef struct {
     int32_t n_antennas;        /* >= 1 */
     int32_t n_pols;            /* must be 2 (dual-polarisation F-engine) */
@@ -80,7 +83,7 @@ typedef struct {
     int64_t chunk_samples;     /* L per polarisation per call: a positive multiple of 2n */
     int32_t spectra_per_heap;  /* S: 1 <= S <= L/2n; 0 selects min(256, L/2n) */
     int32_t precision;         /* fengine_precision */
-    int64_t max_delay_samples; /* D >= 0: every coarse delay must lie in [0, D] */
+    int64_t max_delay_samples; /* D >= 0: every coarse delay must lie in [min_delay_samples, D] */
     const float *weights;      /* host, 2n*T prototype w[t + 2n j] (Eq. 1's w_{t,j});
                                   NULL = built-in Hann-windowed sinc, sum w^2 = 1 */
     /* Tuning knobs (no counterpart in the paper; 0 = built-in choice, see
@@ -90,7 +93,10 @@ typedef struct {
                                   with N2 <= 1024 (and N2 >= 512 / N1 for N1 > 8);
                                   built-in: max(8, N / 1024) */
     int32_t slab_spectra;      /* spectra per slab of the two-phase pipeline, a multiple
-                                  of 32; built-in: an FP32 intermediate of about 40 MiB */
+                                  of 32; built-in: an FP32 intermediate of about 256 MiB */
+    int64_t min_delay_samples; /* Dmin in [-2^30, 0]: the most negative coarse delay
+                                  (Sec. 3.3 allows negative delays). The plan emits
+                                  E = ceil(-Dmin / 2n) spectra later to make room. */
 } fengine_config;
 
 typedef struct fengine_plan_s *fengine_plan_t;
@@ -101,12 +107,15 @@ typedef struct {
     int32_t fft_n1, fft_n2;       /* four-step split N = n1 * n2 used on the device */
     int64_t spectra_per_chunk;    /* M = L / 2n: spectra every call emits per stream */
     int64_t history_samples;      /* H = 2n (T - 1) + D rounded up to a multiple of 16 */
-    int64_t latency_spectra;      /* T - 1: first spectrum of a call = first_sample/2n - (T-1) */
+    int64_t latency_spectra;      /* T - 1 + E: first spectrum of a call = first_sample/2n - (T-1+E) */
     int64_t out_bytes;            /* bytes of d_out per call: n_antennas * M * n * 4 */
     size_t device_bytes;          /* device memory the plan holds */
     size_t scratch_bytes;         /* part of device_bytes used as per-call scratch */
     int32_t slab_spectra;         /* spectra per slab of the two-phase pipeline (one launch pair) */
     int32_t slabs_per_chunk;      /* slabs (phase-1 + phase-2 launch pairs) per call */
+    int32_t heaps_per_chunk;      /* output heaps per antenna per call: ceil(M / S) */
+    int32_t lost_data;            /* 1 if lost-data flags are available (chunk_samples a
+                                     multiple of FENGINE_HEAP_SAMPLES) */
 } fengine_info;
 
 const char *fengine_strerror(fengine_status status);
@@ -146,11 +155,17 @@ fengine_status fengine_set_delay(fengine_plan_t plan, int32_t ant, int32_t pol,
                                  int64_t t_apply, int64_t t_ref, double delay,
                                  double delay_rate, double phase, double phase_rate);
 
-/* Per-channel complex bandpass gains of one stream (Sec. 2.1 step 5). host
- * array of n complex values as interleaved (re, im) floats. Takes effect from
- * the next fengine_process_chunk. */
+/* Per-channel complex bandpass gains of one stream (Sec. 2.1 step 5): host
+ * array of n complex values as interleaved (re, im) floats (copied), used
+ * for spectra with timestamp t0 >= t_apply, like a delay model (the paper
+ * gives no time rule; this is the library's reading). Up to
+ * FENGINE_MAX_GAIN_SETS sets per stream are kept, ordered by t_apply; a set
+ * with the same t_apply replaces the old one; sets that no later spectrum
+ * can use are dropped at the next call. Use a t_apply far in the past (or
+ * the next call's first spectrum timestamp) to apply gains at once.
+ * FENGINE_EINVAL for a bad index, non-finite gains or too many pending sets. */
 fengine_status fengine_set_gains(fengine_plan_t plan, int32_t ant, int32_t pol,
-                                 const float *gains_re_im);
+                                 const float *gains_re_im, int64_t t_apply);
 
 /* Forget the stream history: the next call may start at any first_sample,
  * and samples before it read as zero. */
@@ -161,8 +176,23 @@ fengine_status fengine_reset(fengine_plan_t plan);
  *                  [first_sample, first_sample + L) of each stream.
  *   first_sample   multiple of 2n; after the first call (or a reset) it must
  *                  equal the previous first_sample + L, else FENGINE_ESEQ.
+ *   d_valid        optional (NULL: every heap received) device
+ *                  [antenna][pol][L / FENGINE_HEAP_SAMPLES] bytes, nonzero
+ *                  where the digitiser heap of samples [first_sample + 4096 i,
+ *                  + 4096) arrived (Sec. 3.7). The plan keeps these flags for
+ *                  the history; samples no call delivered (before a stream's
+ *                  first chunk after creation or a reset) count as missing.
+ *   d_heap_flags   optional device [antenna][heaps_per_chunk] bytes out: 1 if
+ *                  every spectrum of the output heap is usable in both
+ *                  polarisations, 0 if a spectrum's PFB window touches a
+ *                  missing heap and the heap should not be transmitted
+ *                  (Sec. 3.7). d_out is written either way (missing samples
+ *                  are whatever d_packed holds). d_valid and d_heap_flags need
+ *                  chunk_samples and first_sample to be multiples of
+ *                  FENGINE_HEAP_SAMPLES (FENGINE_EINVAL); a call that is not
+ *                  leaves the history's flags unknown until fengine_reset.
  *   d_out          device, n_antennas * M * n * 4 bytes: for each antenna the
- *                  M = L/2n spectra m = first_sample/2n - (T-1) + q,
+ *                  M = L/2n spectra m = first_sample/2n - (T-1+E) + q,
  *                  q in [0, M), as heaps of S spectra (the last heap of a call
  *                  may hold fewer, S_h = min(S, M - h S)); heap h is the
  *                  array [k][s][pol][re, im] of int8 with q = h S + s
@@ -176,19 +206,27 @@ fengine_status fengine_reset(fengine_plan_t plan);
  *                  t in [0, 2n), that the first FIR tap of spectrum m uses.
  *   first_spectrum optional host out: the m of q = 0.
  * Every spectrum's window [2n m - c_m, 2n m - c_m + 2n T) lies in the data
- * this call and the plan's history hold, for every c_m in [0, D]; a delay
- * model that puts c_m outside [0, D] for a spectrum of this call is refused
- * with FENGINE_EDELAY before anything is enqueued. Asynchronous on
+ * this call and the plan's history hold, for every c_m in [Dmin, D]; a
+ * delay model that puts c_m outside [Dmin, D] for a spectrum of this call is
+ * refused with FENGINE_EDELAY before anything is enqueued. Asynchronous on
  * cuda_stream; the input may be reused once the stream passes this call. */
 fengine_status fengine_process_chunk(fengine_plan_t plan, void *cuda_stream,
                                      const uint8_t *d_packed, int64_t first_sample,
-                                     int8_t *d_out, float *d_prequant,
-                                     int32_t *d_window_tap, int64_t *first_spectrum);
+                                     const uint8_t *d_valid, int8_t *d_out, uint8_t *d_heap_flags,
+                                     float *d_prequant, int32_t *d_window_tap, int64_t *first_spectrum);
+
+/* Waits for the device (cudaDeviceSynchronize) and reports a device-side
+ * condition the plan's kernels recorded since the last call of this
+ * function: FENGINE_ETIMEOUT if a bounded wait in a tensor-core kernel gave
+ * up, FENGINE_EDELAY if a coarse delay had to be clamped (not reachable
+ * after the host-side range check), FENGINE_ECUDA on a CUDA error; clears
+ * the record. */
+fengine_status fengine_device_status(fengine_plan_t plan);
 
 /* ---- autotuning (no counterpart in the paper) ----
  *
- * Times every valid work split of cfg -- fft_n1 in {8, 16, 32, 64} (only
- * N / 1024 for the tensor-core forms) x slab_spectra in {built-in, 32, 64,
+ * Times every valid work split of cfg -- fft_n1 in {8, 16, 32, 64} (the
+ * tensor-core forms have one: 8 R) x slab_spectra in {built-in, 32, 64,
  * ..., 2048} (capped at the call's spectra) -- by creating a plan for it and
  * running `calls` calls (after
  * two warm-up calls) on zero-filled input on cuda_stream, timed with CUDA
@@ -217,6 +255,8 @@ typedef struct {
     const uint8_t *d_packed;
     int64_t first_sample;
     int8_t *d_out;
+    const uint8_t *d_valid;     /* optional, as fengine_process_chunk */
+    uint8_t *d_heap_flags;      /* optional, as fengine_process_chunk */
 } fengine_chunk_desc;
 
 /* A batch owns n_pool (1..64) internal CUDA streams. */
@@ -262,11 +302,14 @@ fengine_status fengine_service_create(const fengine_service_config *cfg, fengine
 
 /* Queue one chunk of `plan` from HOST memory: h_packed holds the plan's
  * [antenna][pol][5L/4] bytes (pinned memory lets the copy run
- * asynchronously), h_out receives info.out_bytes of 8-bit output. Both must
- * stay valid until fengine_service_wait returns for the ticket. The result
- * equals fengine_process_chunk's for the same chunk. */
+ * asynchronously), h_out receives info.out_bytes of 8-bit output; h_valid
+ * (optional) and h_heap_flags (optional) are host copies of
+ * fengine_process_chunk's d_valid and d_heap_flags. All must stay valid
+ * until fengine_service_wait returns for the ticket. The result equals
+ * fengine_process_chunk's for the same chunk. */
 fengine_status fengine_service_submit(fengine_service_t svc, fengine_plan_t plan, const uint8_t *h_packed,
-                                      int64_t first_sample, int8_t *h_out, int64_t *ticket);
+                                      int64_t first_sample, const uint8_t *h_valid, int8_t *h_out,
+                                      uint8_t *h_heap_flags, int64_t *ticket);
 
 /* fengine_set_delay / fengine_set_gains, applied in order with the plan's
  * queued chunks. */
@@ -274,7 +317,7 @@ fengine_status fengine_service_set_delay(fengine_service_t svc, fengine_plan_t p
                                          int64_t t_apply, int64_t t_ref, double delay, double delay_rate,
                                          double phase, double phase_rate);
 fengine_status fengine_service_set_gains(fengine_service_t svc, fengine_plan_t plan, int32_t ant, int32_t pol,
-                                         const float *gains_re_im);
+                                         const float *gains_re_im, int64_t t_apply);
 
 /* Wait up to timeout_ms (-1: no limit) for a chunk request; returns its
  * status (FENGINE_ETIMEOUT if still running; FENGINE_EBUSY if it can never

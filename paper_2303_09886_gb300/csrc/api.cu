@@ -47,10 +47,19 @@ struct fengine_plan_s {
     int n_ant = 0, n_streams = 0, n = 0, N = 0, T = 0, S = 0, M = 0, N1 = 0, N2 = 0, W = 0, C = 0, R2 = 0;
     int precision = 0;
     int a_elem = 8;                 // bytes per intermediate element
-    long long L = 0, D = 0, H = 0, chunk_bytes = 0, hist_bytes = 0;
+    long long L = 0, D = 0, Dmin = 0, H = 0, chunk_bytes = 0, hist_bytes = 0;
+    int E = 0;                      // emission lag (spectra) that makes room for negative delays
+    // lost data (Sec. 3.7): received flags of the history heaps, ping-pong with d_hist
+    bool lost_ok = false;           // chunk_samples a multiple of the 4096-sample heap
+    bool hv_known = true;           // the device history flags describe the current history
+    int HV = 0;
+    unsigned char *d_hvalid[2] = {nullptr, nullptr};
     // device state
     float *d_w = nullptr;
     float2 *d_tw1 = nullptr, *d_tw2 = nullptr, *d_gains = nullptr, *d_ftab = nullptr, *d_A = nullptr;
+    long long *d_gtap = nullptr;    // [stream][kMaxGainSeg] t_apply of each gain set
+    int *d_ngs = nullptr;           // [stream] gain sets in use
+    unsigned char *d_gsel = nullptr;   // [stream][M] gain set of each spectrum
     // reduced-precision forms: tensor-core phase-1 operand blocks and per-column epilogue scales
     uint16_t *d_bmat = nullptr;
     float *d_oscale = nullptr;
@@ -64,11 +73,17 @@ struct fengine_plan_s {
     size_t device_bytes = 0, scratch_bytes = 0;
     // host mirrors, pinned staging
     std::vector<std::vector<DelaySeg>> segs;
-    std::vector<float2> gains;
+    struct GainSet {
+        long long t_apply;
+        std::vector<float2> g;
+    };
+    std::vector<std::vector<GainSet>> gsets;   // [stream], sorted by t_apply
     bool delay_dirty = true, gains_dirty = true;
     DelaySeg *h_seg = nullptr;
     int *h_nseg = nullptr;
-    float2 *h_gains = nullptr;
+    float2 *h_gains = nullptr;      // [stream][kMaxGainSeg][n]
+    long long *h_gtap = nullptr;
+    int *h_ngs = nullptr;
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
     bool started = false;
@@ -108,12 +123,19 @@ void release(fengine_plan_s *pl) {
     cudaFree(pl->d_hist[0]);
     cudaFree(pl->d_hist[1]);
     cudaFree(pl->d_seg);
+    cudaFree(pl->d_gtap);
+    cudaFree(pl->d_ngs);
+    cudaFree(pl->d_gsel);
+    cudaFree(pl->d_hvalid[0]);
+    cudaFree(pl->d_hvalid[1]);
     cudaFree(pl->d_nseg);
     cudaFree(pl->d_ctab);
     cudaFree(pl->d_err);
     cudaFreeHost(pl->h_seg);
     cudaFreeHost(pl->h_nseg);
     cudaFreeHost(pl->h_gains);
+    cudaFreeHost(pl->h_gtap);
+    cudaFreeHost(pl->h_ngs);
     if (pl->staged) cudaEventDestroy(pl->staged);
     for (cudaEvent_t ev : pl->prof_events) cudaEventDestroy(ev);
     for (int i = 0; i < 2; i++) {
@@ -221,10 +243,13 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     const long long M = cfg->chunk_samples / N;
     if (M > (1LL << 30)) return fail(FENGINE_EINVAL, "chunk too long");
     // the kernels index a stream's history + chunk with 32-bit sample offsets
-    if (cfg->chunk_samples + 2LL * n * T + cfg->max_delay_samples + 16 >= (1LL << 31))
+    if (cfg->chunk_samples + 2LL * n * T + cfg->max_delay_samples - 2 * cfg->min_delay_samples + 2LL * n + 16 >=
+        (1LL << 31))
         return fail(FENGINE_EINVAL, "history + chunk must stay below 2^31 samples per stream");
     if (cfg->max_delay_samples < 0 || cfg->max_delay_samples > (1LL << 30))
         return fail(FENGINE_EINVAL, "max_delay_samples out of range");
+    if (cfg->min_delay_samples > 0 || cfg->min_delay_samples < -(1LL << 30))
+        return fail(FENGINE_EINVAL, "min_delay_samples must lie in [-2^30, 0]");
     int S = cfg->spectra_per_heap;
     if (S == 0) S = (int)(M < 256 ? M : 256);
     if (S < 1 || S > M) return fail(FENGINE_EINVAL, "spectra_per_heap must be in [1, L/2n]");
@@ -264,6 +289,8 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     pl->M = (int)M;
     pl->L = cfg->chunk_samples;
     pl->D = cfg->max_delay_samples;
+    pl->Dmin = cfg->min_delay_samples;
+    pl->E = (int)((-pl->Dmin + N - 1) / N);
     pl->precision = cfg->precision;
     pl->N1 = N1;
     pl->tc1 = tc1;
@@ -271,9 +298,13 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     pl->W = fe::phase1_W(pl->N1, pl->N2);
     pl->C = pl->N1 * pl->W;
     pl->R2 = fe::phase2_R2(pl->N2);
-    long long H = N * (T - 1) + pl->D;
+    // the history reaches back to the earliest window start of the call's
+    // first spectrum: N (T - 1 + E) + D samples before the chunk
+    long long H = N * (T - 1 + pl->E) + pl->D;
     H = (H + 15) / 16 * 16;     // whole 5-byte groups, and 4-byte aligned rows of packed history
     pl->H = H;
+    pl->lost_ok = pl->L % fe::kHeapSamples == 0;
+    pl->HV = (int)((H + fe::kHeapSamples - 1) / fe::kHeapSamples) + 1;
     pl->hist_bytes = H / 4 * 5;
     pl->chunk_bytes = pl->L / 4 * 5;
 
@@ -298,7 +329,12 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     if ((e = dalloc(pl, &pl->d_w, sizeof(float) * N * T)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_tw1, sizeof(float2) * (pl->N1 / 2 + 1) * pl->N2)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_tw2, sizeof(float2) * pl->N2)) != cudaSuccess ||
-        (e = dalloc(pl, &pl->d_gains, sizeof(float2) * ns * n)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_gains, sizeof(float2) * ns * fe::kMaxGainSeg * n)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_gtap, sizeof(long long) * ns * fe::kMaxGainSeg)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_ngs, sizeof(int) * ns)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_gsel, (size_t)ns * M)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_hvalid[0], (size_t)ns * pl->HV)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_hvalid[1], (size_t)ns * pl->HV)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_ftab, sizeof(float2) * ns * M)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_ctab, sizeof(int) * ns * M)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_A, a_bytes)) != cudaSuccess ||
@@ -314,7 +350,9 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     pl->scratch_bytes = a_bytes + sizeof(float2) * ns * M + sizeof(int) * ns * M;
     if ((e = cudaMallocHost((void **)&pl->h_seg, sizeof(DelaySeg) * fe::kMaxSeg * ns)) != cudaSuccess ||
         (e = cudaMallocHost((void **)&pl->h_nseg, sizeof(int) * ns)) != cudaSuccess ||
-        (e = cudaMallocHost((void **)&pl->h_gains, sizeof(float2) * ns * n)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&pl->h_gains, sizeof(float2) * ns * fe::kMaxGainSeg * n)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&pl->h_gtap, sizeof(long long) * ns * fe::kMaxGainSeg)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&pl->h_ngs, sizeof(int) * ns)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&pl->staged, cudaEventDisableTiming)) != cudaSuccess) {
         release(pl);
         g_last_error = std::string("pinned allocation: ") + cudaGetErrorString(e);
@@ -381,14 +419,17 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         for (int t2 = 0; t2 < pl->N2; t2++) tw1[(size_t)k1 * pl->N2 + t2] = unit_root((long long)k1 * t2, N);
     for (int q = 0; q < pl->N2; q++) tw2[q] = unit_root(q, pl->N2);
     pl->segs.assign(ns, std::vector<DelaySeg>{DelaySeg{-(1LL << 62), 0, 0.0, 0.0, 0.0, 0.0}});
-    pl->gains.assign((size_t)ns * n, make_float2(1.0f, 0.0f));
+    pl->gsets.assign(ns, std::vector<fengine_plan_s::GainSet>{
+                             fengine_plan_s::GainSet{-(1LL << 62), std::vector<float2>(n, make_float2(1.0f, 0.0f))}});
 
     if ((e = cudaMemcpy(pl->d_w, w.data(), sizeof(float) * N * T, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(pl->d_tw1, tw1.data(), sizeof(float2) * tw1.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(pl->d_tw2, tw2.data(), sizeof(float2) * tw2.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(pl->d_hist[0], 0, (size_t)pl->hist_bytes * ns + 16)) != cudaSuccess ||
         (e = cudaMemset(pl->d_hist[1], 0, (size_t)pl->hist_bytes * ns + 16)) != cudaSuccess ||
-        (e = cudaMemset(pl->d_err, 0, sizeof(int))) != cudaSuccess) {
+        (e = cudaMemset(pl->d_err, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(pl->d_hvalid[0], 0, (size_t)ns * pl->HV)) != cudaSuccess ||
+        (e = cudaMemset(pl->d_hvalid[1], 0, (size_t)ns * pl->HV)) != cudaSuccess) {
         release(pl);
         return cuda_fail(e, "plan upload");
     }
@@ -413,12 +454,14 @@ fengine_status fengine_get_info(fengine_plan_t pl, fengine_info *info) {
     info->fft_n2 = pl->N2;
     info->spectra_per_chunk = pl->M;
     info->history_samples = pl->H;
-    info->latency_spectra = pl->T - 1;
+    info->latency_spectra = pl->T - 1 + pl->E;
     info->out_bytes = (long long)pl->n_ant * pl->M * pl->n * 4;
     info->device_bytes = pl->device_bytes;
     info->scratch_bytes = pl->scratch_bytes;
     info->slab_spectra = pl->SL;
     info->slabs_per_chunk = pl->n_slabs;
+    info->heaps_per_chunk = (pl->M + pl->S - 1) / pl->S;
+    info->lost_data = pl->lost_ok ? 1 : 0;
     return FENGINE_OK;
 }
 
@@ -443,13 +486,22 @@ fengine_status fengine_set_delay(fengine_plan_t pl, int32_t ant, int32_t pol, in
     return FENGINE_OK;
 }
 
-fengine_status fengine_set_gains(fengine_plan_t pl, int32_t ant, int32_t pol, const float *g) {
+fengine_status fengine_set_gains(fengine_plan_t pl, int32_t ant, int32_t pol, const float *g, int64_t t_apply) {
     if (!pl || !g) return fail(FENGINE_EINVAL, "null argument");
     if (ant < 0 || ant >= pl->n_ant || pol < 0 || pol > 1) return fail(FENGINE_EINVAL, "bad stream index");
     for (int k = 0; k < 2 * pl->n; k++)
         if (!std::isfinite(g[k])) return fail(FENGINE_EINVAL, "gains must be finite");
-    float2 *dst = pl->gains.data() + (size_t)(ant * 2 + pol) * pl->n;
-    for (int k = 0; k < pl->n; k++) dst[k] = make_float2(g[2 * k], g[2 * k + 1]);
+    auto &v = pl->gsets[ant * 2 + pol];
+    fengine_plan_s::GainSet gs{(long long)t_apply, std::vector<float2>(pl->n)};
+    for (int k = 0; k < pl->n; k++) gs.g[k] = make_float2(g[2 * k], g[2 * k + 1]);
+    size_t i = 0;
+    while (i < v.size() && v[i].t_apply < t_apply) i++;
+    if (i < v.size() && v[i].t_apply == t_apply) {
+        v[i] = std::move(gs);
+    } else {
+        if ((int)v.size() >= fe::kMaxGainSeg) return fail(FENGINE_EINVAL, "too many pending gain sets");
+        v.insert(v.begin() + i, std::move(gs));
+    }
     pl->gains_dirty = true;
     return FENGINE_OK;
 }
@@ -460,23 +512,34 @@ fengine_status fengine_reset(fengine_plan_t pl) {
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "reset sync");
     const size_t hb = (size_t)pl->hist_bytes * pl->n_streams + 16;
     if ((e = cudaMemset(pl->d_hist[0], 0, hb)) != cudaSuccess ||
-        (e = cudaMemset(pl->d_hist[1], 0, hb)) != cudaSuccess)
+        (e = cudaMemset(pl->d_hist[1], 0, hb)) != cudaSuccess ||
+        (e = cudaMemset(pl->d_hvalid[0], 0, (size_t)pl->n_streams * pl->HV)) != cudaSuccess ||
+        (e = cudaMemset(pl->d_hvalid[1], 0, (size_t)pl->n_streams * pl->HV)) != cudaSuccess)
         return cuda_fail(e, "reset history");
+    pl->hv_known = true;
     pl->started = false;
     return FENGINE_OK;
 }
 
 fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const uint8_t *d_packed,
-                                     int64_t first_sample, int8_t *d_out, float *d_prequant,
-                                     int32_t *d_window_tap, int64_t *first_spectrum) {
+                                     int64_t first_sample, const uint8_t *d_valid, int8_t *d_out,
+                                     uint8_t *d_heap_flags, float *d_prequant, int32_t *d_window_tap,
+                                     int64_t *first_spectrum) {
     if (!pl || !d_packed || !d_out) return fail(FENGINE_EINVAL, "null argument");
     if (((uintptr_t)d_packed & 3) || ((uintptr_t)d_out & 3))
         return fail(FENGINE_EINVAL, "d_packed and d_out must be 4-byte aligned");
     if (first_sample % pl->N) return fail(FENGINE_EINVAL, "first_sample must be a multiple of 2 n_channels");
     if (pl->started && first_sample != pl->next_sample)
         return fail(FENGINE_ESEQ, "expected first_sample " + std::to_string(pl->next_sample));
+    const bool heap_aligned = pl->lost_ok && first_sample % fe::kHeapSamples == 0;
+    if ((d_valid || d_heap_flags) && !heap_aligned)
+        return fail(FENGINE_EINVAL, "lost-data flags need chunk_samples and first_sample to be multiples of the "
+                                    "4096-sample heap");
+    if (d_heap_flags && !pl->hv_known)
+        return fail(FENGINE_EINVAL, "the history's received flags are unknown (a call was not heap-aligned); "
+                                    "call fengine_reset first");
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const long long m0 = first_sample / pl->N - (pl->T - 1);
+    const long long m0 = first_sample / pl->N - (pl->T - 1) - pl->E;
     const long long t_first = (long long)pl->N * m0, t_last = (long long)pl->N * (m0 + pl->M - 1);
 
     // Drop delay models that no spectrum from this call on can use, then
@@ -499,10 +562,18 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
             hi = hi / pl->N * pl->N;
             if (hi < lo) continue;
             const long long c0 = coarse_delay(v[i], lo), c1 = coarse_delay(v[i], hi);
-            if (c0 < 0 || c1 < 0 || c0 > pl->D || c1 > pl->D)
+            if (c0 < pl->Dmin || c1 < pl->Dmin || c0 > pl->D || c1 > pl->D)
                 return fail(FENGINE_EDELAY, "stream " + std::to_string(s) + ": coarse delay " +
-                                                std::to_string(c0 < 0 || c0 > pl->D ? c0 : c1) +
-                                                " outside [0, " + std::to_string(pl->D) + "]");
+                                                std::to_string(c0 < pl->Dmin || c0 > pl->D ? c0 : c1) + " outside [" +
+                                                std::to_string(pl->Dmin) + ", " + std::to_string(pl->D) + "]");
+        }
+    }
+
+    for (int s = 0; s < pl->n_streams; s++) {
+        auto &v = pl->gsets[s];
+        while (v.size() > 1 && v[1].t_apply <= t_first) {
+            v.erase(v.begin());
+            pl->gains_dirty = true;
         }
     }
 
@@ -524,9 +595,21 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
                 return cuda_fail(e, "delay upload");
         }
         if (pl->gains_dirty) {
-            std::memcpy(pl->h_gains, pl->gains.data(), sizeof(float2) * pl->gains.size());
-            if ((e = cudaMemcpyAsync(pl->d_gains, pl->h_gains, sizeof(float2) * pl->gains.size(),
-                                     cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            const int G = fe::kMaxGainSeg;
+            for (int s = 0; s < pl->n_streams; s++) {
+                const auto &v = pl->gsets[s];
+                pl->h_ngs[s] = (int)v.size();
+                for (size_t i = 0; i < v.size(); i++) {
+                    pl->h_gtap[(size_t)s * G + i] = v[i].t_apply;
+                    std::memcpy(pl->h_gains + ((size_t)s * G + i) * pl->n, v[i].g.data(), sizeof(float2) * pl->n);
+                }
+            }
+            if ((e = cudaMemcpyAsync(pl->d_gains, pl->h_gains, sizeof(float2) * pl->n_streams * G * pl->n,
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(pl->d_gtap, pl->h_gtap, sizeof(long long) * pl->n_streams * G,
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(pl->d_ngs, pl->h_ngs, sizeof(int) * pl->n_streams, cudaMemcpyHostToDevice,
+                                     st)) != cudaSuccess)
                 return cuda_fail(e, "gain upload");
         }
         if ((e = cudaEventRecord(pl->staged, st)) != cudaSuccess) return cuda_fail(e, "staging event");
@@ -541,13 +624,40 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     dp.N = pl->N;
     dp.m0 = m0;
     dp.M = pl->M;
+    dp.min_delay = (int)pl->Dmin;
     dp.max_delay = (int)pl->D;
     dp.ctab = pl->d_ctab;
     dp.ftab = pl->d_ftab;
     dp.err = pl->d_err;
+    dp.g_tapply = pl->d_gtap;
+    dp.n_gsets = pl->d_ngs;
+    dp.gsel = pl->d_gsel;
     prof_begin(pl, 0, st);
     if ((e = fe::launch_delay_table(dp, st)) != cudaSuccess) return cuda_fail(e, "delay table launch");
     prof_end(pl, st);
+
+    // Lost data (Sec. 3.7): heap flags of this call and the history heaps'
+    // received flags for the next one (kept whenever the call is heap-aligned)
+    if (heap_aligned) {
+        fe::LostDataParams lp{};
+        lp.valid = d_valid;
+        lp.hv_in = pl->d_hvalid[pl->cur];
+        lp.hv_out = pl->d_hvalid[1 - pl->cur];
+        lp.HV = pl->HV;
+        lp.heap0 = first_sample / fe::kHeapSamples;
+        lp.chunk_heaps = (int)(pl->L / fe::kHeapSamples);
+        lp.ctab = pl->d_ctab;
+        lp.n_ant = pl->n_ant;
+        lp.N = pl->N;
+        lp.T = pl->T;
+        lp.M = pl->M;
+        lp.S = pl->S;
+        lp.m0 = m0;
+        lp.heap_flags = d_heap_flags;
+        if ((e = fe::launch_lost_data(lp, st)) != cudaSuccess) return cuda_fail(e, "lost-data launch");
+    } else if (pl->lost_ok) {
+        pl->hv_known = false;
+    }
 
     fe::Phase1Params p1{};
     p1.chunk = d_packed;
@@ -573,6 +683,8 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     fe::Phase2Params p2{};
     p2.tw2 = pl->d_tw2;
     p2.gains = pl->d_gains;
+    p2.gsel = pl->d_gsel;
+    p2.n_gsets_max = fe::kMaxGainSeg;
     p2.ftab = pl->d_ftab;
     p2.N = pl->N;
     p2.N1 = pl->N1;
@@ -660,6 +772,19 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     pl->started = true;
     pl->next_sample = first_sample + pl->L;
     if (first_spectrum) *first_spectrum = m0;
+    return FENGINE_OK;
+}
+
+fengine_status fengine_device_status(fengine_plan_t pl) {
+    if (!pl) return fail(FENGINE_EINVAL, "null plan");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "device status");
+    int h = 0;
+    if ((e = cudaMemcpy(&h, pl->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemset(pl->d_err, 0, sizeof(int))) != cudaSuccess)
+        return cuda_fail(e, "device status");
+    if (h == 2) return fail(FENGINE_ETIMEOUT, "a bounded wait of the tensor-core phase 1 gave up");
+    if (h == 1) return fail(FENGINE_EDELAY, "a coarse delay was clamped on the device");
     return FENGINE_OK;
 }
 

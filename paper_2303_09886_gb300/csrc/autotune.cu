@@ -82,11 +82,11 @@ extern "C" fengine_status fengine_autotune(const fengine_config *cfg, void *cuda
             long long t = 0;
             int64_t first = 0;
             for (int i = 0; i < 2 && s == FENGINE_OK; i++, t += cfg->chunk_samples)
-                s = fengine_process_chunk(plan, cuda_stream, d_in, t, d_out, nullptr, nullptr, &first);
+                s = fengine_process_chunk(plan, cuda_stream, d_in, t, nullptr, d_out, nullptr, nullptr, nullptr, &first);
             float ms = 0.0f;
             if (s == FENGINE_OK && cudaEventRecord(e0, st) == cudaSuccess) {
                 for (int i = 0; i < calls && s == FENGINE_OK; i++, t += cfg->chunk_samples)
-                    s = fengine_process_chunk(plan, cuda_stream, d_in, t, d_out, nullptr, nullptr, &first);
+                    s = fengine_process_chunk(plan, cuda_stream, d_in, t, nullptr, d_out, nullptr, nullptr, nullptr, &first);
                 if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                     cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
                     s = FENGINE_ECUDA;

@@ -98,9 +98,9 @@ fengine_status fengine_batch_process(fengine_batch_t b, void *cuda_stream, const
             used[s] = 1;
         }
         int64_t fs = 0;
-        const fengine_status r = fengine_process_chunk(chunks[i].plan, (void *)b->pool[s], chunks[i].d_packed,
-                                                       chunks[i].first_sample, chunks[i].d_out,
-                                                       nullptr, nullptr, &fs);
+        const fengine_status r =
+            fengine_process_chunk(chunks[i].plan, (void *)b->pool[s], chunks[i].d_packed, chunks[i].first_sample,
+                                  chunks[i].d_valid, chunks[i].d_out, chunks[i].d_heap_flags, nullptr, nullptr, &fs);
         if (r != FENGINE_OK) {
             result = r;   // members enqueued so far still run; the join below covers them
             break;

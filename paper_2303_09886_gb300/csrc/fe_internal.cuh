@@ -25,6 +25,8 @@
 namespace fe {
 
 constexpr int kMaxSeg = 16;   // FENGINE_MAX_DELAY_SEGMENTS
+constexpr int kMaxGainSeg = 4;  // FENGINE_MAX_GAIN_SETS
+constexpr int kHeapSamples = 4096;   // samples per digitiser heap (Sec. 2.2)
 
 // One linear delay/phase segment of a stream, applied from t_apply on.
 struct DelaySeg {
@@ -40,11 +42,32 @@ struct DelayTableParams {
     int N;                    // FFT length 2n
     long long m0;             // first spectrum of the call
     int M;                    // spectra per call
-    int max_delay;            // coarse delays clamp into [0, max_delay]
+    int min_delay, max_delay; // coarse delays clamp into [min_delay, max_delay]
     int *ctab;                // out [stream][M] coarse delay
     float2 *ftab;             // out [stream][M] (fine delay delta, phase reduced to [-pi, pi))
     int *err;                 // set to 1 if a coarse delay had to be clamped
+    // gain sets: the set of spectrum t0 is the last one with t_apply <= t0 (set 0 before all)
+    const long long *g_tapply; // [stream][kMaxGainSeg], nullptr: one set
+    const int *n_gsets;        // [stream]
+    unsigned char *gsel;       // out [stream][M] gain-set index (when g_tapply is given)
 };
+
+// Lost data (Sec. 3.7): per-spectrum usability from the received-heap flags,
+// per-output-heap flags, and the received flags of the history heaps kept for
+// the next call. Heaps are kHeapSamples long and start at multiples of it.
+struct LostDataParams {
+    const unsigned char *valid;      // [stream][L / kHeapSamples] of this chunk, nullptr = all received
+    const unsigned char *hv_in;      // [stream][HV] history heaps t_in/4096 - HV + i
+    unsigned char *hv_out;           // [stream][HV] for the next call
+    int HV;                          // history heaps kept
+    long long heap0;                 // t_in / kHeapSamples
+    int chunk_heaps;                 // L / kHeapSamples
+    const int *ctab;                 // [stream][M]
+    int n_ant, N, T, M, S;
+    long long m0;
+    unsigned char *heap_flags;       // out [ant][ceil(M / S)], nullptr = not wanted
+};
+cudaError_t launch_lost_data(const LostDataParams &p, cudaStream_t s);
 
 struct Phase1Params {
     const uint8_t *chunk;     // [stream][chunk_bytes]
@@ -73,7 +96,9 @@ struct Phase2Params {
     int q_begin, q_count;     // the slab of spectra this launch covers
     int a_spectra;            // spectra per stream in the intermediate buffer
     const float2 *tw2;        // [N2] exp(-2 pi i q / N2)
-    const float2 *gains;      // [stream][n]
+    const float2 *gains;      // [stream][n_gsets_max][n] gain sets
+    const unsigned char *gsel;   // [stream][M] gain-set index per spectrum, nullptr = set 0
+    int n_gsets_max;          // sets per stream in `gains`
     const float2 *ftab;       // [stream][M]
     int N, N1, M, S, R2;      // FFT length, first-stage size, spectra/call, spectra/heap, spectra/CTA
     int8_t *out;              // [ant][heap][n][S_h][pol][2]

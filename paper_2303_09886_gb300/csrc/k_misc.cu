@@ -47,12 +47,19 @@ __global__ void k_delay_table(const DelayTableParams p) {
     const double u = phi * 0.31830988618379067154;       // phi / pi
     const double red = u - 2.0 * rint(0.5 * u);          // in [-1, 1]
     long long ci = (long long)c;
-    if (ci < 0 || ci > p.max_delay) {                    // unreachable after the host check
-        ci = ci < 0 ? 0 : p.max_delay;
+    if (ci < p.min_delay || ci > p.max_delay) {          // unreachable after the host check
+        ci = ci < p.min_delay ? p.min_delay : p.max_delay;
         atomicExch(p.err, 1);
     }
     p.ctab[e] = (int)ci;
     p.ftab[e] = make_float2((float)delta, (float)red);
+    if (p.g_tapply) {
+        const long long *ta = p.g_tapply + (long long)st * kMaxGainSeg;
+        int g = 0;
+        for (int k = 0; k < p.n_gsets[st]; k++)
+            if (ta[k] <= t0) g = k;
+        p.gsel[e] = (unsigned char)g;
+    }
 }
 
 cudaError_t launch_delay_table(const DelayTableParams &p, cudaStream_t s) {
@@ -88,6 +95,57 @@ cudaError_t launch_tail_update(const uint8_t *hist_in, const uint8_t *chunk, uin
     if (blocks < 1) blocks = 1;
     k_tail_update<<<(unsigned)blocks, 256, 0, s>>>(hist_in, chunk, hist_out, hist_bytes, chunk_bytes,
                                                    n_streams);
+    return cudaGetLastError();
+}
+
+// Lost data (Sec. 3.7). Block x < n_ant * n_heaps_out: output heap h of
+// antenna a; its threads check the spectra of the heap in both polarisations:
+// spectrum m (coarse delay c) reads [N m - c, N m - c + N T), usable iff every
+// heap that window touches was received (history heaps from hv_in, chunk
+// heaps from valid). The heap is transmitted (flag 1) iff all are usable.
+// The last block writes the received flags of the HV heaps before the end
+// of this chunk, for the next call.
+__global__ void k_lost_data(const LostDataParams p) {
+    const int n_out = (p.M + p.S - 1) / p.S;
+    const long long hist_first = p.heap0 - p.HV;   // heap of hv_in[0]
+    auto received = [&](int stream, long long h) -> bool {
+        if (h >= p.heap0) {
+            const long long i = h - p.heap0;
+            if (i >= p.chunk_heaps) return false;
+            return p.valid ? p.valid[(long long)stream * p.chunk_heaps + i] != 0 : true;
+        }
+        const long long i = h - hist_first;
+        return i >= 0 && p.hv_in[(long long)stream * p.HV + i] != 0;
+    };
+    if ((int)blockIdx.x < p.n_ant * n_out) {
+        if (!p.heap_flags) return;
+        const int a = blockIdx.x / n_out, h = blockIdx.x % n_out;
+        const int q0 = h * p.S, cnt = min(p.S, p.M - q0);
+        int ok = 1;
+        for (int e = threadIdx.x; e < 2 * cnt; e += blockDim.x) {
+            const int pol = e / cnt, q = q0 + e % cnt, stream = 2 * a + pol;
+            const long long start = (long long)p.N * (p.m0 + q) - p.ctab[(long long)stream * p.M + q];
+            const long long end = start + (long long)p.N * p.T - 1;
+            const long long h0 = start >= 0 ? start / kHeapSamples : -((-start + kHeapSamples - 1) / kHeapSamples);
+            const long long h1 = end >= 0 ? end / kHeapSamples : -((-end + kHeapSamples - 1) / kHeapSamples);
+            for (long long hh = h0; hh <= h1 && ok; hh++)
+                if (!received(stream, hh)) ok = 0;
+        }
+        ok = __syncthreads_and(ok);
+        if (threadIdx.x == 0) p.heap_flags[(long long)a * n_out + h] = (unsigned char)ok;
+        return;
+    }
+    // history heaps of the next call: heap (heap0 + chunk_heaps) - HV + i
+    for (int e = threadIdx.x; e < 2 * p.n_ant * p.HV; e += blockDim.x) {
+        const int stream = e / p.HV, i = e % p.HV;
+        const long long hh = p.heap0 + p.chunk_heaps - p.HV + i;
+        p.hv_out[(long long)stream * p.HV + i] = received(stream, hh) ? 1 : 0;
+    }
+}
+
+cudaError_t launch_lost_data(const LostDataParams &p, cudaStream_t s) {
+    const int n_out = (p.M + p.S - 1) / p.S;
+    k_lost_data<<<p.n_ant * n_out + 1, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -259,6 +259,11 @@ __global__ void __launch_bounds__(kP2Threads, 3) k_phase2(const Phase2Params p) 
     const float2 *th0 = thi + r * HP, *th1 = thi + (R2 + r) * HP;
     const float2 *tl0 = tlo + r * LP, *tl1 = tlo + (R2 + r) * LP;
     const float2 qu0 = qup[r], qu1 = qup[R2 + r];
+    // the gain set of this spectrum in each polarisation
+    const int gs0 = p.gsel ? p.gsel[(long long)(ant * 2) * M + q0 + r] : 0;
+    const int gs1 = p.gsel ? p.gsel[(long long)(ant * 2 + 1) * M + q0 + r] : 0;
+    const float2 *gain0 = p.gains + ((long long)(ant * 2) * p.n_gsets_max + gs0) * n;
+    const float2 *gain1 = p.gains + ((long long)(ant * 2 + 1) * p.n_gsets_max + gs1) * n;
     float2 *pre0 = p.prequant ? p.prequant + ((long long)(ant * 2) * M + q0 + r) * n : nullptr;
     float2 *pre1 = p.prequant ? p.prequant + ((long long)(ant * 2 + 1) * M + q0 + r) * n : nullptr;
 #pragma unroll 4
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(kP2Threads, 3) k_phase2(const Phase2Params p) 
         const int pos = pad(dif_pos<N2>(k2));
         const float2 z0 = cmul(cmul(th0[a], tl0[b]), F0[pos]);
         const float2 z1 = cmul(cmul(th1[a], tl1[b]), F1[pos]);
-        const float2 g0 = __ldg(p.gains + (long long)(ant * 2) * n + k), g1 = __ldg(p.gains + (long long)(ant * 2 + 1) * n + k);
+        const float2 g0 = __ldg(gain0 + k), g1 = __ldg(gain1 + k);
         const float2 y0 = up ? cmul(cmul(g0, qu0), cconj(z0)) : cmul(g0, z0);
         const float2 y1 = up ? cmul(cmul(g1, qu1), cconj(z1)) : cmul(g1, z1);
         if (pre0) {

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
     for (int e = threadIdx.x; e < 32 * 32; e += kWThreads) twm[e] = __ldg(p.tw2 + (((e >> 5) * (e & 31)) & (kWN2 - 1)));
     __syncthreads();   // the twiddles are read before the first item's barrier
 
-    int cur = -1;   // (ant, k1) of the gains in gsm
+    long long cur = -1;   // (ant, k1, gain set of each pol) of the gains in gsm
     for (int it = it0; it < it1; it++) {
         // row info alternates between two slots: the previous item's corner
         // turn may still read its slot while this item's is written
@@ -190,13 +190,18 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
             const float u = (HALF_IN && j < 32) ? p.tc_unscale : 1.0f;
             pq[e] = make_float2(cs * u, sn * u);
         }
-        if (ant * 1024 + k1 != cur) {
-            cur = ant * 1024 + k1;
+        // gains staged for the gain set of the item's first spectrum in each pol
+        const int gs0 = p.gsel ? p.gsel[(long long)(ant * 2) * M + q0] : 0;
+        const int gs1 = p.gsel ? p.gsel[(long long)(ant * 2 + 1) * M + q0] : 0;
+        const long long key = (((long long)ant * 1024 + k1) * 256 + gs0) * 256 + gs1;
+        if (key != cur) {
+            cur = key;
             for (int e = threadIdx.x; e < 2 * kWN2; e += kWThreads) {
                 const int ps = e / kWN2, k2 = e % kWN2;
                 const int kc = k1 + N1 * k2;
                 const int k = k2 >= kWN2 / 2 ? N - kc : kc;
-                gsm[e] = (k >= 0 && k < n) ? __ldg(p.gains + (long long)(ant * 2 + ps) * n + k) : make_float2(0.f, 0.f);
+                const float2 *g = p.gains + ((long long)(ant * 2 + ps) * p.n_gsets_max + (ps ? gs1 : gs0)) * n;
+                gsm[e] = (k >= 0 && k < n) ? __ldg(g + k) : make_float2(0.f, 0.f);
             }
         }
         if ((int)threadIdx.x < Rv) {
@@ -243,13 +248,22 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
             const float2 P = pqs[lane], qu = pqs[64];
             const float2 Pu = cmul(qu, cconj(P));
             const float2 *gp = gsm + pol * kWN2;
+            // a spectrum whose gain set differs from the staged one (a gain
+            // update inside the item) reads its gains directly
+            const int gsr = p.gsel ? p.gsel[(long long)stream * M + q0 + r] : 0;
+            const bool staged = gsr == (pol ? gs1 : gs0);
+            const float2 *gdir = p.gains + ((long long)stream * p.n_gsets_max + gsr) * n;
+            auto gain = [&](int k2) -> float2 {
+                const int kc = k1 + N1 * k2;
+                return staged ? gp[k2] : __ldg(gdir + (k2 >= kWN2 / 2 ? N - kc : kc));
+            };
             unsigned short *stg16 = reinterpret_cast<unsigned short *>(stg);
             float2 *pre = p.prequant ? p.prequant + ((long long)stream * M + q0 + r) * n : nullptr;
             // lower half (d < 16): channel k1 + N1 k2
 #pragma unroll
             for (int d = 0; d < 16; d++) {
                 const int k2 = lane + 32 * d;
-                const float2 y = cmul(gp[k2], cmul(cmul(P, pqs[32 + d]), z[d]));
+                const float2 y = cmul(gain(k2), cmul(cmul(P, pqs[32 + d]), z[d]));
                 if (pre) pre[k1 + N1 * k2] = y;
                 stg16[2 * stg_word(k2, r) + pol] =
                     (unsigned short)__byte_perm((unsigned)quant8(y.x), (unsigned)quant8(y.y), 0x0040u);
@@ -259,7 +273,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, 
 #pragma unroll
                 for (int d = 16; d < 32; d++) {
                     const int k2 = lane + 32 * d;
-                    const float2 y = cmul(gp[k2], cmul(cmul(Pu, cconj(pqs[32 + d])), cconj(z[d])));
+                    const float2 y = cmul(gain(k2), cmul(cmul(Pu, cconj(pqs[32 + d])), cconj(z[d])));
                     if (pre) pre[N - (k1 + N1 * k2)] = y;
                     stg16[2 * stg_word(k2, r) + pol] =
                         (unsigned short)__byte_perm((unsigned)quant8(y.x), (unsigned)quant8(y.y), 0x0040u);

@@ -163,6 +163,7 @@ fengine_status fengine_process_chunk_noalloc(const fengine_noalloc_args *a, cons
     dp.N = (int)N;
     dp.m0 = m0;
     dp.M = (int)M;
+    dp.min_delay = 0;
     dp.max_delay = (int)a->max_delay_samples;
     dp.ctab = reinterpret_cast<int *>(base + o_ctab);
     dp.ftab = reinterpret_cast<float2 *>(base + o_ftab);
@@ -193,7 +194,10 @@ fengine_status fengine_process_chunk_noalloc(const fengine_noalloc_args *a, cons
     fe::Phase2Params p2{};
     p2.A = p1.A;
     p2.tw2 = reinterpret_cast<const float2 *>(base + o_tw2);
-    p2.gains = reinterpret_cast<const float2 *>(d_gains);
+    p2.gains = reinterpret_cast<const float2 *>(d_gains);   // one gain set per stream
+    p2.gsel = nullptr;
+    p2.n_gsets_max = 1;
+    p2.tc_unscale = 1.0f;
     p2.ftab = dp.ftab;
     p2.N = (int)N;
     p2.N1 = N1;

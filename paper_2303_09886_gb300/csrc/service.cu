@@ -39,6 +39,9 @@ struct Request {
     fengine_plan_t plan = nullptr;
     const uint8_t *h_in = nullptr;
     int8_t *h_out = nullptr;
+    const uint8_t *h_valid = nullptr;  // optional received-heap flags of the chunk
+    uint8_t *h_flags = nullptr;        // optional output-heap flags
+    size_t valid_bytes = 0, flag_bytes = 0;
     int64_t first_sample = 0;
     size_t in_bytes = 0, out_bytes = 0;
     // updates
@@ -49,7 +52,7 @@ struct Request {
     // progress
     clk::time_point t_submit, t_admit, t_done;
     int stream = -1;
-    void *d_in = nullptr, *d_out = nullptr;
+    void *d_in = nullptr, *d_out = nullptr, *d_valid = nullptr, *d_flags = nullptr;
     fengine_status status = FENGINE_OK;
     bool done = false;
     bool deferred = false;
@@ -100,12 +103,21 @@ fengine_status launch_chunk(fengine_service_s *s, const std::shared_ptr<Request>
     cudaStream_t st = s->streams[r->stream];
     if (cudaMallocAsync(&r->d_in, r->in_bytes, st) != cudaSuccess) return FENGINE_ENOMEM;
     if (cudaMallocAsync(&r->d_out, r->out_bytes, st) != cudaSuccess) return FENGINE_ENOMEM;
+    if (r->h_valid && cudaMallocAsync(&r->d_valid, r->valid_bytes, st) != cudaSuccess) return FENGINE_ENOMEM;
+    if (r->h_flags && cudaMallocAsync(&r->d_flags, r->flag_bytes, st) != cudaSuccess) return FENGINE_ENOMEM;
     if (cudaMemcpyAsync(r->d_in, r->h_in, r->in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FENGINE_ECUDA;
-    const fengine_status ps = fengine_process_chunk(r->plan, (void *)st, (const uint8_t *)r->d_in, r->first_sample,
-                                                    (int8_t *)r->d_out, nullptr, nullptr, nullptr);
+    if (r->h_valid &&
+        cudaMemcpyAsync(r->d_valid, r->h_valid, r->valid_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return FENGINE_ECUDA;
+    const fengine_status ps =
+        fengine_process_chunk(r->plan, (void *)st, (const uint8_t *)r->d_in, r->first_sample,
+                              (const uint8_t *)r->d_valid, (int8_t *)r->d_out, (uint8_t *)r->d_flags, nullptr,
+                              nullptr, nullptr);
     if (ps != FENGINE_OK) return ps;
     if (cudaMemcpyAsync(r->h_out, r->d_out, r->out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return FENGINE_ECUDA;
+    if (r->h_flags && cudaMemcpyAsync(r->h_flags, r->d_flags, r->flag_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return FENGINE_ECUDA;
     return FENGINE_OK;
 }
@@ -121,7 +133,9 @@ void dispatcher(fengine_service_s *s) {
             if (r.done && r.stream >= 0 && r.kind == 0 && (r.d_in || r.d_out)) {
                 cudaFreeAsync(r.d_in, s->streams[r.stream]);
                 cudaFreeAsync(r.d_out, s->streams[r.stream]);
-                r.d_in = r.d_out = nullptr;
+                if (r.d_valid) cudaFreeAsync(r.d_valid, s->streams[r.stream]);
+                if (r.d_flags) cudaFreeAsync(r.d_flags, s->streams[r.stream]);
+                r.d_in = r.d_out = r.d_valid = r.d_flags = nullptr;
                 s->in_use -= (int64_t)(r.in_bytes + r.out_bytes);
                 s->stream_busy[r.stream]--;
                 s->completed++;
@@ -157,7 +171,7 @@ void dispatcher(fengine_service_s *s) {
                 r->stream = si;
                 r->status = r->kind == 1
                     ? fengine_set_delay(r->plan, r->ant, r->pol, r->t_apply, r->t_ref, r->d[0], r->d[1], r->d[2], r->d[3])
-                    : fengine_set_gains(r->plan, r->ant, r->pol, r->gains.data());
+                    : fengine_set_gains(r->plan, r->ant, r->pol, r->gains.data(), r->t_apply);
                 r->done = true;
                 r->t_done = clk::now();
                 it = s->queue.erase(it);
@@ -209,7 +223,9 @@ void dispatcher(fengine_service_s *s) {
                 r->status = st;
                 if (r->d_in) cudaFreeAsync(r->d_in, s->streams[si]);
                 if (r->d_out) cudaFreeAsync(r->d_out, s->streams[si]);
-                r->d_in = r->d_out = nullptr;
+                if (r->d_valid) cudaFreeAsync(r->d_valid, s->streams[si]);
+                if (r->d_flags) cudaFreeAsync(r->d_flags, s->streams[si]);
+                r->d_in = r->d_out = r->d_valid = r->d_flags = nullptr;
                 s->in_use -= need;
                 s->stream_busy[si]--;
                 s->failed++;
@@ -258,7 +274,8 @@ fengine_status fengine_service_create(const fengine_service_config *cfg, fengine
 }
 
 fengine_status fengine_service_submit(fengine_service_t s, fengine_plan_t plan, const uint8_t *h_packed,
-                                      int64_t first_sample, int8_t *h_out, int64_t *ticket) {
+                                      int64_t first_sample, const uint8_t *h_valid, int8_t *h_out,
+                                      uint8_t *h_heap_flags, int64_t *ticket) {
     if (!s || !plan || !h_packed || !h_out || !ticket) return FENGINE_EINVAL;
     fengine_info info;
     if (fengine_get_info(plan, &info) != FENGINE_OK) return FENGINE_EINVAL;
@@ -267,9 +284,14 @@ fengine_status fengine_service_submit(fengine_service_t s, fengine_plan_t plan, 
     r->plan = plan;
     r->h_in = h_packed;
     r->h_out = h_out;
+    r->h_valid = h_valid;
+    r->h_flags = h_heap_flags;
     r->first_sample = first_sample;
-    r->in_bytes = (size_t)info.n_antennas * 2 * (size_t)(info.spectra_per_chunk * 2 * info.n_channels) / 4 * 5;
+    const int64_t L = info.spectra_per_chunk * 2 * info.n_channels;
+    r->in_bytes = (size_t)info.n_antennas * 2 * (size_t)L / 4 * 5;
     r->out_bytes = (size_t)info.out_bytes;
+    r->valid_bytes = (size_t)info.n_antennas * 2 * (size_t)(L / 4096);
+    r->flag_bytes = (size_t)info.n_antennas * (size_t)info.heaps_per_chunk;
     r->t_submit = clk::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -311,7 +333,7 @@ fengine_status fengine_service_set_delay(fengine_service_t s, fengine_plan_t pla
 }
 
 fengine_status fengine_service_set_gains(fengine_service_t s, fengine_plan_t plan, int32_t ant, int32_t pol,
-                                         const float *gains_re_im) {
+                                         const float *gains_re_im, int64_t t_apply) {
     if (!s || !plan || !gains_re_im) return FENGINE_EINVAL;
     fengine_info info;
     if (fengine_get_info(plan, &info) != FENGINE_OK) return FENGINE_EINVAL;
@@ -321,6 +343,7 @@ fengine_status fengine_service_set_gains(fengine_service_t s, fengine_plan_t pla
     r->ant = ant;
     r->pol = pol;
     r->gains.assign(gains_re_im, gains_re_im + 2 * (size_t)info.n_channels);
+    r->t_apply = t_apply;
     r->t_submit = clk::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -392,7 +415,9 @@ fengine_status fengine_service_destroy(fengine_service_t s) {
             if (r.stream >= 0 && (r.d_in || r.d_out)) {
                 cudaFreeAsync(r.d_in, s->streams[r.stream]);
                 cudaFreeAsync(r.d_out, s->streams[r.stream]);
-                r.d_in = r.d_out = nullptr;
+                if (r.d_valid) cudaFreeAsync(r.d_valid, s->streams[r.stream]);
+                if (r.d_flags) cudaFreeAsync(r.d_flags, s->streams[r.stream]);
+                r.d_in = r.d_out = r.d_valid = r.d_flags = nullptr;
             }
         }
     }

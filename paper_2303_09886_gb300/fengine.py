@@ -17,6 +17,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfengine.so")
 
 FP32, TC_FP16, TC_BF16 = 0, 1, 2
+ABI_VERSION = 3
+HEAP_SAMPLES = 4096        # samples per digitiser heap (lost-data flags)
+FAR_PAST = -(2 ** 62)      # t_apply of a model or gain set that applies at once
 STATUS = {0: "FENGINE_OK", 1: "FENGINE_EINVAL", 2: "FENGINE_ENOMEM", 3: "FENGINE_ECUDA",
           4: "FENGINE_ESEQ", 5: "FENGINE_EBUSY", 6: "FENGINE_ETIMEOUT",
           7: "FENGINE_EUNSUPPORTED", 8: "FENGINE_EDELAY"}
@@ -29,7 +32,8 @@ EXPORTS = ("fengine_strerror", "fengine_last_error", "fengine_abi_version", "fen
            "fengine_batch_create", "fengine_batch_destroy", "fengine_batch_process",
            "fengine_service_create", "fengine_service_submit", "fengine_service_set_delay",
            "fengine_service_set_gains", "fengine_service_wait", "fengine_service_get_stats",
-           "fengine_service_destroy", "fengine_process_chunk_noalloc", "fengine_autotune")
+           "fengine_service_destroy", "fengine_process_chunk_noalloc", "fengine_autotune",
+           "fengine_device_status")
 
 
 class FEngineError(RuntimeError):
@@ -44,7 +48,8 @@ class Config(ctypes.Structure):
                 ("chunk_samples", ctypes.c_int64), ("spectra_per_heap", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_delay_samples", ctypes.c_int64),
                 ("weights", ctypes.POINTER(ctypes.c_float)),
-                ("fft_n1", ctypes.c_int32), ("slab_spectra", ctypes.c_int32)]
+                ("fft_n1", ctypes.c_int32), ("slab_spectra", ctypes.c_int32),
+                ("min_delay_samples", ctypes.c_int64)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -58,12 +63,14 @@ class Info(ctypes.Structure):
                 ("spectra_per_chunk", ctypes.c_int64), ("history_samples", ctypes.c_int64),
                 ("latency_spectra", ctypes.c_int64), ("out_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t),
-                ("slab_spectra", ctypes.c_int32), ("slabs_per_chunk", ctypes.c_int32)]
+                ("slab_spectra", ctypes.c_int32), ("slabs_per_chunk", ctypes.c_int32),
+                ("heaps_per_chunk", ctypes.c_int32), ("lost_data", ctypes.c_int32)]
 
 
 class ChunkDesc(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("d_packed", ctypes.c_void_p),
-                ("first_sample", ctypes.c_int64), ("d_out", ctypes.c_void_p)]
+                ("first_sample", ctypes.c_int64), ("d_out", ctypes.c_void_p),
+                ("d_valid", ctypes.c_void_p), ("d_heap_flags", ctypes.c_void_p)]
 
 
 _lib = None
@@ -78,6 +85,10 @@ def load(path: str = LIB_PATH):
         raise FEngineError(-1, f"{path} is missing: run paper_2303_09886_gb300.build.build() "
                                "(the CUDA extension is required; there is no fallback)")
     lib = ctypes.CDLL(path)
+    lib.fengine_abi_version.restype = ctypes.c_int32
+    if lib.fengine_abi_version() != ABI_VERSION:
+        raise FEngineError(-1, f"{path} has ABI version {lib.fengine_abi_version()}, this binding needs "
+                               f"{ABI_VERSION}: rebuild the library")
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.fengine_strerror.argtypes = [ctypes.c_int]
     lib.fengine_strerror.restype = ctypes.c_char_p
@@ -93,9 +104,10 @@ def load(path: str = LIB_PATH):
     lib.fengine_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.fengine_set_delay.argtypes = [vp, i32, i32, i64, i64, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double]
-    lib.fengine_set_gains.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_float)]
+    lib.fengine_set_gains.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_float), i64]
     lib.fengine_reset.argtypes = [vp]
-    lib.fengine_process_chunk.argtypes = [vp, vp, vp, i64, vp, vp, vp, ctypes.POINTER(i64)]
+    lib.fengine_process_chunk.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
+    lib.fengine_device_status.argtypes = [vp]
     lib.fengine_set_profiling.argtypes = [vp, i32]
     lib.fengine_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
     lib.fengine_batch_create.argtypes = [i32, ctypes.POINTER(vp)]
@@ -106,7 +118,8 @@ def load(path: str = LIB_PATH):
     for name in ("fengine_autotune", "fengine_default_weights", "fengine_plan_create", "fengine_plan_destroy",
                  "fengine_get_info", "fengine_set_delay", "fengine_set_gains", "fengine_reset",
                  "fengine_process_chunk", "fengine_set_profiling", "fengine_stage_times",
-                 "fengine_batch_create", "fengine_batch_destroy", "fengine_batch_process"):
+                 "fengine_batch_create", "fengine_batch_destroy", "fengine_batch_process",
+                 "fengine_device_status"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -146,7 +159,7 @@ class Plan:
 
     def __init__(self, n_antennas: int, n_channels: int, n_taps: int, chunk_samples: int,
                  spectra_per_heap: int = 0, max_delay_samples: int = 0, weights=None,
-                 precision: int = FP32, fft_n1: int = 0, slab_spectra: int = 0):
+                 precision: int = FP32, fft_n1: int = 0, slab_spectra: int = 0, min_delay_samples: int = 0):
         lib = load()
         self._w = None
         if weights is not None:
@@ -156,7 +169,7 @@ class Plan:
         cfg = Config(n_antennas, 2, n_channels, n_taps, chunk_samples, spectra_per_heap, precision,
                      max_delay_samples,
                      self._w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if self._w is not None else None,
-                     fft_n1, slab_spectra)
+                     fft_n1, slab_spectra, min_delay_samples)
         h = ctypes.c_void_p()
         _check(lib.fengine_plan_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -167,6 +180,7 @@ class Plan:
         self.N = 2 * n_channels
         self.M = int(self.info.spectra_per_chunk)
         self.S = int(self.info.spectra_per_heap)
+        self.heaps = int(self.info.heaps_per_chunk)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -184,10 +198,15 @@ class Plan:
         _check(load().fengine_set_delay(self._h, ant, pol, t_apply, t_ref, delay, rate, phase,
                                         phase_rate))
 
-    def set_gains(self, ant: int, pol: int, gains):
+    def set_gains(self, ant: int, pol: int, gains, t_apply: int = FAR_PAST):
         g = np.ascontiguousarray(np.broadcast_to(np.asarray(gains, np.complex64), (self.n_channels,)))
         gi = g.view(np.float32)
-        _check(load().fengine_set_gains(self._h, ant, pol, gi.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        _check(load().fengine_set_gains(self._h, ant, pol, gi.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        t_apply))
+
+    def device_status(self):
+        """fengine_device_status: synchronise and raise if a kernel recorded a fault."""
+        _check(load().fengine_device_status(self._h))
 
     def reset(self):
         _check(load().fengine_reset(self._h))
@@ -204,9 +223,12 @@ class Plan:
         _check(load().fengine_stage_times(self._h, ms, ctypes.byref(calls)))
         return dict(zip(self.STAGES, list(ms))), calls.value
 
-    def process(self, packed, first_sample: int, out, prequant=None, window_tap=None, stream=None):
+    def process(self, packed, first_sample: int, out, prequant=None, window_tap=None, stream=None,
+                valid=None, heap_flags=None):
         """Enqueue one chunk. packed: uint8 CUDA tensor [ant, pol, 5L/4]; out: int8
-        CUDA tensor of info.out_bytes. Returns the first spectrum index."""
+        CUDA tensor of info.out_bytes; valid: optional uint8 CUDA tensor
+        [ant, pol, L/4096] of received-heap flags; heap_flags: optional uint8 CUDA
+        tensor [ant, heaps_per_chunk] out. Returns the first spectrum index."""
         import torch
         if packed.dtype != torch.uint8 or out.dtype != torch.int8:
             raise TypeError("packed must be uint8 and out int8")
@@ -218,11 +240,17 @@ class Plan:
             raise ValueError("prequant has the wrong size")
         if window_tap is not None and window_tap.numel() != self.n_antennas * 2 * self.M * self.N:
             raise ValueError("window_tap has the wrong size")
+        if valid is not None and (valid.dtype != torch.uint8 or
+                                  valid.numel() != self.n_antennas * 2 * (self.chunk_samples // HEAP_SAMPLES)):
+            raise ValueError("valid must be uint8 [ant, pol, L/4096]")
+        if heap_flags is not None and (heap_flags.dtype != torch.uint8 or
+                                       heap_flags.numel() != self.n_antennas * self.heaps):
+            raise ValueError("heap_flags must be uint8 [ant, heaps_per_chunk]")
         s = stream if stream is not None else torch.cuda.current_stream()
         fs = ctypes.c_int64()
         _check(load().fengine_process_chunk(self._h, ctypes.c_void_p(s.cuda_stream), _ptr(packed),
-                                            first_sample, _ptr(out), _ptr(prequant), _ptr(window_tap),
-                                            ctypes.byref(fs)))
+                                            first_sample, _ptr(valid), _ptr(out), _ptr(heap_flags),
+                                            _ptr(prequant), _ptr(window_tap), ctypes.byref(fs)))
         return fs.value
 
 
@@ -232,7 +260,7 @@ def autotune(n_antennas: int, n_channels: int, n_taps: int, chunk_samples: int, 
     ({"fft_n1": .., "slab_spectra": ..} of the fastest, [(fft_n1, slab_spectra, ms_per_call), ...])."""
     import torch
     cfg = Config(n_antennas, 2, n_channels, n_taps, chunk_samples, spectra_per_heap, precision,
-                 max_delay_samples, None, 0, 0)
+                 max_delay_samples, None, 0, 0, 0)
     tuned = Config()
     entries = (TuneEntry * 32)()
     n = ctypes.c_int32()
@@ -263,17 +291,22 @@ class Batch:
             pass
 
     def process(self, members, stream=None):
-        """members: list of (Plan, packed uint8 CUDA tensor, first_sample, out int8 CUDA tensor).
-        Returns the first spectrum index of every member."""
+        """members: list of (Plan, packed uint8 CUDA tensor, first_sample, out int8 CUDA tensor
+        [, valid, heap_flags]). Returns the first spectrum index of every member."""
         import torch
         n = len(members)
         descs = (ChunkDesc * max(n, 1))()
-        for i, (plan, packed, first, out) in enumerate(members):
+        for i, m in enumerate(members):
+            plan, packed, first, out = m[:4]
+            valid = m[4] if len(m) > 4 else None
+            flags = m[5] if len(m) > 5 else None
             if packed.numel() != plan.n_antennas * 2 * plan.chunk_samples * 5 // 4:
                 raise ValueError(f"member {i}: packed has the wrong size")
             if out.numel() != plan.info.out_bytes:
                 raise ValueError(f"member {i}: out has the wrong size")
-            descs[i] = ChunkDesc(plan._h.value, _ptr(packed).value, first, _ptr(out).value)
+            descs[i] = ChunkDesc(plan._h.value, _ptr(packed).value, first, _ptr(out).value,
+                                 _ptr(valid).value if valid is not None else None,
+                                 _ptr(flags).value if flags is not None else None)
         fs = (ctypes.c_int64 * max(n, 1))()
         s = stream if stream is not None else torch.cuda.current_stream()
         _check(load().fengine_batch_process(self._h, ctypes.c_void_p(s.cuda_stream), descs, n, fs))
@@ -294,10 +327,10 @@ class ServiceStats(ctypes.Structure):
 def _service_signatures(lib):
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.fengine_service_create.argtypes = [ctypes.POINTER(ServiceConfig), ctypes.POINTER(vp)]
-    lib.fengine_service_submit.argtypes = [vp, vp, vp, i64, vp, ctypes.POINTER(i64)]
+    lib.fengine_service_submit.argtypes = [vp, vp, vp, i64, vp, vp, vp, ctypes.POINTER(i64)]
     lib.fengine_service_set_delay.argtypes = [vp, vp, i32, i32, i64, i64, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double]
-    lib.fengine_service_set_gains.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ctypes.c_float)]
+    lib.fengine_service_set_gains.argtypes = [vp, vp, i32, i32, ctypes.POINTER(ctypes.c_float), i64]
     lib.fengine_service_wait.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_double)]
     lib.fengine_service_get_stats.argtypes = [vp, ctypes.POINTER(ServiceStats)]
     lib.fengine_service_destroy.argtypes = [vp]
@@ -322,15 +355,23 @@ class Service:
         self._h = h
         self._keep = {}
 
-    def submit(self, plan: Plan, h_packed: np.ndarray, first_sample: int, h_out: np.ndarray) -> int:
+    def submit(self, plan: Plan, h_packed: np.ndarray, first_sample: int, h_out: np.ndarray,
+               h_valid: np.ndarray = None, h_heap_flags: np.ndarray = None) -> int:
         if not (h_packed.flags["C_CONTIGUOUS"] and h_out.flags["C_CONTIGUOUS"]):
             raise ValueError("host buffers must be contiguous")
         if h_packed.nbytes != plan.n_antennas * 2 * plan.chunk_samples * 5 // 4 or h_out.nbytes != plan.info.out_bytes:
             raise ValueError("host buffer size mismatch")
+        if h_valid is not None and h_valid.nbytes != plan.n_antennas * 2 * (plan.chunk_samples // HEAP_SAMPLES):
+            raise ValueError("h_valid size mismatch")
+        if h_heap_flags is not None and h_heap_flags.nbytes != plan.n_antennas * plan.heaps:
+            raise ValueError("h_heap_flags size mismatch")
         t = ctypes.c_int64()
         _check(load().fengine_service_submit(self._h, plan._h, h_packed.ctypes.data, first_sample,
-                                             h_out.ctypes.data, ctypes.byref(t)))
-        self._keep[t.value] = (h_packed, h_out)
+                                             h_valid.ctypes.data if h_valid is not None else None,
+                                             h_out.ctypes.data,
+                                             h_heap_flags.ctypes.data if h_heap_flags is not None else None,
+                                             ctypes.byref(t)))
+        self._keep[t.value] = (h_packed, h_out, h_valid, h_heap_flags)
         return t.value
 
     def set_delay(self, plan: Plan, ant: int, pol: int, delay: float, rate: float = 0.0, phase: float = 0.0,
@@ -338,11 +379,11 @@ class Service:
         _check(load().fengine_service_set_delay(self._h, plan._h, ant, pol, t_apply, t_ref, delay, rate, phase,
                                                 phase_rate))
 
-    def set_gains(self, plan: Plan, ant: int, pol: int, gains):
+    def set_gains(self, plan: Plan, ant: int, pol: int, gains, t_apply: int = FAR_PAST):
         g = np.ascontiguousarray(np.broadcast_to(np.asarray(gains, np.complex64), (plan.n_channels,)))
         gi = g.view(np.float32)
         _check(load().fengine_service_set_gains(self._h, plan._h, ant, pol,
-                                                gi.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+                                                gi.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), t_apply))
 
     def wait(self, ticket: int, timeout_ms: int = -1) -> float:
         """Block until the chunk is done; returns its latency in microseconds."""

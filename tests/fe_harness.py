@@ -40,20 +40,28 @@ def streams(seed, n_ant, total, sigma, tones=(), chirp=None):
 
 
 def run_gpu(samples, n_ch, T, L, n_chunks, delays, gains, S=0, D=0, weights=None, start=0,
-            taps=True, prequant=True, precision=fengine.FP32, fft_n1=0, slab_spectra=0):
+            taps=True, prequant=True, precision=fengine.FP32, fft_n1=0, slab_spectra=0, Dmin=0,
+            valids=None, flags=False):
     """Process consecutive chunks of `samples` (starting at absolute `start`).
-    delays[a][p]: list of Seg; gains[a][p]: complex array or None.
-    Returns list of dicts per call (numpy copies of every output)."""
+    delays[a][p]: list of Seg; gains[a][p]: complex array, a list of
+    (t_apply, complex array) gain sets, or None. valids: per call a uint8
+    [ant, pol, L/4096] array of received-heap flags (or None); flags: read
+    back the output-heap flags. Returns list of dicts per call (numpy copies
+    of every output)."""
     import torch
     n_ant = samples.shape[0]
     plan = fengine.Plan(n_ant, n_ch, T, L, spectra_per_heap=S, max_delay_samples=D, weights=weights,
-                        precision=precision, fft_n1=fft_n1, slab_spectra=slab_spectra)
+                        precision=precision, fft_n1=fft_n1, slab_spectra=slab_spectra, min_delay_samples=Dmin)
     for a in range(n_ant):
         for p in range(2):
             for sg in delays[a][p]:
                 plan.set_delay(a, p, sg.delay, sg.rate, sg.phase, sg.phase_rate, sg.t_apply, sg.t_ref)
             if gains is not None and gains[a][p] is not None:
-                plan.set_gains(a, p, gains[a][p])
+                if isinstance(gains[a][p], list):
+                    for t_apply, g in gains[a][p]:
+                        plan.set_gains(a, p, g, t_apply)
+                else:
+                    plan.set_gains(a, p, gains[a][p])
     M, N = plan.M, 2 * n_ch
     res = []
     for c in range(n_chunks):
@@ -64,12 +72,16 @@ def run_gpu(samples, n_ch, T, L, n_chunks, delays, gains, S=0, D=0, weights=None
         d_out = torch.empty(plan.info.out_bytes, dtype=torch.int8, device="cuda")
         d_pre = torch.empty(n_ant * 2 * M * n_ch * 2, dtype=torch.float32, device="cuda") if prequant else None
         d_tap = torch.empty(n_ant * 2 * M * N, dtype=torch.int32, device="cuda") if taps else None
-        m0 = plan.process(d_in, start + lo, d_out, d_pre, d_tap)
+        d_valid = (torch.from_numpy(np.ascontiguousarray(valids[c], np.uint8)).cuda()
+                   if valids is not None and valids[c] is not None else None)
+        d_flags = torch.full((n_ant, plan.heaps), 7, dtype=torch.uint8, device="cuda") if flags else None
+        m0 = plan.process(d_in, start + lo, d_out, d_pre, d_tap, valid=d_valid, heap_flags=d_flags)
         torch.cuda.synchronize()
         res.append(dict(
-            m0=m0, out=d_out.cpu().numpy(),
+            m0=m0, out=d_out.cpu().numpy(), flags=(d_flags.cpu().numpy() if flags else None),
             pre=(d_pre.cpu().numpy().view(np.complex64).reshape(n_ant, 2, M, n_ch) if prequant else None),
             tap=(d_tap.cpu().numpy().reshape(n_ant, 2, M, N) if taps else None)))
+    plan.device_status()          # raises if a kernel recorded a timeout or a clamped delay
     plan.close()
     return res, M, plan.S
 
@@ -89,6 +101,8 @@ def run_oracle(samples, n_ch, T, delays, gains, m0, M, weights=None, start=0):
     for a in range(n_ant):
         for p in range(2):
             g = np.ones(n_ch) if gains is None or gains[a][p] is None else gains[a][p]
+            if isinstance(g, list):
+                g = [(t, np.asarray(x)) for t, x in g]
             dm = oracle_model(delays[a][p]) if delays[a][p] else O.DelayModel()
             pr, qq, cc = O.channelize(samples[a, p].astype(np.int32), start, N, T, w, dm, g, m0, M)
             pre[a, p], q[a, p], co[a, p] = pr, qq, cc

@@ -35,7 +35,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_strerror(lib):
-    assert lib.fengine_abi_version() == 2
+    assert lib.fengine_abi_version() == 3 == fengine.ABI_VERSION
     for st in range(9):
         assert lib.fengine_strerror(st)
     assert b"unknown" in lib.fengine_strerror(99)
@@ -74,12 +74,14 @@ def test_quantiser_matches_oracle_on_every_tie_and_neighbour(lib):
     (dict(chunk_samples=1000), 1), (dict(spectra_per_heap=10 ** 6), 1),
     (dict(max_delay_samples=-1), 1), (dict(n_antennas=0), 1),
     (dict(fft_n1=12), 1), (dict(fft_n1=128), 1), (dict(fft_n1=2), 1), (dict(slab_spectra=33), 1),
-    (dict(slab_spectra=-32), 1), (dict(precision=1, n_channels=16, chunk_samples=32 * 8), 7),
+    (dict(slab_spectra=-32), 1), (dict(min_delay_samples=1), 1), (dict(min_delay_samples=-(2 ** 31)), 1),
+    (dict(precision=1, n_channels=16, chunk_samples=32 * 8), 7),
     (dict(precision=2, n_channels=16, chunk_samples=32 * 8), 7),
     (dict(precision=1, n_channels=8192, fft_n1=32, chunk_samples=16384 * 4), 1)])
 def test_plan_config_validation_before_any_device_call(lib, kw, status):
     cfg = dict(n_antennas=1, n_pols=2, n_channels=1024, n_taps=16, chunk_samples=2048 * 8,
-               spectra_per_heap=0, precision=0, max_delay_samples=0, weights=None, fft_n1=0, slab_spectra=0)
+               spectra_per_heap=0, precision=0, max_delay_samples=0, weights=None, fft_n1=0, slab_spectra=0,
+               min_delay_samples=0)
     cfg.update(kw)
     c = fengine.Config(**cfg)
     h = ctypes.c_void_p()
@@ -100,7 +102,7 @@ def test_binding_refuses_without_library(tmp_path):
 def test_autotune_rejects_bad_arguments_before_any_device_call(lib):
     c = fengine.Config(n_antennas=1, n_pols=2, n_channels=1024, n_taps=16, chunk_samples=2048 * 8,
                        spectra_per_heap=0, precision=0, max_delay_samples=0, weights=None, fft_n1=0,
-                       slab_spectra=0)
+                       slab_spectra=0, min_delay_samples=0)
     tuned = fengine.Config()
     n = ctypes.c_int32(-1)
     assert lib.fengine_autotune(ctypes.byref(c), None, 0, ctypes.byref(tuned), None, 0, ctypes.byref(n)) == 1
@@ -126,9 +128,9 @@ def test_batch_and_service_refuse_bad_arguments_before_any_device_call(lib):
     assert lib.fengine_service_create(None, ctypes.byref(h)) == EINVAL
     assert lib.fengine_service_create(ctypes.byref(fengine.ServiceConfig(4, 1 << 30)), None) == EINVAL
     ticket = ctypes.c_int64()
-    assert lib.fengine_service_submit(None, None, None, 0, None, ctypes.byref(ticket)) == EINVAL
+    assert lib.fengine_service_submit(None, None, None, 0, None, None, None, ctypes.byref(ticket)) == EINVAL
     assert lib.fengine_service_set_delay(None, None, 0, 0, 0, 0, 1.0, 0.0, 0.0, 0.0) == EINVAL
-    assert lib.fengine_service_set_gains(None, None, 0, 0, None) == EINVAL
+    assert lib.fengine_service_set_gains(None, None, 0, 0, None, 0) == EINVAL
     lat = ctypes.c_double()
     assert lib.fengine_service_wait(None, 0, 10, ctypes.byref(lat)) == EINVAL
     assert lib.fengine_service_get_stats(None, None) == EINVAL
