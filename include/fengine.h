@@ -341,7 +341,9 @@ fengine_status fengine_service_destroy(fengine_service_t svc);
  * file-scope device array of FENGINE_NOALLOC_SCRATCH_BYTES that every GPU
  * which loads the library holds until the process exits.
  *  - The first call on a device looks up that array's device address (with
- *    the device current); make that first call before any stream capture.
+ *    the device current); make that first call before any stream capture
+ *    (a first call on a stream that is being captured is refused with
+ *    FENGINE_EINVAL).
  *  - Every call shares the array and overwrites it: calls whose work
  *    overlaps on the GPU (different streams, or different host threads
  *    without ordering) race; order them on one stream.
@@ -363,7 +365,9 @@ typedef struct {
  * d_weights    device [2n T] prototype w[t + 2n j].
  * d_gains      device [antenna][pol][n] complex gains as (re, im) floats.
  * delay_models host [antenna][pol][5] doubles: delay, delay_rate, phase,
- *              phase_rate, t_ref -- one model per stream, as fengine_set_delay.
+ *              phase_rate, t_ref -- one model per stream, as fengine_set_delay;
+ *              all finite and t_ref an integer (FENGINE_EINVAL otherwise).
+ *              Coarse delays must stay in [0, D] (no negative delays here).
  * d_out        device, same layout as fengine_process_chunk's.
  * All device buffers 4-byte aligned. The output equals fengine_process_chunk's
  * for the same samples, weights, gains and delay models (within the

@@ -9,6 +9,7 @@
 // its working storage (delay table, twiddle tables, delay models and the
 // inter-phase intermediate) in one file-scope device array of fixed size,
 // which every GPU that loads the library holds until the process exits.
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -30,14 +31,23 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mu;
 unsigned char *g_scratch_dev[kMaxDevices] = {nullptr};
 
-// Set-up once per device, with that device current.
-cudaError_t scratch_address(unsigned char **out) {
+// Set-up once per device, with that device current. The lookup is not
+// attempted while `st` is being captured into a graph (the first call on a
+// device must come before any capture): that call is refused instead.
+cudaError_t scratch_address(unsigned char **out, cudaStream_t st, bool *capturing) {
+    *capturing = false;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch_dev[dev]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess) return e;
+        if (cs != cudaStreamCaptureStatusNone) {
+            *capturing = true;
+            return cudaErrorStreamCaptureUnsupported;
+        }
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
@@ -50,7 +60,8 @@ cudaError_t scratch_address(unsigned char **out) {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Models {
-    double d[FENGINE_NOALLOC_MAX_STREAMS][5];   // delay, rate, phase, phase_rate, t_ref
+    double d[FENGINE_NOALLOC_MAX_STREAMS][4];   // delay, rate, phase, phase_rate
+    long long t_ref[FENGINE_NOALLOC_MAX_STREAMS];
 };
 
 // Writes one delay segment per stream into the scratch (so the shared delay
@@ -63,7 +74,7 @@ __global__ void k_noalloc_setup(Models m, int n_streams, fe::DelaySeg *seg, int 
     if (i < n_streams) {
         fe::DelaySeg s;
         s.t_apply = -(1LL << 62);
-        s.t_ref = (long long)m.d[i][4];
+        s.t_ref = m.t_ref[i];
         s.d0 = m.d[i][0];
         s.rate = m.d[i][1];
         s.phi0 = m.d[i][2];
@@ -98,8 +109,9 @@ fengine_status fengine_process_chunk_noalloc(const fengine_noalloc_args *a, cons
                                              const float *d_gains, const double *delay_models,
                                              int8_t *d_out, void *cuda_stream) {
     if (!a || !d_history || !d_packed || !d_weights || !d_gains || !delay_models || !d_out) return FENGINE_EINVAL;
+    if (a->n_antennas < 1 || a->n_antennas > FENGINE_NOALLOC_MAX_STREAMS / 2) return FENGINE_EINVAL;
     const int n = a->n_channels, T = a->n_taps, nant = a->n_antennas, ns = 2 * nant;
-    if (nant < 1 || ns > FENGINE_NOALLOC_MAX_STREAMS || !is_pow2(n) || n < 16 || n > 32768) return FENGINE_EINVAL;
+    if (!is_pow2(n) || n < 16 || n > 32768) return FENGINE_EINVAL;
     if (!(T == 1 || T == 2 || T == 4 || T == 8 || T == 16 || T == 32)) return FENGINE_EINVAL;
     const long long N = 2LL * n;
     if (a->chunk_samples <= 0 || a->chunk_samples % N || a->first_sample % N) return FENGINE_EINVAL;
@@ -109,9 +121,20 @@ fengine_status fengine_process_chunk_noalloc(const fengine_noalloc_args *a, cons
     if (S < 1 || S > M || M > (1LL << 30)) return FENGINE_EINVAL;
     if (a->chunk_samples + N * T + a->max_delay_samples + 16 >= (1LL << 31)) return FENGINE_EINVAL;
     if (((uintptr_t)d_history & 3) || ((uintptr_t)d_packed & 3) || ((uintptr_t)d_out & 3)) return FENGINE_EINVAL;
+    // every model finite, t_ref an integer timestamp (converted once, used
+    // by both the range check below and the device's delay table)
+    Models m;
+    for (int s = 0; s < ns; s++) {
+        for (int j = 0; j < 5; j++)
+            if (!std::isfinite(delay_models[5 * s + j])) return FENGINE_EINVAL;
+        const double tr = delay_models[5 * s + 4];
+        if (tr != std::floor(tr) || std::fabs(tr) > 9.0e18) return FENGINE_EINVAL;
+        m.t_ref[s] = (long long)tr;
+        for (int j = 0; j < 4; j++) m.d[s][j] = delay_models[5 * s + j];
+    }
     for (int s = 0; s < ns; s++) {
         // the one delay model of each stream must keep c in [0, D] over the call
-        const double dt0 = (double)(N * (a->first_sample / N - (T - 1))) - delay_models[5 * s + 4];
+        const double dt0 = (double)(N * (a->first_sample / N - (T - 1)) - m.t_ref[s]);
         const double dt1 = dt0 + (double)(N * (M - 1));
         for (double dt : {dt0, dt1}) {
             volatile double prod = delay_models[5 * s + 1] * dt;
@@ -141,13 +164,10 @@ fengine_status fengine_process_chunk_noalloc(const fengine_noalloc_args *a, cons
     if (SL > (M + 31) / 32 * 32) SL = (M + 31) / 32 * 32;
     if (SL < 32) return FENGINE_EINVAL;   // this shape needs more than the fixed scratch
 
-    unsigned char *base = nullptr;
-    if (scratch_address(&base) != cudaSuccess) return FENGINE_ECUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-
-    Models m;
-    for (int s = 0; s < ns; s++)
-        for (int j = 0; j < 5; j++) m.d[s][j] = delay_models[5 * s + j];
+    unsigned char *base = nullptr;
+    bool capturing = false;
+    if (scratch_address(&base, st, &capturing) != cudaSuccess) return capturing ? FENGINE_EINVAL : FENGINE_ECUDA;
     const int setup_n = (N1 / 2 + 1) * N2 > ns ? (N1 / 2 + 1) * N2 : ns;
     k_noalloc_setup<<<(setup_n + 255) / 256, 256, 0, st>>>(
         m, ns, reinterpret_cast<fe::DelaySeg *>(base + o_seg), reinterpret_cast<int *>(base + o_nseg),

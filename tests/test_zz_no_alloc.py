@@ -42,9 +42,14 @@ def _pack(s):
     return np.stack([np.stack([synth.pack10(s[a, p]) for p in range(2)]) for a in range(s.shape[0])])
 
 
-def test_noalloc_matches_plan_on_two_calls(lib):
+@pytest.mark.parametrize("n_ant,n,T,M,D,S", [
+    (2, 1024, 16, 48, 40, 16),     # one slab, N2 = 256
+    (1, 32768, 16, 128, 40, 20),   # N1 = 64, N2 = 1024 (persistent second stage); its working storage
+                                   # holds 96 spectra, so a call is two slabs through one intermediate,
+                                   # and heaps of 20 spectra straddle the slab boundary
+])
+def test_noalloc_matches_plan_on_two_calls(lib, n_ant, n, T, M, D, S):
     import torch
-    n_ant, n, T, M, D, S = 2, 1024, 16, 48, 40, 16
     N = 2 * n
     L = N * M
     H = (N * (T - 1) + D + 15) // 16 * 16
@@ -82,7 +87,7 @@ def test_noalloc_matches_plan_on_two_calls(lib):
         torch.cuda.synchronize()
         a_ref, a_out = ref.cpu().numpy().astype(np.int16), out.cpu().numpy().astype(np.int16)
         diff = np.abs(a_ref - a_out)
-        print(f"[no-alloc] call {c}: exact fraction {np.mean(diff == 0):.6f}")
+        print(f"[no-alloc] n={n} call {c}: exact fraction {np.mean(diff == 0):.6f}")
         assert diff.max() <= 1
     plan.close()
 
@@ -99,3 +104,20 @@ def test_noalloc_refuses_shapes_beyond_its_storage(lib):
             dm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), dummy.data_ptr(),
             torch.cuda.current_stream().cuda_stream)
         assert st == 1
+
+
+def test_noalloc_refuses_non_finite_or_fractional_models(lib):
+    import torch
+    n, T, L = 1024, 4, 2048 * 8
+    dummy = torch.zeros(2 * L, dtype=torch.uint8, device="cuda")
+    w = torch.zeros(2 * n * T, dtype=torch.float32, device="cuda")
+    g = torch.zeros(4 * n, dtype=torch.float32, device="cuda")
+    out = torch.zeros(n * 8 * 4, dtype=torch.int8, device="cuda")
+    args = NoAllocArgs(1, n, T, 0, L, 10, 0)
+    for bad in ([1.0, float("nan"), 0, 0, 0], [1.0, 0, float("inf"), 0, 0], [1.0, 0, 0, 0, 0.5]):
+        dm = np.array(bad + [1.0, 0, 0, 0, 0], np.float64)
+        st = lib.fengine_process_chunk_noalloc(
+            ctypes.byref(args), dummy.data_ptr(), dummy.data_ptr(), w.data_ptr(), g.data_ptr(),
+            dm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.data_ptr(),
+            torch.cuda.current_stream().cuda_stream)
+        assert st == 1, bad
