@@ -60,9 +60,12 @@ struct fengine_plan_s {
     long long *d_gtap = nullptr;    // [stream][kMaxGainSeg] t_apply of each gain set
     int *d_ngs = nullptr;           // [stream] gain sets in use
     unsigned char *d_gsel = nullptr;   // [stream][M] gain set of each spectrum
+    unsigned char *d_cchg = nullptr;   // [stream][M] coarse delay changes at this spectrum
     // reduced-precision forms: tensor-core phase-1 operand blocks and per-column epilogue scales
     uint16_t *d_bmat = nullptr;
     float *d_oscale = nullptr;
+    uint16_t *d_cols = nullptr;     // FP16 column sequences of history + chunk (per call)
+    int cols_rtp = 0;
     float tc_unscale = 1.0f;        // inverse of the FP16 intermediate's scale
     bool tc1 = false;               // phase 1 on tensor cores
     int tc_splits = 1;              // tensor-core phase-1 item ranges per column group (per slab)
@@ -117,6 +120,7 @@ void release(fengine_plan_s *pl) {
     cudaFree(pl->d_tw2);
     cudaFree(pl->d_bmat);
     cudaFree(pl->d_oscale);
+    cudaFree(pl->d_cols);
     cudaFree(pl->d_gains);
     cudaFree(pl->d_ftab);
     cudaFree(pl->d_A);
@@ -126,6 +130,7 @@ void release(fengine_plan_s *pl) {
     cudaFree(pl->d_gtap);
     cudaFree(pl->d_ngs);
     cudaFree(pl->d_gsel);
+    cudaFree(pl->d_cchg);
     cudaFree(pl->d_hvalid[0]);
     cudaFree(pl->d_hvalid[1]);
     cudaFree(pl->d_nseg);
@@ -333,6 +338,7 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         (e = dalloc(pl, &pl->d_gtap, sizeof(long long) * ns * fe::kMaxGainSeg)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_ngs, sizeof(int) * ns)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_gsel, (size_t)ns * M)) != cudaSuccess ||
+        (e = dalloc(pl, &pl->d_cchg, (size_t)ns * M)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_hvalid[0], (size_t)ns * pl->HV)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_hvalid[1], (size_t)ns * pl->HV)) != cudaSuccess ||
         (e = dalloc(pl, &pl->d_ftab, sizeof(float2) * ns * M)) != cudaSuccess ||
@@ -394,6 +400,14 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         float s_int = 1.0f;
         fe::build_phase1_tc_tables((int)N, T, pl->precision, w.data(), bmat, osc, s_int);
         pl->tc_unscale = 1.0f / s_int;
+        pl->cols_rtp = fe::unpack_cols_rows(pl->H, pl->L, pl->D, pl->Dmin, (int)N, T);
+        const size_t cols_bytes = sizeof(uint16_t) * (size_t)pl->n_streams * (N / 8) * pl->cols_rtp;
+        if ((e = dalloc(pl, &pl->d_cols, cols_bytes)) != cudaSuccess) {
+            release(pl);
+            g_last_error = std::string("device allocation: ") + cudaGetErrorString(e);
+            return FENGINE_ENOMEM;
+        }
+        pl->scratch_bytes += cols_bytes;
         if ((e = dalloc(pl, &pl->d_bmat, sizeof(uint16_t) * bmat.size())) != cudaSuccess ||
             (e = dalloc(pl, &pl->d_oscale, sizeof(float) * osc.size())) != cudaSuccess ||
             (e = cudaMemcpy(pl->d_bmat, bmat.data(), sizeof(uint16_t) * bmat.size(), cudaMemcpyHostToDevice)) !=
@@ -406,10 +420,12 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        // column groups x item ranges: about eight CTAs per SM over a slab
+        // column groups x item ranges: one wave of two CTAs per SM (the
+        // CTAs keep their operand blocks for all their items; a second wave
+        // would reload them and leave SMs idle at its end)
         const int R = fe::phase1_tc_R((int)N), n_cg = pl->N2 / (8 / R);
         const long long items = (long long)pl->n_streams * ((pl->SL + 127) / 128);
-        long long sp = ((long long)8 * (sms > 0 ? sms : 148) + n_cg - 1) / n_cg;
+        long long sp = (long long)2 * (sms > 0 ? sms : 148) / n_cg;
         if (sp > items) sp = items;
         pl->tc_splits = (int)(sp < 1 ? 1 : sp);
     }
@@ -632,6 +648,7 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     dp.g_tapply = pl->d_gtap;
     dp.n_gsets = pl->d_ngs;
     dp.gsel = pl->d_gsel;
+    dp.cchg = pl->d_cchg;
     prof_begin(pl, 0, st);
     if ((e = fe::launch_delay_table(dp, st)) != cudaSuccess) return cuda_fail(e, "delay table launch");
     prof_end(pl, st);
@@ -698,23 +715,44 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     p2.tc_unscale = pl->tc_unscale;
 
     fe::Phase1TcParams pt{};
-    pt.chunk = d_packed;
-    pt.hist = pl->d_hist[pl->cur];
-    pt.chunk_bytes = pl->chunk_bytes;
-    pt.hist_bytes = pl->hist_bytes;
-    pt.H = pl->H;
-    pt.L = pl->L;
+    if (pl->tc1) {
+        // unpack history + chunk into FP16 column sequences (row origin a
+        // multiple of 8, so that 16-byte copies of a column stay aligned)
+        const long long P = pl->N / 8;
+        auto fdiv = [](long long a, long long b) { return a / b - ((a % b != 0 && a < 0) ? 1 : 0); };
+        fe::UnpackColsParams up{};
+        up.chunk = d_packed;
+        up.hist = pl->d_hist[pl->cur];
+        up.chunk_bytes = pl->chunk_bytes;
+        up.hist_bytes = pl->hist_bytes;
+        up.H = pl->H;
+        up.L = pl->L;
+        up.t_in = first_sample;
+        up.P = (int)P;
+        // pre-delayed by c0 in [Dmin, D]: rows from the history start shifted by Dmin
+        up.rb = fdiv(fdiv(first_sample - pl->H + pl->Dmin, P), 8) * 8;
+        up.RT = (int)(fdiv(first_sample + pl->L + pl->D, P) + 1 - up.rb);
+        up.ctab = pl->d_ctab;
+        up.M = pl->M;
+        up.RTP = pl->cols_rtp;
+        up.cols = pl->d_cols;
+        up.n_streams = pl->n_streams;
+        if ((e = fe::launch_unpack_cols(up, st)) != cudaSuccess) return cuda_fail(e, "unpack launch");
+        pt.cols = pl->d_cols;
+        pt.rb = up.rb;
+        pt.RTP = pl->cols_rtp;
+    }
     pt.N = pl->N;
     pt.N2 = pl->N2;
     pt.M = pl->M;
     pt.m0 = m0;
-    pt.t_in = first_sample;
     pt.a_spectra = pl->SL;
     pt.n_streams = pl->n_streams;
     pt.splits = pl->tc_splits;
     pt.bmat = pl->d_bmat;
     pt.oscale = pl->d_oscale;
     pt.ctab = pl->d_ctab;
+    pt.cchg = pl->d_cchg;
     pt.window_tap = d_window_tap;
     pt.err = pl->d_err;
 

@@ -50,6 +50,7 @@ struct DelayTableParams {
     const long long *g_tapply; // [stream][kMaxGainSeg], nullptr: one set
     const int *n_gsets;        // [stream]
     unsigned char *gsel;       // out [stream][M] gain-set index (when g_tapply is given)
+    unsigned char *cchg;       // out [stream][M] 1 where the coarse delay differs from the previous spectrum's (optional)
 };
 
 // Lost data (Sec. 3.7): per-spectrum usability from the received-heap flags,
@@ -137,21 +138,38 @@ size_t phase2_smem_bytes(int N2, int R2);
 // (k_phase1_tc.cu): first-stage radix N1 = 8 R with R = phase1_tc_R(N), so
 // N2 = N / N1 <= 1024; the output is the second-stage input
 // [stream][a_spectra][N1/2 + 1][N2] as FP16 pairs (FP16 form, scaled by
-// s_int) or FP32 pairs (BF16 form).
-struct Phase1TcParams {
+// s_int) or FP32 pairs (BF16 form). It reads the samples as FP16 column
+// sequences: cols[stream][col][r] holds the sample at timestamp
+// (rb + r) P + col - c0, P = N / 8, c0 = the stream's first coarse delay of
+// the call (k_unpack_cols writes them each call).
+struct UnpackColsParams {
     const uint8_t *chunk;     // [stream][chunk_bytes]
     const uint8_t *hist;      // [stream][hist_bytes], samples [t_in - H, t_in)
     long long chunk_bytes, hist_bytes;
-    long long H, L;           // history samples, chunk samples
+    long long H, L, t_in;
+    int P;                    // N / 8
+    long long rb;             // absolute row of column row 0 (a multiple of 8)
+    int RT, RTP;              // rows holding samples; rows per column (padded, a multiple of 64)
+    uint16_t *cols;           // out [stream][P][RTP] FP16, pre-delayed by ctab[stream][0]
+    const int *ctab;          // [stream][M] coarse delays
+    int M;
+    int n_streams;
+};
+
+struct Phase1TcParams {
+    const uint16_t *cols;     // [stream][P][RTP] FP16 samples (UnpackColsParams)
+    long long rb;
+    int RTP;
     int N, N2;                // FFT length, second-stage size
     int M;                    // spectra per call
-    long long m0, t_in;       // first spectrum of the call, first sample of the chunk
+    long long m0;             // first spectrum of the call
     int q_begin, q_count;     // the slab of spectra this launch covers
     int a_spectra;            // spectra per stream in the intermediate buffer
-    int n_streams, splits;    // item ranges per column group (grid = column groups x splits)
+    int n_streams, splits;    // item ranges per column group (grid = column groups x slices x splits)
     const uint16_t *bmat;     // operand blocks, build_phase1_tc_tables
     const float *oscale;      // [N2] epilogue scale per output column
     const int *ctab;          // [stream][M] coarse delays
+    const unsigned char *cchg;   // [stream][M] 1 where the coarse delay changes (DelayTableParams::cchg)
     void *A;                  // out: second-stage input
     int *window_tap;          // optional out [stream][M][N]
     int *err;                 // set to 2 if a bounded wait gave up
@@ -162,5 +180,14 @@ size_t phase1_tc_smem_bytes(int R, int T, int precision);
 void build_phase1_tc_tables(int N, int T, int precision, const float *w, std::vector<uint16_t> &bmat,
                             std::vector<float> &oscale, float &s_int);
 cudaError_t launch_phase1_tc(int T, int precision, const Phase1TcParams &p, cudaStream_t s);
+cudaError_t launch_unpack_cols(const UnpackColsParams &p, cudaStream_t s);
+// rows of the FP16 column buffer: a call's history + chunk plus the reach of
+// a 128-spectrum pass past the chunk end, padded to a multiple of 64
+inline int unpack_cols_rows(long long H, long long L, long long D, long long Dmin, int N, int T) {
+    const long long P = N / 8;
+    const long long rt = (H + L + D - Dmin) / P + 3 + 8;
+    const long long reach = 8LL * (127 + (T < 2 ? 2 : T)) + 64;
+    return (int)((rt + reach + 63) / 64 * 64);
+}
 
 }  // namespace fe

@@ -53,6 +53,21 @@ __global__ void k_delay_table(const DelayTableParams p) {
     }
     p.ctab[e] = (int)ci;
     p.ftab[e] = make_float2((float)delta, (float)red);
+    if (p.cchg) {
+        // the previous spectrum's coarse delay, recomputed the same way
+        int chg = 0;
+        if (q > 0) {
+            const long long tp = t0 - p.N;
+            int sp = 0;
+            for (int k = 0; k < ns; k++)
+                if (sg[k].t_apply <= tp) sp = k;
+            const double dp = __dadd_rn(sg[sp].d0, __dmul_rn(sg[sp].rate, (double)(tp - sg[sp].t_ref)));
+            long long cp = (long long)floor(__dadd_rn(dp, 0.5));
+            cp = cp < p.min_delay ? p.min_delay : (cp > p.max_delay ? p.max_delay : cp);
+            chg = cp != ci;
+        }
+        p.cchg[e] = (unsigned char)chg;
+    }
     if (p.g_tapply) {
         const long long *ta = p.g_tapply + (long long)st * kMaxGainSeg;
         int g = 0;

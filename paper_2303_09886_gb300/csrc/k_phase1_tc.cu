@@ -29,13 +29,16 @@
 // FP16 form: 10-bit integers are exact in FP16. BF16 form: a sample is split
 // into hi + lo BF16 parts (both exact), two MMAs per K step.
 //
-// A CTA owns 8 physical columns (CW = 8 / R output columns) and a range of
+// The packed stream is first unpacked into FP16 column sequences
+// (k_unpack_cols: coalesced reads of the packed rows, one transpose through
+// shared memory), so that a CTA reads each of its columns contiguously. A
+// CTA owns 8 physical columns (CW = 8 / R output columns) and a range of
 // (stream, 128-spectrum tile) items; each tile is one pass per run of equal
-// coarse delay. Passes are double-buffered: the CTA decodes pass p + 1 while
-// the tensor core runs pass p and the epilogue drains pass p - 1 from the
-// other half of tensor memory (tcgen05.ld), scales it and stores the
-// second-stage input [stream][spectrum][k1][t2] (FP16 pairs, or FP32 pairs in
-// the BF16 form).
+// coarse delay. Warp roles overlap the passes: fill warps copy pass p + 1's
+// column sequences into shared memory while the MMA warp runs pass p on the
+// tensor core and the epilogue warps drain pass p - 1 from the other half of
+// tensor memory (tcgen05.ld), scale it and store the second-stage input
+// [stream][spectrum][k1][t2] (FP16 pairs, or FP32 pairs in the BF16 form).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -49,7 +52,7 @@ namespace fe {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 288;   // 4 epilogue warps, 4 fill warps, 1 MMA warp
 constexpr int kTcRows = 128;     // spectra per pass: the MMA's M
 constexpr int kTcPhys = 8;       // physical FIR columns per CTA
 constexpr int kTcTmemCols = 256; // tensor-memory columns per CTA (two pass buffers)
@@ -66,7 +69,7 @@ constexpr long long kTcSmemMax = 227 * 1024;
 __host__ __device__ constexpr long long tc_smem(int R, int T, int prec, int ks, int nxb) {
     return 2LL * ((prec == 2 ? 2 : 1) * kTcPhys * (long long)tc_nm(R, ks) * 8 * tc_tp(T) +
                   (long long)nxb * (prec == 2 ? 2 : 1) * kTcPhys * tc_xl(T)) +
-           4 * kTcRows + 64 + 2048;
+           4 * kTcRows + 64 + 2048 + 256;
 }
 // fewest k1-slices, then two decode buffers (the decode of the next pass
 // under the current one's MMAs), that fit in shared memory; 0 if none does
@@ -111,22 +114,17 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
+// try_wait with a suspend-time hint: the thread sleeps (up to about 20 us)
+// until the phase completes instead of spinning on issue slots
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, "
+        "p;\n\t}\n"
         : "=r"(ok)
-        : "r"(mbar), "r"(parity)
+        : "r"(mbar), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
-}
-
-// Wait for the given phase of an mbarrier, giving up after about a second.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try(mbar, parity))
-        if (clock64() - t0 > 2000000000LL) return false;
-    return true;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -151,45 +149,225 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 
 // ---- 10-bit samples ----
 
-// Offset-binary FP16 of a 10-bit two's-complement field f: the FP16 with
-// exponent 2^10 and mantissa (f ^ 512) is 1024 + (v + 512); subtracting 1536
-// (exact) gives v. Two fields at once as a half2.
+// FP16 of a 10-bit two's-complement field f: the FP16 with exponent 2^10 and
+// mantissa (f ^ 512) is 1024 + (v + 512); subtracting 1536 (exact) gives v.
+__device__ __forceinline__ uint16_t field_to_half(uint32_t f) {
+    const __half h = __hsub(__ushort_as_half((unsigned short)(((f ^ 0x200u) | 0x6400u) & 0xFFFFu)),
+                            __ushort_as_half(0x6600u));
+    return __half_as_ushort(h);
+}
+
+// Two fields as an FP16 pair (f0 in the low half).
 __device__ __forceinline__ uint32_t fields_to_half2(uint32_t f0, uint32_t f1) {
     const uint32_t h = (((f0 ^ 0x200u) | 0x6400u) & 0xFFFFu) | ((((f1 ^ 0x200u) | 0x6400u) & 0xFFFFu) << 16);
-    const __half2 r = __hsub2(*reinterpret_cast<const __half2 *>(&h), __halves2half2(__ushort_as_half(0x6600u),
-                                                                                     __ushort_as_half(0x6600u)));
+    const __half2 r = __hsub2(*reinterpret_cast<const __half2 *>(&h),
+                              __halves2half2(__ushort_as_half(0x6600u), __ushort_as_half(0x6600u)));
     return *reinterpret_cast<const uint32_t *>(&r);
 }
 
-__device__ __forceinline__ int field_value(uint32_t f) { return (int)f - (int)((f & 0x200u) << 1); }
-
-// BF16 hi and lo parts of two integer samples (|v| <= 512): hi = RN(v), lo = v - hi, both exact.
-__device__ __forceinline__ void ints_to_bf16x2(int v0, int v1, uint32_t &hi, uint32_t &lo) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn((float)v0), h1 = __float2bfloat16_rn((float)v1);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn((float)v0 - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn((float)v1 - __bfloat162float(h1));
+// BF16 hi and lo parts of two integer samples held as an FP16 pair: hi =
+// RN(v), lo = v - hi, both exact (|v| <= 512).
+__device__ __forceinline__ void half2_to_bf16x2(uint32_t h2, uint32_t &hi, uint32_t &lo) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&h2));
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(f.x), h1 = __float2bfloat16_rn(f.y);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(f.x - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(f.y - __bfloat162float(h1));
     hi = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
     lo = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
 }
 
-// Sample at position s from the first history sample (history, then chunk;
-// zero outside [0, HL)); fields are read as two big-endian bytes.
-__device__ __forceinline__ uint32_t field_at(const uint8_t *hist, const uint8_t *chunk, long long s, long long H,
-                                             long long HL) {
-    if (s < 0 || s >= HL) return 0u;   // the field of value 0
-    const bool h = s < H;
-    const long long u = h ? s : s - H;
-    const uint8_t *b = (h ? hist : chunk) + ((5 * u) >> 2);
-    const unsigned v = ((unsigned)__ldg(b) << 8) | (unsigned)__ldg(b + 1);
-    return (v >> (6u - 2u * (unsigned)(u & 3))) & 0x3FFu;
+__device__ __forceinline__ long long floor_div(long long a, long long b) {
+    const long long q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
 }
 
+// ---- pass enumeration (one warp at a time, every role the same sequence) ----
+//
+// A pass is a run of consecutive spectra [ra, rb) of one (stream, 128-spectrum
+// tile) item with one coarse delay c (Eq. 1's window start moves with c). A
+// warp keeps the delay-change flags of the current item as a 128-bit ballot
+// mask and loads the next item's flags, row-0 delay and its stream's first
+// delay c0 one item ahead, so that no load latency sits between passes.
 struct Pass {
-    int st, q0, ra, rb, c;
+    int st, q0, ra, rb, c, c0;
 };
+
+struct PassIter {
+    int it, it_end, ra, rows, st, q0, c_row0, c0;
+    unsigned m[4];            // bit l of m[k]: the delay changes at row 32 k + l
+    unsigned char f[4];       // prefetched flags of rows 32 k + lane of the next item
+    int pc_row0, pc0;         // prefetched delays of the next item
+};
+
+__device__ __forceinline__ void pass_prefetch(PassIter &s, const Phase1TcParams &p, int n_tiles, int item) {
+    const int lane = threadIdx.x & 31;
+    if (item >= s.it_end) return;
+    const int st = item / n_tiles, q0 = p.q_begin + (item % n_tiles) * kTcRows;
+    const int rows = min(kTcRows, p.q_begin + p.q_count - q0);
+    const unsigned char *cf = p.cchg + (long long)st * p.M + q0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) s.f[k] = (32 * k + lane < rows) ? __ldg(cf + 32 * k + lane) : (unsigned char)0;
+    s.pc_row0 = __ldg(p.ctab + (long long)st * p.M + q0);
+    s.pc0 = __ldg(p.ctab + (long long)st * p.M);
+}
+
+__device__ __forceinline__ bool warp_next_pass(PassIter &s, Pass &ps, const Phase1TcParams &p, int n_tiles) {
+    for (;;) {
+        if (s.ra < 0) {
+            if (s.it >= s.it_end) return false;
+            s.st = s.it / n_tiles;
+            s.q0 = p.q_begin + (s.it % n_tiles) * kTcRows;
+            s.rows = min(kTcRows, p.q_begin + p.q_count - s.q0);
+#pragma unroll
+            for (int k = 0; k < 4; k++) s.m[k] = __ballot_sync(0xFFFFFFFFu, s.f[k] != 0);
+            s.c_row0 = s.pc_row0;
+            s.c0 = s.pc0;
+            s.ra = 0;
+            pass_prefetch(s, p, n_tiles, s.it + 1);
+        }
+        if (s.ra >= s.rows) {
+            s.ra = -1;
+            s.it++;
+            continue;
+        }
+        // first change after ra
+        int rb = s.rows;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int lo = s.ra + 1 - 32 * k;   // rows >= ra + 1 in this word
+            unsigned mk = s.m[k];
+            if (lo >= 32) mk = 0u;
+            else if (lo > 0) mk &= ~0u << lo;
+            if (mk && rb == s.rows) rb = 32 * k + __ffs(mk) - 1;
+        }
+        if (rb > s.rows) rb = s.rows;
+        const int c = s.ra == 0 ? s.c_row0 : __ldg(p.ctab + (long long)s.st * p.M + s.q0 + s.ra);
+        ps = Pass{s.st, s.q0, s.ra, rb, c, s.c0};
+        s.ra = rb;
+        return true;
+    }
+}
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Unpack into FP16 columns, pre-delayed by each stream's first coarse delay
+// c0 = ctab[stream][0]: cols[st][col][r] holds the sample at timestamp
+// (rb + r) P + col - c0 (zero before the history and past the chunk), so that
+// for every pass with coarse delay c0 a FIR column's sequence x_t[u] starts
+// at a row that is a multiple of 8 (16-byte aligned) and is read as one
+// contiguous block. Tile: 64 rows x 64 columns per CTA: the packed rows are
+// read as aligned 32-bit words (24 per 64-sample segment, all segments of a
+// tile at one bit offset), a thread converts 8 samples of two rows into FP16
+// pairs, and the tile is written out column by column.
+__global__ void __launch_bounds__(256) k_unpack_cols(const UnpackColsParams p) {
+    __shared__ uint32_t raw[64][25];     // words 0 .. 23 of each row segment (the last ones only feed shifts)
+    __shared__ uint32_t tile[64][33];    // [column][row pair] FP16 pairs
+    const int col0 = blockIdx.x * 64, r0 = blockIdx.y * 64, st = blockIdx.z;
+    const int tid = threadIdx.x;
+    const long long c0 = p.ctab[(long long)st * p.M];
+    // relative sample (from the first history sample) of row 0, column col0;
+    // history and chunk are one bit stream (10 H is a multiple of 32)
+    const long long rel00 = (p.rb + r0) * (long long)p.P + col0 - c0 - (p.t_in - p.H);
+    const long long bit00 = 10 * rel00;
+    const int off = (int)(bit00 & 31);   // the same for every row (10 P is a multiple of 32)
+    {
+        // thread: row tid / 4, words 6 part .. 6 part + 5 of the row segment
+        const int row = tid >> 2, part = tid & 3;
+        const uint32_t *hw = reinterpret_cast<const uint32_t *>(p.hist + (long long)st * p.hist_bytes);
+        const uint32_t *cw = reinterpret_cast<const uint32_t *>(p.chunk + (long long)st * p.chunk_bytes);
+        const long long hwords = 10 * p.H / 32, cwords = p.chunk_bytes / 4;
+        const long long w0 = ((bit00 + (long long)row * 10 * p.P) >> 5) + 6 * part;
+        const bool live = r0 + row < p.RT;
+        uint32_t v[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            const long long w = w0 + i;
+            v[i] = 0u;
+            if (live && w >= 0) {
+                if (w < hwords) v[i] = __ldg(hw + w);
+                else if (w - hwords < cwords) v[i] = __ldg(cw + (w - hwords));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; i++) raw[row][6 * part + i] = __byte_perm(v[i], 0u, 0x0123u);   // big-endian bits
+    }
+    __syncthreads();
+    {
+        // thread: rows 2 rp, 2 rp + 1, samples 8 g .. 8 g + 7 (bits off + 80 g .. + 80)
+        const int rp = tid >> 3, g = tid & 7;
+        const int b0 = off + 80 * g, w0 = b0 >> 5, sh = b0 & 31;
+        uint32_t f[2][8];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int row = 2 * rp + h;
+            uint32_t a[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = __funnelshift_l(raw[row][w0 + i + 1], raw[row][w0 + i], (unsigned)sh);
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int bb = 10 * k;
+                f[h][k] = __funnelshift_l(a[(bb >> 5) + 1], a[bb >> 5], (unsigned)(bb & 31)) >> 22;
+            }
+            // samples before the first history sample, or rows past the data, are zero
+            const long long rel = rel00 + (long long)row * p.P + 8 * g;
+            if (r0 + row >= p.RT || rel + 7 < 0) {
+#pragma unroll
+                for (int k = 0; k < 8; k++) f[h][k] = 0u;
+            } else if (rel < 0) {
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    if (rel + k < 0) f[h][k] = 0u;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) tile[8 * g + k][rp] = fields_to_half2(f[0][k], f[1][k]);
+    }
+    __syncthreads();
+    {
+        // column c: row pairs 0 .. 31 (128 contiguous bytes), 4 threads of 32 bytes
+        const int c = tid >> 2, part = tid & 3;
+        uint4 *dst = reinterpret_cast<uint4 *>(p.cols + ((long long)st * p.P + col0 + c) * p.RTP + r0 + 16 * part);
+        const uint32_t *t = &tile[c][8 * part];
+        dst[0] = make_uint4(t[0], t[1], t[2], t[3]);
+        dst[1] = make_uint4(t[4], t[5], t[6], t[7]);
+    }
+}
+
+// The same for P < 64 (n_channels < 256): one thread per output sample,
+// read as two bytes of the packed stream.
+__global__ void k_unpack_cols_small(const UnpackColsParams p) {
+    const long long total = (long long)p.n_streams * p.P * p.RTP;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % p.RTP);
+        const long long sc = e / p.RTP;
+        const int col = (int)(sc % p.P), st = (int)(sc / p.P);
+        const long long rel = (p.rb + r) * (long long)p.P + col - p.ctab[(long long)st * p.M] - (p.t_in - p.H);
+        uint16_t v = 0;
+        if (r < p.RT && rel >= 0 && rel < p.H + p.L) {
+            const bool h = rel < p.H;
+            const long long u = h ? rel : rel - p.H;
+            const uint8_t *b = (h ? p.hist + (long long)st * p.hist_bytes : p.chunk + (long long)st * p.chunk_bytes) +
+                               ((5 * u) >> 2);
+            const unsigned w = ((unsigned)__ldg(b) << 8) | (unsigned)__ldg(b + 1);
+            v = field_to_half((w >> (6u - 2u * (unsigned)(u & 3))) & 0x3FFu);
+        }
+        p.cols[e] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The tensor-core kernel, warp-specialised:
+//   warps 0-3  epilogue: tensor memory -> scale -> second-stage input in HBM
+//   warps 4-7  fill: the pass's 8 column sequences from cols into the ring of
+//              shared-memory data buffers (BF16: hi and lo planes)
+//   warp 8     MMA: the tcgen05 chain of a pass into one of two tensor-memory
+//              buffers, committed to the barriers that free its data buffer
+//              and hand the accumulator to the epilogue
+// Each role walks the same pass sequence; they synchronise only through
+// mbarriers (xfull / xempty per data buffer, tfull / tempty per tensor-memory
+// buffer), every wait bounded.
 template <int R, int T, int PREC>
 __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParams p) {
     constexpr int KS = tc_ks(R, T, PREC), KPS = tc_kps(R, KS);   // k1-slices, k1 values per slice
@@ -200,19 +378,20 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
     constexpr int BBLK = NM * K;              // 16-bit elements per operand block
     constexpr int TMC = CW * NM;              // tensor-memory columns per pass buffer
     constexpr int NG = (2 * KPS + 7) / 8;     // 8-column groups holding (Re, Im) of the slice's k1
-    constexpr int NXB = tc_nxb(R, T, PREC);   // decode buffers
+    constexpr int NXB = tc_nxb(R, T, PREC);   // data buffers
     static_assert(KS > 0, "shape does not fit in shared memory");
     static_assert(2 * TMC <= kTcTmemCols, "tensor memory");
     extern __shared__ __align__(1024) uint8_t smem[];
     uint16_t *bsm = reinterpret_cast<uint16_t *>(smem);            // [NPB][kTcPhys][BBLK]
     uint16_t *xsm = bsm + NPB * kTcPhys * BBLK;                    // [NXB][NPL][kTcPhys][XL]
-    int *c_sm = reinterpret_cast<int *>(xsm + NXB * NPL * kTcPhys * XL);
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(c_sm + kTcRows);   // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
-    int *flag_sm = reinterpret_cast<int *>(tmem_slot + 1);         // [0] abort
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(xsm + NXB * NPL * kTcPhys * XL);
+    unsigned long long *xfull = bar, *xempty = bar + 2, *tfull = bar + 4, *tempty = bar + 6;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 8);
+    volatile int *abort_sm = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    long long *fsrc = reinterpret_cast<long long *>(bar + 9);          // [NXB][kTcPhys] column source offsets
+    int *fsh = reinterpret_cast<int *>(fsrc + 2 * kTcPhys);            // [NXB][kTcPhys] row0 mod 8
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_cg = p.N2 / CW;
     // block = (column group, k1-slice, item range)
     const int cg = blockIdx.x / (p.splits * KS), slice = (blockIdx.x / p.splits) % KS, split = blockIdx.x % p.splits;
     const int k1_lo = slice * KPS, k1_hi = min(H1 + 1, k1_lo + KPS);
@@ -220,7 +399,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
     const int n_items = p.n_streams * n_tiles;
     const int it_begin = (int)((long long)n_items * split / p.splits);
     const int it_end = (int)((long long)n_items * (split + 1) / p.splits);
-    if (cg >= n_cg) return;
+    const int P = p.N / 8, N2 = p.N2;
 
     // the CTA's operand blocks (weights x DFT x twiddle), resident for all its items
     {
@@ -229,234 +408,240 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
         uint4 *dst = reinterpret_cast<uint4 *>(bsm);
         for (int i = tid; i < NPB * kTcPhys * BBLK / 8; i += kTcThreads) dst[i] = __ldg(src + i);
     }
-    float osc[CW];
-#pragma unroll
-    for (int c = 0; c < CW; c++) osc[c] = __ldg(p.oscale + cg * CW + c);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])));
+        for (int i = 0; i < 2; i++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&xfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&xempty[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&tempty[i])), "r"(128));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        flag_sm[0] = 0;
+        *abort_sm = 0;
     }
-    if (warp == 0) {
+    if (warp == 8) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                      "r"(kTcTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the operand blocks, for the tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const long long H = p.H, HL = p.H + p.L;
-    const int P = p.N / 8, N2 = p.N2;
-    constexpr uint32_t idesc = mma_idesc(kTcRows, NM, PREC == 2 ? 1 : 0);
-
-    // ---- pass generation (every thread computes the same sequence) ----
-    int it = it_begin, ra = -1, rows = 0, st = 0, q0 = 0, uniform = 0;
-    // coarse delay of row tid of an item, loaded one item ahead
-    auto item_delay = [&](int item) -> int {
-        const int s2 = item / n_tiles, qq = p.q_begin + (item % n_tiles) * kTcRows;
-        return (item < it_end && qq + tid < p.q_begin + p.q_count && tid < kTcRows)
-                   ? __ldg(p.ctab + (long long)s2 * p.M + qq + tid)
-                   : 0;
-    };
-    int c_pref = item_delay(it);
-    auto next_pass = [&](Pass &ps) -> bool {
-        for (;;) {
-            if (ra < 0) {
-                if (it >= it_end) return false;
-                st = it / n_tiles;
-                q0 = p.q_begin + (it % n_tiles) * kTcRows;
-                rows = min(kTcRows, p.q_begin + p.q_count - q0);
-                const int c_this = c_pref;
-                c_pref = item_delay(it + 1);
-                __syncthreads();   // the previous item's delays are no longer read
-                if (tid < rows) c_sm[tid] = c_this;
-                __syncthreads();
-                uniform = __syncthreads_and(tid >= rows || c_sm[tid] == c_sm[0]);
-                ra = 0;
+    // a bounded wait that also gives up once another role has
+    auto wait_bar = [&](unsigned long long *b, uint32_t parity) -> bool {
+        const uint32_t a = smem_addr(b);
+        const long long t0 = clock64();
+        while (!mbar_try(a, parity)) {
+            if (*abort_sm) return false;
+            if (clock64() - t0 > 2000000000LL) {
+                *abort_sm = 1;
+                atomicExch(p.err, 2);
+                return false;
             }
-            if (ra >= rows) {
-                ra = -1;
-                it++;
+        }
+        return true;
+    };
+    auto arrive = [&](unsigned long long *b) {
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(b))
+                     : "memory");
+    };
+    // index in the pre-delayed columns (timestamp + c0) of row v = 0 of physical
+    // column i (run j = i / CW, column c = i % CW)
+    auto col_start = [&](const Pass &ps, int i) -> long long {
+        return (long long)p.N * (p.m0 + ps.q0) - ps.c + ps.c0 + (long long)cg * CW + (i % CW) + (long long)N2 * (i / CW);
+    };
+
+    PassIter iter{};
+    iter.it = it_begin;
+    iter.it_end = it_end;
+    iter.ra = -1;
+    pass_prefetch(iter, p, n_tiles, it_begin);
+    Pass ps;
+    if (warp >= 4 && warp < 8) {
+        // ---------------- fill ----------------
+        // A column's sequence starts at element row0 of its FP16 column;
+        // it is copied in 16-byte chunks from the aligned element
+        // row0 - sh (sh = row0 mod 8), each output chunk taking 16 bytes at
+        // byte offset 2 sh of two consecutive source chunks.
+        const int ft = tid - 128;
+        constexpr int CPC = XL / 8;                 // 16-byte chunks per column sequence
+        for (int pc = 0; warp_next_pass(iter, ps, p, n_tiles); pc++) {
+            const int s = pc % NXB, use = pc / NXB;
+            // the decision to go on is the same in every fill thread (a thread
+            // must not leave while the others wait at the named barrier)
+            int ok = use == 0 || ft != 0 || wait_bar(&xempty[s], (use - 1) & 1);
+            asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\tbar.red.and.pred q, 1, 128, q;\n\t"
+                         "selp.s32 %0, 1, 0, q;\n\t}\n"
+                         : "=r"(ok)
+                         : "r"(ok)
+                         : "memory");
+            if (!ok) break;
+            uint16_t *xb = xsm + (size_t)s * NPL * kTcPhys * XL;
+            if (PREC == 1 && !p.window_tap && ps.c == ps.c0) {
+                // the pass's delay is the columns' c0: every column sequence starts at
+                // row 8 (m0 + q0) - rb, 16-byte aligned, one bulk copy each
+                if (ft == 0) {
+                    constexpr uint32_t bytes = (uint32_t)(kTcPhys * XL * 2);
+                    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                                 ::"r"(smem_addr(&xfull[s])), "r"(bytes) : "memory");
+                    const long long row0 = 8LL * (p.m0 + ps.q0) - p.rb;
+#pragma unroll 1
+                    for (int i = 0; i < kTcPhys; i++) {
+                        const long long t = (long long)cg * CW + (i % CW) + (long long)N2 * (i / CW);
+                        const uint16_t *src = p.cols + ((long long)ps.st * P + t) * p.RTP + row0;
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                            ::"r"(smem_addr(xb + (size_t)i * XL)), "l"(src), "r"((uint32_t)(XL * 2)),
+                            "r"(smem_addr(&xfull[s]))
+                            : "memory");
+                    }
+                }
                 continue;
             }
-            const int c = c_sm[ra];
-            int rb = ra + 1;
-            if (ra == 0 && uniform) {
-                rb = rows;
-            } else {
-                while (rb < rows && c_sm[rb] == c) rb++;
+            if (ft < kTcPhys) {
+                const long long a0 = col_start(ps, ft);
+                const long long ra = floor_div(a0, P);
+                const long long col = a0 - ra * P, row0 = ra - p.rb;
+                fsrc[s * kTcPhys + ft] = ((long long)ps.st * P + col) * p.RTP + (row0 & ~7LL);
+                fsh[s * kTcPhys + ft] = (int)(row0 & 7);
             }
-            ps = Pass{st, q0, ra, rb, c};
-            ra = rb;
-            return true;
-        }
-    };
-
-    // ---- decode of one pass into data buffer b ----
-    // Fast path (the pass's samples all inside the chunk): a thread takes
-    // (run j, rows v and v + 1) items, a run being CW consecutive columns of
-    // one row; its packed words are loaded into registers by fetch() one
-    // step ahead (under the previous pass's epilogue), and decode() converts
-    // them into 16-bit samples in shared memory.
-    constexpr int NIT = R * (XL / 2);                              // items per pass
-    constexpr int MAXI = (NIT + kTcThreads - 1) / kTcThreads;      // items per thread
-    constexpr int NW = (30 + 10 * CW) / 32 + 1;                    // words covering a run at any bit offset
-    constexpr int PFI = MAXI * 2 * NW <= 40 ? MAXI : 40 / (2 * NW);   // items prefetched into registers
-    uint32_t rw[PFI][2][NW];
-    // position (from the first history sample) of row v = 0 at column t = 0
-    auto pass_base = [&](const Pass &ps) -> long long {
-        return (long long)p.N * (p.m0 + ps.q0) - (p.t_in - H) - ps.c;
-    };
-    auto is_fast = [&](const Pass &ps) -> bool {
-        const long long base = pass_base(ps);
-        const long long lo = base + cg * CW, hi = base + cg * CW + (long long)N2 * (R - 1) + CW +
-                                                  (long long)P * (XL - 1);
-        return lo >= H && hi < HL - 16 && !p.window_tap;
-    };
-    // bit position (from the chunk start) of the first bit of item e's row rr
-    auto item_bit = [&](long long base, int e, int rr) -> long long {
-        const int j = e / (XL / 2), v = 2 * (e - j * (XL / 2));
-        return 10 * (base - H + cg * CW + (long long)N2 * j + (long long)P * (v + rr));
-    };
-    auto fetch = [&](const Pass &ps, bool fast) {
-        if (!fast) return;
-        const uint32_t *w32 = reinterpret_cast<const uint32_t *>(p.chunk + (long long)ps.st * p.chunk_bytes);
-        const long long base = pass_base(ps);
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            for (int e0 = ft; e0 < kTcPhys * CPC; e0 += 128 * 3) {
+                uint4 a[3], b[3];
 #pragma unroll
-        for (int i = 0; i < PFI; i++) {
-            const int e = tid + i * kTcThreads;
-            if (e < NIT) {
-#pragma unroll
-                for (int rr = 0; rr < 2; rr++) {
-                    const uint32_t *wp = w32 + (item_bit(base, e, rr) >> 5);
-#pragma unroll
-                    for (int k = 0; k < NW; k++) rw[i][rr][k] = __ldg(wp + k);
-                }
-            }
-        }
-    };
-    auto decode = [&](const Pass &ps, int b, bool fast) {
-        uint16_t *xb = xsm + (size_t)(b % NXB) * NPL * kTcPhys * XL;
-        const long long base = pass_base(ps);
-        if (fast) {
-            const uint32_t *w32 = reinterpret_cast<const uint32_t *>(p.chunk + (long long)ps.st * p.chunk_bytes);
-#pragma unroll
-            for (int i = 0; i < MAXI; i++) {
-                const int e = tid + i * kTcThreads;
-                if (e >= NIT) break;
-                const int j = e / (XL / 2), v = 2 * (e - j * (XL / 2));
-                uint32_t f[2][CW];
-#pragma unroll
-                for (int rr = 0; rr < 2; rr++) {
-                    const long long bit = item_bit(base, e, rr);
-                    const int off = (int)(bit & 31);
-                    // big-endian words, then shifted so that bit 0 is the run's first bit:
-                    // field c sits at the compile-time bit 10 c
-                    uint32_t w[NW + 1], a[NW];
-#pragma unroll
-                    for (int k = 0; k < NW; k++) {
-                        const uint32_t raw = i < PFI ? rw[i < PFI ? i : 0][rr][k] : __ldg(w32 + (bit >> 5) + k);
-                        w[k] = __byte_perm(raw, 0u, 0x0123u);
-                    }
-                    w[NW] = 0u;
-#pragma unroll
-                    for (int k = 0; k < NW; k++) a[k] = __funnelshift_l(w[k + 1], w[k], (unsigned)off);
-#pragma unroll
-                    for (int c = 0; c < CW; c++) {
-                        const int bb = 10 * c;
-                        const uint32_t hi = a[bb >> 5], lo = (bb >> 5) + 1 < NW ? a[(bb >> 5) + 1] : 0u;
-                        f[rr][c] = __funnelshift_l(lo, hi, (unsigned)(bb & 31)) >> 22;
+                for (int u = 0; u < 3; u++) {
+                    const int e = e0 + 128 * u;
+                    if (e < kTcPhys * CPC) {
+                        const int i = e / CPC, j = e - i * CPC;
+                        const uint4 *src = reinterpret_cast<const uint4 *>(p.cols + fsrc[s * kTcPhys + i]) + j;
+                        a[u] = __ldg(src);
+                        b[u] = __ldg(src + 1);
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < CW; c++) {
-                    const int i2 = j * CW + c;
+                for (int u = 0; u < 3; u++) {
+                    const int e = e0 + 128 * u;
+                    if (e < kTcPhys * CPC) {
+                        const int i = e / CPC, j = e - i * CPC;
+                        const int sh = fsh[s * kTcPhys + i];
+                        const uint32_t w[8] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
+                        uint32_t o[4];
+                        const uint32_t sel = (sh & 1) ? 0x5432u : 0x3210u;   // 2-byte shift for odd sh
+                        switch (sh >> 1) {
+                            case 0:
+#pragma unroll
+                                for (int m = 0; m < 4; m++) o[m] = __byte_perm(w[m], w[m + 1], sel);
+                                break;
+                            case 1:
+#pragma unroll
+                                for (int m = 0; m < 4; m++) o[m] = __byte_perm(w[m + 1], w[m + 2], sel);
+                                break;
+                            case 2:
+#pragma unroll
+                                for (int m = 0; m < 4; m++) o[m] = __byte_perm(w[m + 2], w[m + 3], sel);
+                                break;
+                            default:
+#pragma unroll
+                                for (int m = 0; m < 4; m++) o[m] = __byte_perm(w[m + 3], w[m + 4], sel);
+                                break;
+                        }
+                        if constexpr (PREC == 2) {
+                            uint32_t h[4], l[4];
+#pragma unroll
+                            for (int m = 0; m < 4; m++) half2_to_bf16x2(o[m], h[m], l[m]);
+                            reinterpret_cast<uint4 *>(xb + (size_t)i * XL)[j] = make_uint4(h[0], h[1], h[2], h[3]);
+                            reinterpret_cast<uint4 *>(xb + (size_t)(kTcPhys + i) * XL)[j] =
+                                make_uint4(l[0], l[1], l[2], l[3]);
+                        } else {
+                            reinterpret_cast<uint4 *>(xb + (size_t)i * XL)[j] = make_uint4(o[0], o[1], o[2], o[3]);
+                        }
+                    }
+                }
+            }
+            if (p.window_tap) {
+                // debug tap: the first FIR tap of spectrum q0 + v / 8 at offset P (v % 8) + t
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                const uint16_t *xv = xsm + (size_t)s * NPL * kTcPhys * XL;
+                for (int e = ft; e < kTcPhys * 8 * kTcRows; e += 128) {
+                    const int i = e / (8 * kTcRows), vv = e - i * (8 * kTcRows), mrow = vv >> 3;
+                    if (mrow < ps.ra || mrow >= ps.rb) continue;
+                    float x;
                     if constexpr (PREC == 2) {
-                        uint32_t h, l;
-                        ints_to_bf16x2(field_value(f[0][c]), field_value(f[1][c]), h, l);
-                        *reinterpret_cast<uint32_t *>(xb + (size_t)i2 * XL + v) = h;
-                        *reinterpret_cast<uint32_t *>(xb + (size_t)(kTcPhys + i2) * XL + v) = l;
+                        x = __bfloat162float(__ushort_as_bfloat16(xv[(size_t)i * XL + vv])) +
+                            __bfloat162float(__ushort_as_bfloat16(xv[(size_t)(kTcPhys + i) * XL + vv]));
                     } else {
-                        *reinterpret_cast<uint32_t *>(xb + (size_t)i2 * XL + v) = fields_to_half2(f[0][c], f[1][c]);
+                        x = __half2float(__ushort_as_half(xv[(size_t)i * XL + vv]));
                     }
+                    const long long t = (long long)cg * CW + (i % CW) + (long long)N2 * (i / CW);
+                    p.window_tap[((long long)ps.st * p.M + ps.q0 + mrow) * p.N + (long long)P * (vv & 7) + t] = (int)x;
                 }
             }
-        } else {
-            // general: every sample checked against history / chunk / range;
-            // the debug window tap (first FIR tap of each spectrum) is written here
-            const uint8_t *hist = p.hist + (long long)ps.st * p.hist_bytes;
-            const uint8_t *chunk = p.chunk + (long long)ps.st * p.chunk_bytes;
-            for (int e = tid; e < kTcPhys * (XL / 2); e += kTcThreads) {
-                const int i = e / (XL / 2), v = 2 * (e - i * (XL / 2));
-                const int j = i / CW, c = i - j * CW;
-                const long long t = (long long)cg * CW + c + (long long)N2 * j;
-                uint32_t f[2];
-#pragma unroll
-                for (int rr = 0; rr < 2; rr++) {
-                    f[rr] = field_at(hist, chunk, base + t + (long long)P * (v + rr), H, HL);
-                    const int vv = v + rr;
-                    if (p.window_tap && vv < 8 * kTcRows) {
-                        const int mrow = vv >> 3, t1 = vv & 7;
-                        if (mrow >= ps.ra && mrow < ps.rb)
-                            p.window_tap[((long long)ps.st * p.M + ps.q0 + mrow) * p.N + (long long)P * t1 + t] =
-                                field_value(f[rr]);
-                    }
-                }
-                if constexpr (PREC == 2) {
-                    uint32_t h, l;
-                    ints_to_bf16x2(field_value(f[0]), field_value(f[1]), h, l);
-                    *reinterpret_cast<uint32_t *>(xb + (size_t)i * XL + v) = h;
-                    *reinterpret_cast<uint32_t *>(xb + (size_t)(kTcPhys + i) * XL + v) = l;
-                } else {
-                    *reinterpret_cast<uint32_t *>(xb + (size_t)i * XL + v) = fields_to_half2(f[0], f[1]);
-                }
-            }
+            // every fill thread's writes, then one arrival
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (ft == 0) arrive(&xfull[s]);
         }
-    };
-
-    // ---- MMAs of one pass (one thread) ----
-    auto issue = [&](int b) {
-        const uint32_t d0 = tmem + (uint32_t)(b * TMC);
-        const uint32_t xa0 = smem_addr(xsm + (size_t)(b % NXB) * NPL * kTcPhys * XL), ba0 = smem_addr(bsm);
+    } else if (warp == 8) {
+        // ---------------- MMA ----------------
+        constexpr uint32_t idesc = mma_idesc(kTcRows, NM, PREC == 2 ? 1 : 0);
+        for (int pc = 0; warp_next_pass(iter, ps, p, n_tiles); pc++) {
+            const int s = pc % NXB, b = pc & 1;
+            bool ok = true;
+            if (lane == 0) {
+                ok = wait_bar(&xfull[s], (pc / NXB) & 1);
+                ok = ok && (pc < 2 || wait_bar(&tempty[b], ((pc >> 1) - 1) & 1));
+            }
+            if (!__shfl_sync(0xFFFFFFFFu, (int)ok, 0)) break;   // the same decision in every lane
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t d0 = tmem + (uint32_t)(b * TMC);
+                const uint32_t xa0 = smem_addr(xsm + (size_t)s * NPL * kTcPhys * XL), ba0 = smem_addr(bsm);
 #pragma unroll 1
-        for (int c = 0; c < CW; c++) {
+                for (int c = 0; c < CW; c++) {
 #pragma unroll 1
-            for (int j = 0; j < R; j++) {
-                const int i = j * CW + c;
-                // FP16: x B. BF16: x_hi B_hi + x_lo B_hi + x_hi B_lo (x_lo B_lo is
-                // below 2^-9 / 512 of the result and left out)
+                    for (int j = 0; j < R; j++) {
+                        const int i = j * CW + c;
+                        // FP16: x B. BF16: x_hi B_hi + x_lo B_hi + x_hi B_lo (x_lo B_lo
+                        // is below 2^-9 / 512 of the result and left out)
 #pragma unroll
-                for (int pp = 0; pp < (PREC == 2 ? 3 : 1); pp++) {
-                    const int pl = pp == 1 ? 1 : 0, pb = pp == 2 ? 1 : 0;
-                    const uint32_t xa = xa0 + (uint32_t)((pl * kTcPhys + i) * XL * 2);
-                    const uint32_t ba = ba0 + (uint32_t)((pb * kTcPhys + i) * BBLK * 2);
+                        for (int pp = 0; pp < (PREC == 2 ? 3 : 1); pp++) {
+                            const int pl = pp == 1 ? 1 : 0, pb = pp == 2 ? 1 : 0;
+                            const uint32_t xa = xa0 + (uint32_t)((pl * kTcPhys + i) * XL * 2);
+                            const uint32_t ba = ba0 + (uint32_t)((pb * kTcPhys + i) * BBLK * 2);
 #pragma unroll
-                    for (int kk = 0; kk < K / 16; kk++) {
-                        const uint64_t ad = mat_desc(xa + 32u * kk, 16u, 128u);
-                        const uint64_t bd = mat_desc(ba + (uint32_t)kk * 2u * (NM / 8) * 128u, (NM / 8) * 128u, 128u);
-                        mma_f16_ss(d0 + (uint32_t)(c * NM), ad, bd, idesc, (j | pp | kk) ? 1u : 0u);
+                            for (int kk = 0; kk < K / 16; kk++) {
+                                const uint64_t ad = mat_desc(xa + 32u * kk, 16u, 128u);
+                                const uint64_t bd =
+                                    mat_desc(ba + (uint32_t)kk * 2u * (NM / 8) * 128u, (NM / 8) * 128u, 128u);
+                                mma_f16_ss(d0 + (uint32_t)(c * NM), ad, bd, idesc, (j | pp | kk) ? 1u : 0u);
+                            }
+                        }
                     }
                 }
+                mma_commit(smem_addr(&xempty[s]));   // the data buffer is read
+                mma_commit(smem_addr(&tfull[b]));    // the accumulator is complete
             }
+            __syncwarp();
         }
-        mma_commit(smem_addr(&mbar[b]));
-    };
-
-    // ---- epilogue of one pass from tensor-memory buffer b ----
-    auto epilogue = [&](const Pass &ps, int b) {
-        const int wg = warp >> 2, row = 32 * (warp & 3) + lane;
-        const bool valid = row >= ps.ra && row < ps.rb;
-        const uint32_t trow = tmem + (uint32_t)(b * TMC) + ((uint32_t)(32 * (warp & 3)) << 16);
-        const long long q_rel = ps.q0 + row - p.q_begin;
-        for (int g = wg; g < NG; g += 2) {
-            float v[CW][8];
+    } else {
+        // ---------------- epilogue ----------------
+        const int row = 32 * warp + lane;   // this thread's tensor-memory lane = spectrum row
+        float osc[CW];
 #pragma unroll
-            for (int c = 0; c < CW; c++) tmem_ld8(trow + (uint32_t)(c * NM + 8 * g), v[c]);
-            tmem_ld_wait();
-            if (valid) {
+        for (int c = 0; c < CW; c++) osc[c] = __ldg(p.oscale + cg * CW + c);
+        for (int pc = 0; warp_next_pass(iter, ps, p, n_tiles); pc++) {
+            const int b = pc & 1;
+            const bool got = lane == 0 ? wait_bar(&tfull[b], (pc >> 1) & 1) : true;
+            if (!__shfl_sync(0xFFFFFFFFu, (int)got, 0)) break;
+            tc_fence_after();
+            const bool valid = row >= ps.ra && row < ps.rb;
+            const uint32_t trow = tmem + (uint32_t)(b * TMC) + ((uint32_t)(32 * warp) << 16);
+            const long long q_rel = ps.q0 + row - p.q_begin;
+            // store the (Re, Im) pairs of k1 = k1_lo + 4 g + kq of this row and the CW columns
+            auto store_group = [&](int g, const float (&v)[CW][8]) {
+                if (!valid) return;
 #pragma unroll
                 for (int kq = 0; kq < 4; kq++) {
                     const int k1 = k1_lo + 4 * g + kq;
@@ -487,81 +672,47 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
                         }
                     }
                 }
-            }
-        }
-        tc_fence_before();
-    };
-
-    // ---- the pipeline ----
-    Pass cur{}, prev{}, nxt{};
-    bool have_prev = false;
-    int b = 0;
-    uint32_t parity = 0u;   // bit k: next phase parity of mbar[k]
-    bool aborted = false;
-    bool have_cur = next_pass(cur);
-    bool fast_cur = have_cur && is_fast(cur);
-    if (have_cur) fetch(cur, fast_cur);
-    while (have_cur) {
-        if (NXB == 1 && have_prev) {
-            // one decode buffer: the previous pass's MMAs must have read it
-            // (the epilogue's wait below returns at once for this phase)
-            if (!mbar_wait(smem_addr(&mbar[b ^ 1]), (parity >> (b ^ 1)) & 1u)) {
-                flag_sm[0] = 1;
-                atomicExch(p.err, 2);
-            }
-        }
-        decode(cur, b, fast_cur);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (flag_sm[0]) {
-            aborted = true;
-            break;
-        }
-        if (tid == 0) issue(b);
-        __syncwarp();
-        // the next pass's packed words are in flight during this epilogue
-        const bool have_nxt = next_pass(nxt);
-        const bool fast_nxt = have_nxt && is_fast(nxt);
-        if (have_nxt) fetch(nxt, fast_nxt);
-        if (have_prev) {
-            const int pb = b ^ 1;
-            const bool ok = mbar_wait(smem_addr(&mbar[pb]), (parity >> pb) & 1u);
-            parity ^= 1u << pb;
-            if (!ok) {
-                flag_sm[0] = 1;
-                atomicExch(p.err, 2);
+            };
+            if constexpr (NG * CW <= 16) {
+                // all of the pass's accumulator columns in registers, one wait,
+                // tensor memory released before the stores
+                float vall[NG][CW][8];
+#pragma unroll
+                for (int g = 0; g < NG; g++)
+#pragma unroll
+                    for (int c = 0; c < CW; c++) tmem_ld8(trow + (uint32_t)(c * NM + 8 * g), vall[g][c]);
+                tmem_ld_wait();
+                tc_fence_before();
+                arrive(&tempty[b]);   // tensor memory free for the pass after next
+#pragma unroll
+                for (int g = 0; g < NG; g++) store_group(g, vall[g]);
             } else {
-                tc_fence_after();
-                epilogue(prev, pb);
+#pragma unroll 1
+                for (int g = 0; g < NG; g++) {
+                    float v[CW][8];
+#pragma unroll
+                    for (int c = 0; c < CW; c++) tmem_ld8(trow + (uint32_t)(c * NM + 8 * g), v[c]);
+                    tmem_ld_wait();
+                    if (g == NG - 1) {
+                        tc_fence_before();
+                        arrive(&tempty[b]);
+                    }
+                    store_group(g, v);
+                }
             }
         }
-        prev = cur;
-        have_prev = true;
-        b ^= 1;
-        cur = nxt;
-        have_cur = have_nxt;
-        fast_cur = fast_nxt;
     }
-    if (have_prev && !aborted) {
-        const int pb = b ^ 1;
-        const bool ok = mbar_wait(smem_addr(&mbar[pb]), (parity >> pb) & 1u);
-        if (!ok) {
-            atomicExch(p.err, 2);
-        } else {
-            tc_fence_after();
-            epilogue(prev, pb);
+    // teardown: every role has left its loop; the last accumulator was read
+    // (or a wait gave up: give the tensor core a bounded moment to finish)
+    if (*abort_sm && warp == 8) {
+        const long long t0 = clock64();
+        while (clock64() - t0 < 20000000LL) {
         }
-    } else if (have_prev && aborted) {
-        // a wait gave up: wait (bounded) for the last committed pass before
-        // releasing tensor memory
-        mbar_wait(smem_addr(&mbar[b ^ 1]), (parity >> (b ^ 1)) & 1u);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
+    if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
 }
 
 // ---------------------------------------------------------------- host side
@@ -688,6 +839,19 @@ static cudaError_t launch_tc_r(int R, int T, const Phase1TcParams &p, cudaStream
         case 8: return launch_tc_t<8, PREC>(T, p, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_unpack_cols(const UnpackColsParams &p, cudaStream_t s) {
+    if (p.RTP % 64) return cudaErrorInvalidValue;
+    if (p.P % 64) {
+        const long long total = (long long)p.n_streams * p.P * p.RTP;
+        const long long blocks = (total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192;
+        k_unpack_cols_small<<<(unsigned)blocks, 256, 0, s>>>(p);
+    } else {
+        dim3 grid(p.P / 64, p.RTP / 64, p.n_streams);
+        k_unpack_cols<<<grid, 256, 0, s>>>(p);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_phase1_tc(int T, int precision, const Phase1TcParams &p, cudaStream_t s) {
