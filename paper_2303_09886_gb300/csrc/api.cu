@@ -68,7 +68,7 @@ struct fengine_plan_s {
     int cols_rtp = 0;
     float tc_unscale = 1.0f;        // inverse of the FP16 intermediate's scale
     bool tc1 = false;               // phase 1 on tensor cores
-    int tc_splits = 1;              // tensor-core phase-1 item ranges per column group (per slab)
+    int tc_splits = 1;              // SMs of the device (the tensor-core phase 1 runs one wave)
     uint8_t *d_hist[2] = {nullptr, nullptr};
     int cur = 0;
     DelaySeg *d_seg = nullptr;
@@ -213,7 +213,8 @@ const char *fengine_strerror(fengine_status st) {
         case FENGINE_EBUSY: return "busy: no slot or over budget";
         case FENGINE_ETIMEOUT: return "device wait timed out";
         case FENGINE_EUNSUPPORTED: return "unsupported in this build";
-        case FENGINE_EDELAY: return "coarse delay outside [0, max_delay_samples]";
+        case FENGINE_EDELAY: return "coarse delay outside [min_delay_samples, max_delay_samples]";
+        case FENGINE_EIO: return "host file could not be written";
     }
     return "unknown status";
 }
@@ -420,14 +421,9 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        // column groups x item ranges: one wave of two CTAs per SM (the
-        // CTAs keep their operand blocks for all their items; a second wave
-        // would reload them and leave SMs idle at its end)
-        const int R = fe::phase1_tc_R((int)N), n_cg = pl->N2 / (8 / R);
-        const long long items = (long long)pl->n_streams * ((pl->SL + 127) / 128);
-        long long sp = (long long)2 * (sms > 0 ? sms : 148) / n_cg;
-        if (sp > items) sp = items;
-        pl->tc_splits = (int)(sp < 1 ? 1 : sp);
+        // one wave of two CTAs per SM, each a contiguous, equal share of the
+        // (column group, k1-slice, item) passes
+        pl->tc_splits = sms > 0 ? sms : 148;
     }
     // twiddles, evaluated in FP64 with exact integer phase reduction
     std::vector<float2> tw1((size_t)(pl->N1 / 2 + 1) * pl->N2), tw2(pl->N2);
@@ -737,7 +733,9 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
         up.RTP = pl->cols_rtp;
         up.cols = pl->d_cols;
         up.n_streams = pl->n_streams;
+        prof_begin(pl, 4, st);
         if ((e = fe::launch_unpack_cols(up, st)) != cudaSuccess) return cuda_fail(e, "unpack launch");
+        prof_end(pl, st);
         pt.cols = pl->d_cols;
         pt.rb = up.rb;
         pt.RTP = pl->cols_rtp;
@@ -834,7 +832,7 @@ fengine_status fengine_set_profiling(fengine_plan_t pl, int32_t enable) {
 
 fengine_status fengine_stage_times(fengine_plan_t pl, float *ms, int32_t *calls) {
     if (!pl || !ms || !calls) return fail(FENGINE_EINVAL, "null argument");
-    for (int i = 0; i < 4; i++) ms[i] = 0.0f;
+    for (int i = 0; i < 5; i++) ms[i] = 0.0f;
     const size_t n_rec = pl->prof_used / 2;
     for (size_t r = 0; r < n_rec; r++) {
         cudaEvent_t a = pl->prof_events[2 * r], b = pl->prof_events[2 * r + 1];
@@ -843,7 +841,7 @@ fengine_status fengine_stage_times(fengine_plan_t pl, float *ms, int32_t *calls)
         float t = 0.0f;
         if ((e = cudaEventElapsedTime(&t, a, b)) != cudaSuccess) return cuda_fail(e, "stage timing");
         const int stage = r < pl->prof_stage.size() ? pl->prof_stage[r] : 0;
-        if (stage >= 0 && stage < 4) ms[stage] += t;
+        if (stage >= 0 && stage < 5) ms[stage] += t;
     }
     *calls = pl->prof_calls;
     pl->prof_used = 0;

@@ -165,7 +165,9 @@ struct Phase1TcParams {
     long long m0;             // first spectrum of the call
     int q_begin, q_count;     // the slab of spectra this launch covers
     int a_spectra;            // spectra per stream in the intermediate buffer
-    int n_streams, splits;    // item ranges per column group (grid = column groups x slices x splits)
+    int n_streams;
+    int splits;               // SMs of the device: the grid is one wave (1 or 2 CTAs per SM), each CTA a
+                              // contiguous share of the passes
     const uint16_t *bmat;     // operand blocks, build_phase1_tc_tables
     const float *oscale;      // [N2] epilogue scale per output column
     const int *ctab;          // [stream][M] coarse delays
@@ -176,7 +178,7 @@ struct Phase1TcParams {
 };
 int phase1_tc_R(int N);
 bool phase1_tc_supported(int N, int T, int precision);
-size_t phase1_tc_smem_bytes(int R, int T, int precision);
+int phase1_tc_phys(int N, int T, int precision);
 void build_phase1_tc_tables(int N, int T, int precision, const float *w, std::vector<uint16_t> &bmat,
                             std::vector<float> &oscale, float &s_int);
 cudaError_t launch_phase1_tc(int T, int precision, const Phase1TcParams &p, cudaStream_t s);

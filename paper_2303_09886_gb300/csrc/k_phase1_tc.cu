@@ -52,10 +52,7 @@ namespace fe {
 
 namespace {
 
-constexpr int kTcThreads = 288;   // 4 epilogue warps, 4 fill warps, 1 MMA warp
 constexpr int kTcRows = 128;     // spectra per pass: the MMA's M
-constexpr int kTcPhys = 8;       // physical FIR columns per CTA
-constexpr int kTcTmemCols = 256; // tensor-memory columns per CTA (two pass buffers)
 
 __host__ __device__ constexpr int tc_tp(int T) { return T < 2 ? 2 : T; }                 // K = 8 T' >= 16
 __host__ __device__ constexpr int tc_xl(int T) { return 8 * (kTcRows - 1 + tc_tp(T)); } // samples per column
@@ -64,24 +61,47 @@ __host__ __device__ constexpr int tc_kps(int R, int ks) { return (4 * R + 1 + ks
 __host__ __device__ constexpr int tc_nm(int R, int ks) { return 16 * ((2 * tc_kps(R, ks) + 15) / 16); }
 constexpr long long kTcSmemMax = 227 * 1024;
 
-// Shared-memory bytes with ks k1-slices and nxb decode buffers: the operand
-// blocks (BF16: hi and lo planes) and the decoded data (BF16: hi and lo).
-__host__ __device__ constexpr long long tc_smem(int R, int T, int prec, int ks, int nxb) {
-    return 2LL * ((prec == 2 ? 2 : 1) * kTcPhys * (long long)tc_nm(R, ks) * 8 * tc_tp(T) +
-                  (long long)nxb * (prec == 2 ? 2 : 1) * kTcPhys * tc_xl(T)) +
+// Shared-memory bytes with ph physical columns per CTA, ks k1-slices and nxb
+// data buffers: the operand blocks (BF16: hi and lo planes) and the data
+// (BF16: hi and lo).
+__host__ __device__ constexpr long long tc_smem_ph(int ph, int R, int T, int prec, int ks, int nxb) {
+    return 2LL * ((prec == 2 ? 2 : 1) * ph * (long long)tc_nm(R, ks) * 8 * tc_tp(T) +
+                  (long long)nxb * (prec == 2 ? 2 : 1) * ph * tc_xl(T)) +
            4 * kTcRows + 64 + 2048 + 256;
+}
+// Physical FIR columns per CTA: 16 where the FP16 form's operands of R <= 2
+// fit with two data buffers (the epilogue then stores 8 consecutive FP16
+// pairs = one whole 32-byte sector per (spectrum, k1), whatever the other
+// CTAs do), else 8 (one CTA per SM with 16, two with 8).
+__host__ __device__ constexpr int tc_phys(int R, int T, int prec) {
+    return (prec == 1 && R <= 2 && tc_smem_ph(16, R, T, prec, 1, 2) <= kTcSmemMax) ? 16 : 8;
+}
+// warps: 4 epilogue (one per 32 tensor-memory lanes), F fill, 1 MMA. Four
+// fill warps at one CTA per SM (PH = 16); two at two CTAs per SM, which
+// leaves each thread 128 registers
+__host__ __device__ constexpr int tc_fill_warps(int ph) { return ph == 16 ? 4 : 2; }
+__host__ __device__ constexpr int tc_threads(int ph) { return 32 * (5 + tc_fill_warps(ph)); }
+__host__ __device__ constexpr long long tc_smem(int ph, int R, int T, int prec, int ks, int nxb) {
+    return tc_smem_ph(ph, R, T, prec, ks, nxb);
 }
 // fewest k1-slices, then two decode buffers (the decode of the next pass
 // under the current one's MMAs), that fit in shared memory; 0 if none does
-__host__ __device__ constexpr int tc_ks(int R, int T, int prec) {
-    return tc_smem(R, T, prec, 1, 1) <= kTcSmemMax   ? 1
-           : tc_smem(R, T, prec, 2, 1) <= kTcSmemMax ? 2
-           : tc_smem(R, T, prec, 4, 1) <= kTcSmemMax ? 4
-           : tc_smem(R, T, prec, 8, 1) <= kTcSmemMax ? 8
-                                                      : 0;
+__host__ __device__ constexpr int tc_ks(int ph, int R, int T, int prec) {
+    return tc_smem(ph, R, T, prec, 1, 1) <= kTcSmemMax   ? 1
+           : tc_smem(ph, R, T, prec, 2, 1) <= kTcSmemMax ? 2
+           : tc_smem(ph, R, T, prec, 4, 1) <= kTcSmemMax ? 4
+           : tc_smem(ph, R, T, prec, 8, 1) <= kTcSmemMax ? 8
+                                                          : 0;
 }
-__host__ __device__ constexpr int tc_nxb(int R, int T, int prec) {
-    return tc_smem(R, T, prec, tc_ks(R, T, prec) > 0 ? tc_ks(R, T, prec) : 1, 2) <= kTcSmemMax ? 2 : 1;
+__host__ __device__ constexpr int tc_ks1(int ph, int R, int T, int prec) {
+    return tc_ks(ph, R, T, prec) > 0 ? tc_ks(ph, R, T, prec) : 1;
+}
+__host__ __device__ constexpr int tc_nxb(int ph, int R, int T, int prec) {
+    return tc_smem(ph, R, T, prec, tc_ks1(ph, R, T, prec), 2) <= kTcSmemMax ? 2 : 1;
+}
+// tensor-memory columns: two pass buffers of CW x NM, a power of two >= 32
+__host__ __device__ constexpr int tc_tmem_cols(int ph, int R, int T, int prec) {
+    return 2 * (ph / R) * tc_nm(R, tc_ks1(ph, R, T, prec)) <= 256 ? 256 : 512;
 }
 
 // ---- tcgen05 / mbarrier primitives (PTX ISA, sm_100a family) ----
@@ -359,55 +379,51 @@ __global__ void k_unpack_cols_small(const UnpackColsParams p) {
 
 // ---------------------------------------------------------------------------
 // The tensor-core kernel, warp-specialised:
-//   warps 0-3  epilogue: tensor memory -> scale -> second-stage input in HBM
-//   warps 4-7  fill: the pass's 8 column sequences from cols into the ring of
-//              shared-memory data buffers (BF16: hi and lo planes)
-//   warp 8     MMA: the tcgen05 chain of a pass into one of two tensor-memory
-//              buffers, committed to the barriers that free its data buffer
-//              and hand the accumulator to the epilogue
+//   warps 0-3    epilogue: tensor memory -> scale -> second-stage input in HBM
+//   next F warps fill: the pass's PH column sequences from cols into the ring
+//                of shared-memory data buffers (BF16: hi and lo planes); F = 4
+//                at PH = 16 (one CTA per SM), 2 at PH = 8 (two CTAs per SM)
+//   last warp    MMA: the tcgen05 chain of a pass into one of two tensor-memory
+//                buffers, committed to the barriers that free its data buffer
+//                and hand the accumulator to the epilogue
 // Each role walks the same pass sequence; they synchronise only through
 // mbarriers (xfull / xempty per data buffer, tfull / tempty per tensor-memory
 // buffer), every wait bounded.
-template <int R, int T, int PREC>
-__global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParams p) {
-    constexpr int KS = tc_ks(R, T, PREC), KPS = tc_kps(R, KS);   // k1-slices, k1 values per slice
-    constexpr int NM = tc_nm(R, KS), TP = tc_tp(T), K = 8 * TP, XL = tc_xl(T), CW = kTcPhys / R;
+template <int R, int T, int PREC, int PH>   // PH: physical FIR columns of the CTA
+__global__ void __launch_bounds__(tc_threads(PH), PH == 16 ? 1 : 2) k_phase1_tc(const Phase1TcParams p) {
+    constexpr int KS = tc_ks(PH, R, T, PREC), KPS = tc_kps(R, KS);   // k1-slices, k1 values per slice
+    constexpr int TMEMC = tc_tmem_cols(PH, R, T, PREC);               // tensor-memory columns allocated
+    constexpr int NM = tc_nm(R, KS), TP = tc_tp(T), K = 8 * TP, XL = tc_xl(T), CW = PH / R;
     constexpr int NPL = PREC == 2 ? 2 : 1;    // data planes: BF16 hi + lo
     constexpr int NPB = PREC == 2 ? 2 : 1;    // operand planes: BF16 hi + lo
     constexpr int H1 = 4 * R;                 // k1 in [0, H1]
     constexpr int BBLK = NM * K;              // 16-bit elements per operand block
     constexpr int TMC = CW * NM;              // tensor-memory columns per pass buffer
     constexpr int NG = (2 * KPS + 7) / 8;     // 8-column groups holding (Re, Im) of the slice's k1
-    constexpr int NXB = tc_nxb(R, T, PREC);   // data buffers
+    constexpr int NXB = tc_nxb(PH, R, T, PREC);   // data buffers
+    constexpr int NTH = tc_threads(PH), FT = 32 * tc_fill_warps(PH);   // threads, fill threads
+    constexpr int WMMA = 4 + tc_fill_warps(PH);                         // the MMA warp
     static_assert(KS > 0, "shape does not fit in shared memory");
-    static_assert(2 * TMC <= kTcTmemCols, "tensor memory");
+    static_assert(2 * TMC <= TMEMC, "tensor memory");
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint16_t *bsm = reinterpret_cast<uint16_t *>(smem);            // [NPB][kTcPhys][BBLK]
-    uint16_t *xsm = bsm + NPB * kTcPhys * BBLK;                    // [NXB][NPL][kTcPhys][XL]
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(xsm + NXB * NPL * kTcPhys * XL);
+    uint16_t *bsm = reinterpret_cast<uint16_t *>(smem);            // [NPB][PH][BBLK]
+    uint16_t *xsm = bsm + NPB * PH * BBLK;                    // [NXB][NPL][PH][XL]
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(xsm + NXB * NPL * PH * XL);
     unsigned long long *xfull = bar, *xempty = bar + 2, *tfull = bar + 4, *tempty = bar + 6;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 8);
     volatile int *abort_sm = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    long long *fsrc = reinterpret_cast<long long *>(bar + 9);          // [NXB][kTcPhys] column source offsets
-    int *fsh = reinterpret_cast<int *>(fsrc + 2 * kTcPhys);            // [NXB][kTcPhys] row0 mod 8
+    long long *fsrc = reinterpret_cast<long long *>(bar + 9);          // [NXB][PH] column source offsets
+    int *fsh = reinterpret_cast<int *>(fsrc + 2 * PH);            // [NXB][PH] row0 mod 8
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // block = (column group, k1-slice, item range)
-    const int cg = blockIdx.x / (p.splits * KS), slice = (blockIdx.x / p.splits) % KS, split = blockIdx.x % p.splits;
-    const int k1_lo = slice * KPS, k1_hi = min(H1 + 1, k1_lo + KPS);
     const int n_tiles = (p.q_count + kTcRows - 1) / kTcRows;
     const int n_items = p.n_streams * n_tiles;
-    const int it_begin = (int)((long long)n_items * split / p.splits);
-    const int it_end = (int)((long long)n_items * (split + 1) / p.splits);
     const int P = p.N / 8, N2 = p.N2;
-
-    // the CTA's operand blocks (weights x DFT x twiddle), resident for all its items
-    {
-        const uint4 *src =
-            reinterpret_cast<const uint4 *>(p.bmat) + ((long long)cg * KS + slice) * (NPB * kTcPhys * BBLK / 8);
-        uint4 *dst = reinterpret_cast<uint4 *>(bsm);
-        for (int i = tid; i < NPB * kTcPhys * BBLK / 8; i += kTcThreads) dst[i] = __ldg(src + i);
-    }
+    // Work units: (column group, k1-slice, item), item fastest; CTA b takes a
+    // contiguous range of equal length (persistent: one wave of CTAs), which
+    // spans few (column group, slice) segments, each loading its operand blocks.
+    const long long n_units = (long long)(N2 / CW) * KS * n_items;
+    const long long u_begin = n_units * blockIdx.x / gridDim.x, u_end = n_units * (blockIdx.x + 1) / gridDim.x;
     if (tid == 0) {
         for (int i = 0; i < 2; i++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&xfull[i])));
@@ -418,12 +434,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_sm = 0;
     }
-    if (warp == 8) {
+    if (warp == WMMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                     "r"(kTcTmemCols));
+                     "r"(TMEMC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the operand blocks, for the tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -447,6 +462,28 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
         asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(b))
                      : "memory");
     };
+    // pass counters of the roles: the barriers' phases run on across segments
+    int pc_fill = 0, pc_mma = 0, pc_epi = 0;
+    for (long long u = u_begin; u < u_end;) {
+    const long long cgs = u / n_items;   // (column group, slice) of this segment
+    const int it_begin = (int)(u - cgs * n_items);
+    const int it_end = (int)(u_end - cgs * n_items < n_items ? u_end - cgs * n_items : n_items);
+    u = cgs * n_items + it_end;
+    const int cg = (int)(cgs / KS), slice = (int)(cgs % KS);
+    const int k1_lo = slice * KPS, k1_hi = min(H1 + 1, k1_lo + KPS);
+    // the segment's operand blocks (weights x DFT x twiddle); the previous
+    // segment's MMAs have completed (its last accumulator was drained)
+    {
+        const uint4 *src =
+            reinterpret_cast<const uint4 *>(p.bmat) + ((long long)cg * KS + slice) * (NPB * PH * BBLK / 8);
+        uint4 *dst = reinterpret_cast<uint4 *>(bsm);
+        for (int i = tid; i < NPB * PH * BBLK / 8; i += NTH) dst[i] = __ldg(src + i);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the operand blocks, for the tensor core
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (*abort_sm) break;
     // index in the pre-delayed columns (timestamp + c0) of row v = 0 of physical
     // column i (run j = i / CW, column c = i % CW)
     auto col_start = [&](const Pass &ps, int i) -> long long {
@@ -459,7 +496,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
     iter.ra = -1;
     pass_prefetch(iter, p, n_tiles, it_begin);
     Pass ps;
-    if (warp >= 4 && warp < 8) {
+    if (warp >= 4 && warp < WMMA) {
         // ---------------- fill ----------------
         // A column's sequence starts at element row0 of its FP16 column;
         // it is copied in 16-byte chunks from the aligned element
@@ -467,28 +504,28 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
         // byte offset 2 sh of two consecutive source chunks.
         const int ft = tid - 128;
         constexpr int CPC = XL / 8;                 // 16-byte chunks per column sequence
-        for (int pc = 0; warp_next_pass(iter, ps, p, n_tiles); pc++) {
+        for (int &pc = pc_fill; warp_next_pass(iter, ps, p, n_tiles); pc++) {
             const int s = pc % NXB, use = pc / NXB;
             // the decision to go on is the same in every fill thread (a thread
             // must not leave while the others wait at the named barrier)
             int ok = use == 0 || ft != 0 || wait_bar(&xempty[s], (use - 1) & 1);
-            asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\tbar.red.and.pred q, 1, 128, q;\n\t"
+            asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\tbar.red.and.pred q, 1, %2, q;\n\t"
                          "selp.s32 %0, 1, 0, q;\n\t}\n"
                          : "=r"(ok)
-                         : "r"(ok)
+                         : "r"(ok), "n"(FT)
                          : "memory");
             if (!ok) break;
-            uint16_t *xb = xsm + (size_t)s * NPL * kTcPhys * XL;
+            uint16_t *xb = xsm + (size_t)s * NPL * PH * XL;
             if (PREC == 1 && !p.window_tap && ps.c == ps.c0) {
                 // the pass's delay is the columns' c0: every column sequence starts at
                 // row 8 (m0 + q0) - rb, 16-byte aligned, one bulk copy each
                 if (ft == 0) {
-                    constexpr uint32_t bytes = (uint32_t)(kTcPhys * XL * 2);
+                    constexpr uint32_t bytes = (uint32_t)(PH * XL * 2);
                     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
                                  ::"r"(smem_addr(&xfull[s])), "r"(bytes) : "memory");
                     const long long row0 = 8LL * (p.m0 + ps.q0) - p.rb;
 #pragma unroll 1
-                    for (int i = 0; i < kTcPhys; i++) {
+                    for (int i = 0; i < PH; i++) {
                         const long long t = (long long)cg * CW + (i % CW) + (long long)N2 * (i / CW);
                         const uint16_t *src = p.cols + ((long long)ps.st * P + t) * p.RTP + row0;
                         asm volatile(
@@ -500,32 +537,32 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
                 }
                 continue;
             }
-            if (ft < kTcPhys) {
+            if (ft < PH) {
                 const long long a0 = col_start(ps, ft);
                 const long long ra = floor_div(a0, P);
                 const long long col = a0 - ra * P, row0 = ra - p.rb;
-                fsrc[s * kTcPhys + ft] = ((long long)ps.st * P + col) * p.RTP + (row0 & ~7LL);
-                fsh[s * kTcPhys + ft] = (int)(row0 & 7);
+                fsrc[s * PH + ft] = ((long long)ps.st * P + col) * p.RTP + (row0 & ~7LL);
+                fsh[s * PH + ft] = (int)(row0 & 7);
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            for (int e0 = ft; e0 < kTcPhys * CPC; e0 += 128 * 3) {
+            asm volatile("bar.sync 1, %0;" ::"n"(FT) : "memory");
+            for (int e0 = ft; e0 < PH * CPC; e0 += FT * 3) {
                 uint4 a[3], b[3];
 #pragma unroll
                 for (int u = 0; u < 3; u++) {
-                    const int e = e0 + 128 * u;
-                    if (e < kTcPhys * CPC) {
+                    const int e = e0 + FT * u;
+                    if (e < PH * CPC) {
                         const int i = e / CPC, j = e - i * CPC;
-                        const uint4 *src = reinterpret_cast<const uint4 *>(p.cols + fsrc[s * kTcPhys + i]) + j;
+                        const uint4 *src = reinterpret_cast<const uint4 *>(p.cols + fsrc[s * PH + i]) + j;
                         a[u] = __ldg(src);
                         b[u] = __ldg(src + 1);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < 3; u++) {
-                    const int e = e0 + 128 * u;
-                    if (e < kTcPhys * CPC) {
+                    const int e = e0 + FT * u;
+                    if (e < PH * CPC) {
                         const int i = e / CPC, j = e - i * CPC;
-                        const int sh = fsh[s * kTcPhys + i];
+                        const int sh = fsh[s * PH + i];
                         const uint32_t w[8] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
                         uint32_t o[4];
                         const uint32_t sel = (sh & 1) ? 0x5432u : 0x3210u;   // 2-byte shift for odd sh
@@ -552,7 +589,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
 #pragma unroll
                             for (int m = 0; m < 4; m++) half2_to_bf16x2(o[m], h[m], l[m]);
                             reinterpret_cast<uint4 *>(xb + (size_t)i * XL)[j] = make_uint4(h[0], h[1], h[2], h[3]);
-                            reinterpret_cast<uint4 *>(xb + (size_t)(kTcPhys + i) * XL)[j] =
+                            reinterpret_cast<uint4 *>(xb + (size_t)(PH + i) * XL)[j] =
                                 make_uint4(l[0], l[1], l[2], l[3]);
                         } else {
                             reinterpret_cast<uint4 *>(xb + (size_t)i * XL)[j] = make_uint4(o[0], o[1], o[2], o[3]);
@@ -562,15 +599,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
             }
             if (p.window_tap) {
                 // debug tap: the first FIR tap of spectrum q0 + v / 8 at offset P (v % 8) + t
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                const uint16_t *xv = xsm + (size_t)s * NPL * kTcPhys * XL;
-                for (int e = ft; e < kTcPhys * 8 * kTcRows; e += 128) {
+                asm volatile("bar.sync 1, %0;" ::"n"(FT) : "memory");
+                const uint16_t *xv = xsm + (size_t)s * NPL * PH * XL;
+                for (int e = ft; e < PH * 8 * kTcRows; e += FT) {
                     const int i = e / (8 * kTcRows), vv = e - i * (8 * kTcRows), mrow = vv >> 3;
                     if (mrow < ps.ra || mrow >= ps.rb) continue;
                     float x;
                     if constexpr (PREC == 2) {
                         x = __bfloat162float(__ushort_as_bfloat16(xv[(size_t)i * XL + vv])) +
-                            __bfloat162float(__ushort_as_bfloat16(xv[(size_t)(kTcPhys + i) * XL + vv]));
+                            __bfloat162float(__ushort_as_bfloat16(xv[(size_t)(PH + i) * XL + vv]));
                     } else {
                         x = __half2float(__ushort_as_half(xv[(size_t)i * XL + vv]));
                     }
@@ -580,13 +617,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
             }
             // every fill thread's writes, then one arrival
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(FT) : "memory");
             if (ft == 0) arrive(&xfull[s]);
         }
-    } else if (warp == 8) {
+    } else if (warp == WMMA) {
         // ---------------- MMA ----------------
         constexpr uint32_t idesc = mma_idesc(kTcRows, NM, PREC == 2 ? 1 : 0);
-        for (int pc = 0; warp_next_pass(iter, ps, p, n_tiles); pc++) {
+        for (int &pc = pc_mma; warp_next_pass(iter, ps, p, n_tiles); pc++) {
             const int s = pc % NXB, b = pc & 1;
             bool ok = true;
             if (lane == 0) {
@@ -597,7 +634,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
             tc_fence_after();
             if (lane == 0) {
                 const uint32_t d0 = tmem + (uint32_t)(b * TMC);
-                const uint32_t xa0 = smem_addr(xsm + (size_t)s * NPL * kTcPhys * XL), ba0 = smem_addr(bsm);
+                const uint32_t xa0 = smem_addr(xsm + (size_t)s * NPL * PH * XL), ba0 = smem_addr(bsm);
 #pragma unroll 1
                 for (int c = 0; c < CW; c++) {
 #pragma unroll 1
@@ -608,8 +645,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
 #pragma unroll
                         for (int pp = 0; pp < (PREC == 2 ? 3 : 1); pp++) {
                             const int pl = pp == 1 ? 1 : 0, pb = pp == 2 ? 1 : 0;
-                            const uint32_t xa = xa0 + (uint32_t)((pl * kTcPhys + i) * XL * 2);
-                            const uint32_t ba = ba0 + (uint32_t)((pb * kTcPhys + i) * BBLK * 2);
+                            const uint32_t xa = xa0 + (uint32_t)((pl * PH + i) * XL * 2);
+                            const uint32_t ba = ba0 + (uint32_t)((pb * PH + i) * BBLK * 2);
 #pragma unroll
                             for (int kk = 0; kk < K / 16; kk++) {
                                 const uint64_t ad = mat_desc(xa + 32u * kk, 16u, 128u);
@@ -631,7 +668,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
         float osc[CW];
 #pragma unroll
         for (int c = 0; c < CW; c++) osc[c] = __ldg(p.oscale + cg * CW + c);
-        for (int pc = 0; warp_next_pass(iter, ps, p, n_tiles); pc++) {
+        for (int &pc = pc_epi; warp_next_pass(iter, ps, p, n_tiles); pc++) {
             const int b = pc & 1;
             const bool got = lane == 0 ? wait_bar(&tfull[b], (pc >> 1) & 1) : true;
             if (!__shfl_sync(0xFFFFFFFFu, (int)got, 0)) break;
@@ -660,11 +697,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
                             hv[c] = *reinterpret_cast<const uint32_t *>(&h);
                         }
                         uint32_t *out = reinterpret_cast<uint32_t *>(p.A) + o;
-                        if constexpr (CW == 8) {
-                            reinterpret_cast<uint4 *>(out)[0] = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                            reinterpret_cast<uint4 *>(out)[1] = make_uint4(hv[4], hv[5], hv[6], hv[7]);
-                        } else if constexpr (CW == 4) {
-                            reinterpret_cast<uint4 *>(out)[0] = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        static_assert(CW == 1 || CW == 2 || CW % 4 == 0, "column group width");
+                        if constexpr (CW % 4 == 0) {
+#pragma unroll
+                            for (int c = 0; c < CW; c += 4)
+                                reinterpret_cast<uint4 *>(out)[c / 4] = make_uint4(hv[c], hv[c + 1], hv[c + 2], hv[c + 3]);
                         } else if constexpr (CW == 2) {
                             reinterpret_cast<uint2 *>(out)[0] = make_uint2(hv[0], hv[1]);
                         } else {
@@ -673,9 +710,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
                     }
                 }
             };
-            if constexpr (NG * CW <= 16) {
+            if constexpr (NG * CW <= (PH == 16 ? 16 : 4)) {
                 // all of the pass's accumulator columns in registers, one wait,
-                // tensor memory released before the stores
+                // tensor memory released before the stores (within the register
+                // budget of two CTAs per SM when PH = 8)
                 float vall[NG][CW][8];
 #pragma unroll
                 for (int g = 0; g < NG; g++)
@@ -702,9 +740,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
             }
         }
     }
+    // end of segment: every role is through its passes (the epilogue drained
+    // the last accumulator, so every MMA of the segment has completed)
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    }
     // teardown: every role has left its loop; the last accumulator was read
     // (or a wait gave up: give the tensor core a bounded moment to finish)
-    if (*abort_sm && warp == 8) {
+    if (*abort_sm && warp == WMMA) {
         const long long t0 = clock64();
         while (clock64() - t0 < 20000000LL) {
         }
@@ -712,16 +756,20 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_phase1_tc(const Phase1TcParam
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
+    if (warp == WMMA) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEMC));
 }
 
 // ---------------------------------------------------------------- host side
 
-int phase1_tc_slices(int R, int T, int precision) { return tc_ks(R, T, precision); }
+// Physical FIR columns per CTA for an N-point transform: 16 where tc_phys
+// allows it and the N2 output columns hold a group of 16 / R (all but N = 64)
+int phase1_tc_phys(int N, int T, int precision) {
+    const int R = phase1_tc_R(N);
+    return tc_phys(R, T, precision) == 16 && N / 8 / R >= 16 / R ? 16 : 8;
+}
 
-size_t phase1_tc_smem_bytes(int R, int T, int precision) {
-    const int ks = tc_ks(R, T, precision);
-    const size_t b = (size_t)tc_smem(R, T, precision, ks > 0 ? ks : 1, tc_nxb(R, T, precision));
+static size_t tc_smem_bytes(int ph, int R, int T, int precision) {
+    const size_t b = (size_t)tc_smem(ph, R, T, precision, tc_ks1(ph, R, T, precision), tc_nxb(ph, R, T, precision));
     // at most two CTAs per SM (the tensor memory of two fills the 512 columns)
     const size_t floor = 80 * 1024;
     return b < floor ? floor : b;
@@ -735,17 +783,17 @@ int phase1_tc_R(int N) {
 bool phase1_tc_supported(int N, int T, int precision) {
     const int R = phase1_tc_R(N);
     return N >= 64 && N <= 65536 && (R == 1 || R == 2 || R == 4 || R == 8) && T >= 1 && T <= 32 &&
-           tc_ks(R, T, precision) > 0;
+           tc_ks(phase1_tc_phys(N, T, precision), R, T, precision) > 0;
 }
 
 void build_phase1_tc_tables(int N, int T, int precision, const float *w, std::vector<uint16_t> &bmat,
                             std::vector<float> &oscale, float &s_int) {
-    const int R = phase1_tc_R(N), P = N / 8, N2 = P / R, CW = kTcPhys / R;
-    const int KS = tc_ks(R, T, precision), KPS = tc_kps(R, KS), NM = tc_nm(R, KS), TP = tc_tp(T), K = 8 * TP;
+    const int R = phase1_tc_R(N), P = N / 8, N2 = P / R, PH = phase1_tc_phys(N, T, precision), CW = PH / R;
+    const int KS = tc_ks(PH, R, T, precision), KPS = tc_kps(R, KS), NM = tc_nm(R, KS), TP = tc_tp(T), K = 8 * TP;
     const int H1 = 4 * R, NPB = precision == 2 ? 2 : 1;
     const int n_cg = N2 / CW;
     // [column group][k1-slice][plane][physical column][NM x K]
-    bmat.assign((size_t)n_cg * KS * NPB * kTcPhys * NM * K, 0);
+    bmat.assign((size_t)n_cg * KS * NPB * PH * NM * K, 0);
     oscale.assign(N2, 1.0f);
     // global scale of the FP16 intermediate: |Z| <= 512 sum_j sum_r |w[t + P r]|
     double zmax = 0.0;
@@ -775,7 +823,7 @@ void build_phase1_tc_tables(int N, int T, int precision, const float *w, std::ve
             for (int sl = 0; sl < KS; sl++)
                 for (int j = 0; j < R; j++) {
                     const long long t = t2 + (long long)N2 * j;
-                    const size_t blk0 = (((size_t)cgi * KS + sl) * NPB * kTcPhys + j * CW + c) * NM * K;
+                    const size_t blk0 = (((size_t)cgi * KS + sl) * NPB * PH + j * CW + c) * NM * K;
                     for (int nrow = 0; nrow < NM; nrow++) {
                         const int k1 = sl * KPS + nrow / 2, im = nrow % 2;
                         for (int k = 0; k < K; k++) {
@@ -794,7 +842,7 @@ void build_phase1_tc_tables(int N, int T, int precision, const float *w, std::ve
                                 const __nv_bfloat16 hi = __float2bfloat16_rn((float)val);
                                 const __nv_bfloat16 lo = __float2bfloat16_rn((float)(val - (double)__bfloat162float(hi)));
                                 bmat[blk0 + off] = __bfloat16_as_ushort(hi);
-                                bmat[blk0 + (size_t)kTcPhys * NM * K + off] = __bfloat16_as_ushort(lo);
+                                bmat[blk0 + (size_t)PH * NM * K + off] = __bfloat16_as_ushort(lo);
                             } else {
                                 bmat[blk0 + off] = __half_as_ushort(__float2half_rn((float)val));
                             }
@@ -805,16 +853,34 @@ void build_phase1_tc_tables(int N, int T, int precision, const float *w, std::ve
     }
 }
 
-template <int R, int T, int PREC>
-static cudaError_t launch_tc(const Phase1TcParams &p, cudaStream_t s) {
-    const size_t smem = phase1_tc_smem_bytes(R, T, PREC);
-    cudaError_t e = cudaFuncSetAttribute(k_phase1_tc<R, T, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int R, int T, int PREC, int PH>
+static cudaError_t launch_tc_ph(const Phase1TcParams &p, cudaStream_t s) {
+    const size_t smem = tc_smem_bytes(PH, R, T, PREC);
+    cudaError_t e = cudaFuncSetAttribute(k_phase1_tc<R, T, PREC, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const int n_cg = p.N2 / (kTcPhys / R);
-    constexpr int KS = tc_ks(R, T, PREC) > 0 ? tc_ks(R, T, PREC) : 1;
-    k_phase1_tc<R, T, PREC><<<n_cg * KS * p.splits, kTcThreads, smem, s>>>(p);
+    const int n_cg = p.N2 / (PH / R);
+    constexpr int KS = tc_ks1(PH, R, T, PREC);
+    const long long n_units = (long long)n_cg * KS * p.n_streams * ((p.q_count + kTcRows - 1) / kTcRows);
+    // one wave: two CTAs per SM when two fit in shared memory, else one
+    const long long ctas = (long long)p.splits * (smem <= 113 * 1024 ? 2 : 1);
+    const int grid = (int)(n_units < ctas ? n_units : ctas);
+    if (grid < 1) return cudaErrorInvalidValue;
+    k_phase1_tc<R, T, PREC, PH><<<grid, tc_threads(PH), smem, s>>>(p);
     return cudaGetLastError();
+}
+
+// the kernel with the column count phase1_tc_phys gives for this N
+template <int R, int T, int PREC>
+static cudaError_t launch_tc(const Phase1TcParams &p, cudaStream_t s) {
+    if constexpr (tc_phys(R, T, PREC) == 16) {
+        if constexpr (R == 1) {
+            if (p.N2 < 16) return launch_tc_ph<R, T, PREC, 8>(p, s);
+        }
+        return launch_tc_ph<R, T, PREC, 16>(p, s);
+    } else {
+        return launch_tc_ph<R, T, PREC, 8>(p, s);
+    }
 }
 
 template <int R, int PREC>
