@@ -47,6 +47,7 @@ KERNEL_SOURCES = {
     "k_phase2": ['k_phase2.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase2w": ['k_phase2w.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase1_tc": ['k_phase1_tc.cu', 'fe_device.cuh', 'fe_internal.cuh'],
+    "k_unpack_cols": ['k_phase1_tc.cu', 'fe_device.cuh', 'fe_internal.cuh'],
 }
 _CAPTURED = 33554432   # input samples of the captured launch
 NCU_TRAFFIC = {
@@ -244,19 +245,35 @@ def _base_streams(seed: int, n: int, sigma: float = 32.0):
 
 
 def run_batched(args):
+    """Workload 4 as its own JSON line."""
+    import torch
+    from paper_2303_09886_gb300 import build as fe_build
+    from paper_2303_09886_gb300 import fengine
+
+    torch.cuda.set_device(0)
+    fe_build.build()
+    fengine.load()
+    r = batched_result(args, fengine, torch)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": r["workload"], "samples_per_step": r["samples_per_step"],
+                       "pool_streams": args.pool},
+            "sequential_single_stream": r["sequential_single_stream"], "gpu_launches": r["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def batched_result(args, fengine, torch):
     """Workload 4: many uneven independent streams in one batched call.
 
     64 plans (1 antenna x 2 pols each) with channels drawn from {1024, 4096,
     8192, 32768}, taps from {4, 8, 16}, chunk lengths uniform in
     [2^20, 2^26] samples/pol truncated to a multiple of 2n, random delays and
-    gains. One step = one fengine_batch_process over one chunk of every plan."""
-    import torch
-    from paper_2303_09886_gb300 import build as fe_build
-    from paper_2303_09886_gb300 import fengine, synth
+    gains. One step = one fengine_batch_process over one chunk of every plan;
+    the same members one call after another on one stream are timed beside it."""
+    from paper_2303_09886_gb300 import synth
 
-    torch.cuda.set_device(0)
-    fe_build.build()
-    fengine.load()
     g = synth.rng(synth.SEED_BASE + 4)
     n_plans = args.plans or 64
     base = _base_streams(synth.SEED_BASE + 4, 1 << 26)
@@ -317,37 +334,49 @@ def run_batched(args):
     torch.cuda.synchronize()
     ms_seq = e0.elapsed_time(e1)
     value = total * args.steps / (ms / 1e3) / 1e9
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched uneven: {n_plans} independent dual-pol streams, channels in "
-                                   "{1024,4096,8192,32768}, taps in {4,8,16}, chunks U[2^20,2^26] samples/pol",
-                       "samples_per_step": total, "pool_streams": args.pool},
-            "sequential_single_stream": {"value": total * k2 / (ms_seq / 1e3) / 1e9, "unit": UNIT,
-                                         "ms_per_step": ms_seq / k2},
-            "gpu_launches": None}
-    print(json.dumps(line), flush=True)
+    res = {"value": value, "unit": UNIT, "ms_per_step": ms / args.steps, "steps": args.steps,
+           "workload": f"batched uneven: {n_plans} independent dual-pol streams, channels in "
+                       "{1024,4096,8192,32768}, taps in {4,8,16}, chunks U[2^20,2^26] samples/pol",
+           "samples_per_step": total,
+           "sequential_single_stream": {"value": total * k2 / (ms_seq / 1e3) / 1e9, "unit": UNIT,
+                                        "ms_per_step": ms_seq / k2},
+           "gpu_launches": args.steps * sum(2 + 2 * m[0].info.slabs_per_chunk for m in members)}
     batch.close()
     for p in plans:
         p.close()
-    return 0
+    return res
 
 
 def run_service(args):
-    """Workload 5: streaming service. 16 plans (1 antenna x 2 pols, 8192
-    channels, 16 taps), chunks of 2^24 samples/pol arriving by a Poisson
-    process at `--load` times the sustained rate measured first; delay updates
-    every 2^22 samples; HBM budget 40 GB. Reports admitted Gsample/s and
-    chunk latency p50/p99 (submit -> output in host memory)."""
-    import threading as th
-
+    """Workload 5 as its own JSON line."""
     import torch
     from paper_2303_09886_gb300 import build as fe_build
-    from paper_2303_09886_gb300 import fengine, synth
+    from paper_2303_09886_gb300 import fengine
 
     torch.cuda.set_device(0)
     fe_build.build()
     fengine.load()
+    r = service_result(args, fengine, torch)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": r["chunks_total"], "warmup": r["warmup_chunks"], "ms_per_step": r["ms_per_chunk"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": r["workload"], "pool_streams": args.pool},
+            "service": {k: v for k, v in r.items() if k not in ("value", "workload")}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def service_result(args, fengine, torch):
+    """Workload 5: streaming service. 16 plans (1 antenna x 2 pols, 8192
+    channels, 16 taps), chunks of 2^24 samples/pol submitted from host memory
+    by a Poisson process at `--load` times the rate the device sustains on
+    resident input (measured first on the same plans), so that requests queue
+    behind the host copies; delay updates every 2^22 samples; an HBM budget of
+    `--budget-gb` for the buffers in flight, small enough that admission
+    defers. Reports delivered Gsample/s, chunk latency p50/p99 (submit ->
+    output in host memory) and the admitted / deferred counts."""
+    from paper_2303_09886_gb300 import synth
+
     n_ant, n, T, L = 16, 8192, 16, 1 << 24
     chunks = args.chunks
     g = synth.rng(synth.SEED_BASE + 5)
@@ -357,24 +386,31 @@ def run_service(args):
     outs = [[torch.empty(p.info.out_bytes, dtype=torch.int8).pin_memory().numpy() for _ in range(2)]
             for p in plans]
     d0 = g.uniform(0, 2000, n_ant)
-    # sustained rate: the 16 plans back to back through the service, no arrival gaps
-    svc = fengine.Service(n_streams=args.pool, hbm_budget_bytes=40 << 30)
-    t0 = time.perf_counter()
-    tk = []
-    for c in range(2):
-        for a, p in enumerate(plans):
-            svc.set_delay(p, 0, 0, float(d0[a]), 1e-9)
-            svc.set_delay(p, 0, 1, float(d0[a]), 1e-9)
-            tk.append(svc.submit(p, h_in, c * L, outs[a][c % 2]))
-    for x in tk:
-        svc.wait(x)
-    sustained = 2 * n_ant * 2 * L / (time.perf_counter() - t0)
-    svc.close()
+    budget = int(args.budget_gb * (1 << 30))
+    # device-resident sustained rate of the same plans: resident input,
+    # back-to-back calls on one stream
+    d_in = torch.from_numpy(base).cuda()
+    d_out = torch.empty(plans[0].info.out_bytes, dtype=torch.int8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for a, p in enumerate(plans):
+        p.set_delay(0, 0, float(d0[a]), 1e-9)
+        p.set_delay(0, 1, float(d0[a]), 1e-9)
+        p.process(d_in, 0, d_out, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for c in range(1, 3):
+        for p in plans:
+            p.process(d_in, c * L, d_out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sustained = 2 * n_ant * 2 * L / (e0.elapsed_time(e1) / 1e3)
+    del d_in, d_out
     for p in plans:
         p.reset()
     # Poisson arrivals at load x sustained
     rate = args.load * sustained / (2 * L)          # chunks per second, all antennas
-    svc = fengine.Service(n_streams=args.pool, hbm_budget_bytes=40 << 30)
+    svc = fengine.Service(n_streams=args.pool, hbm_budget_bytes=budget)
     arrivals = np.cumsum(g.exponential(1.0 / rate, n_ant * chunks))
     order = [(k % n_ant, k // n_ant) for k in range(n_ant * chunks)]
     tickets = []
@@ -392,23 +428,20 @@ def run_service(args):
     wall = time.perf_counter() - t_start
     st = svc.stats()
     svc.close()
-    line = {"metric": METRIC, "value": n_ant * chunks * 2 * L / wall / 1e9, "unit": UNIT, "n_gpus": 1,
-            "steps": n_ant * chunks, "warmup": 2 * n_ant, "ms_per_step": wall * 1e3 / (n_ant * chunks),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"streaming service: {n_ant} ant x 2 pol, 8192 ch, 16 taps, chunks 2^24 "
-                                   f"samples/pol, Poisson arrivals at {args.load}x sustained, delay updates "
-                                   f"every 2^22 samples, HBM budget 40 GB, {chunks} chunks per antenna",
-                       "pool_streams": args.pool},
-            "service": {"sustained_Gsps": sustained / 1e9, "offered_Gsps": args.load * sustained / 1e9,
-                        "latency_p50_ms": float(np.percentile(lat, 50)) / 1e3,
-                        "latency_p99_ms": float(np.percentile(lat, 99)) / 1e3,
-                        "admitted": st["admitted"], "deferred": st["deferred"],
-                        "peak_bytes": st["peak_bytes"]}}
-    print(json.dumps(line), flush=True)
+    res = {"value": n_ant * chunks * 2 * L / wall / 1e9, "unit": UNIT,
+           "workload": f"streaming service: {n_ant} ant x 2 pol, 8192 ch, 16 taps, chunks 2^24 samples/pol "
+                       f"from host memory, Poisson arrivals at {args.load}x the device-resident rate, delay "
+                       f"updates every 2^22 samples, HBM budget {args.budget_gb:g} GiB, {chunks} chunks per antenna",
+           "chunks_total": n_ant * chunks, "warmup_chunks": n_ant, "ms_per_chunk": wall * 1e3 / (n_ant * chunks),
+           "device_resident_Gsps": sustained / 1e9, "offered_Gsps": args.load * sustained / 1e9,
+           "latency_p50_ms": float(np.percentile(lat, 50)) / 1e3,
+           "latency_p99_ms": float(np.percentile(lat, 99)) / 1e3,
+           "service_p50_ms": st["latency_p50_us"] / 1e3, "service_p99_ms": st["latency_p99_us"] / 1e3,
+           "admitted": st["admitted"], "deferred": st["deferred"], "failed": st["failed"],
+           "peak_bytes": st["peak_bytes"], "budget_bytes": budget}
     for p in plans:
         p.close()
-    return 0
+    return res
 
 
 def _tuned_split(fengine, wl, prec, args):
@@ -418,10 +451,15 @@ def _tuned_split(fengine, wl, prec, args):
         return {"fft_n1": n1, "slab_spectra": sl, "autotuned": False}
     if args.no_autotune:
         return {"fft_n1": 0, "slab_spectra": 0, "autotuned": False}
+    if args.tune_cache:
+        best, hit = fengine.autotune_cached(args.tune_cache, wl.n_antennas, wl.n_channels, wl.n_taps,
+                                            wl.chunk_samples, spectra_per_heap=wl.spectra_per_heap,
+                                            max_delay_samples=wl.max_delay, precision=prec, calls=3)
+        return {**best, "autotuned": True, "from_cache": hit}
     best, table = fengine.autotune(wl.n_antennas, wl.n_channels, wl.n_taps, wl.chunk_samples,
                                    spectra_per_heap=wl.spectra_per_heap, max_delay_samples=wl.max_delay,
                                    precision=prec, calls=3)
-    return {**best, "autotuned": True,
+    return {**best, "autotuned": True, "from_cache": False,
             "candidates_ms_per_call": {f"n1={a},slab={b}": round(ms, 4) for a, b, ms in table}}
 
 
@@ -477,10 +515,16 @@ def main(argv=None):
     ap.add_argument("--chunk-samples", type=int, default=0, help="override the chunk length")
     ap.add_argument("--plans", type=int, default=0, help="workload 4: number of plans (default 64)")
     ap.add_argument("--pool", type=int, default=8, help="workloads 4/5: internal CUDA streams")
-    ap.add_argument("--chunks", type=int, default=8, help="workload 5: chunks per antenna")
+    ap.add_argument("--chunks", type=int, default=64, help="workload 5: chunks per antenna")
+    ap.add_argument("--budget-gb", type=float, default=4.0, help="workload 5: HBM budget of the service (GiB)")
     ap.add_argument("--load", type=float, default=1.5, help="workload 5: offered load / sustained rate")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision forms")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched (workload 4) and service (workload 5) keys of the default line")
     ap.add_argument("--no-autotune", action="store_true", help="use the built-in work split instead of the autotuner's")
+    ap.add_argument("--tune-cache", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                         "paper_2303_09886_gb300", "autotune_cache.jsonl"),
+                    help="JSON Lines file of autotuned splits ('' = always tune)")
     ap.add_argument("--split", default="", help="fixed work split 'N1,SLAB' (fft_n1, slab_spectra) instead of tuning")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="fp32 plain form, or the tensor-core forms (FP16/BF16 operands, FP32 accumulation)")
@@ -631,37 +675,53 @@ def main(argv=None):
             if name != args.precision:
                 forms[name] = _time_form(fengine, torch, wl, name, d_in, args)
     clocks.stop()
+    # workloads 4 (batched uneven streams) and 5 (service) on the same GPU,
+    # after the headline's timed region, as extra keys of the line
+    extra = {}
+    if ws == 1 and not args.no_extra and args.workload == 2:
+        import copy
+        ab = copy.copy(args)
+        ab.steps, ab.warmup = min(args.steps, 10), 3
+        extra["batched"] = batched_result(ab, fengine, torch)
+        extra["service"] = service_result(args, fengine, torch)
 
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (algorithmic bytes per launch / mean launch time)
+    # roofline of the dominant kernel: the method's algorithmic bytes (1.25 B
+    # packed in + 1 B out per input sample) of the samples one launch covers,
+    # over that kernel's mean launch duration (CUDA events on its stream)
     N1 = plan.info.fft_n1
+    tc = args.precision != "fp32"
     # bytes of intermediate per input sample (FP32 pairs; FP16 pairs in the FP16 form)
     inter = (N1 // 2 + 1) / N1 * (4.0 if args.precision == "fp16" else 8.0)
     spl = wl.samples_per_step
-    bytes_per_sample = {"phase1": 1.25 + inter, "phase2": inter + 1.0}
-    dom = max(("phase1", "phase2"), key=lambda k: stage_ms[k])
+    # bytes each kernel itself must move per input sample (with the intermediates)
+    kernel_bytes = {"phase1": (2.0 if tc else 1.25) + inter, "phase2": inter + 1.0, "unpack": 1.25 + 2.0}
+    stages = [k for k in ("phase1", "phase2", "unpack") if stage_ms.get(k, 0.0) > 0.0]
+    dom = max(stages, key=lambda k: stage_ms[k])
     slabs = max(int(plan.info.slabs_per_chunk), 1)
-    kernel_ms_per_step = stage_ms[dom] / max(calls, 1)       # all slab launches of one step
-    launch_ms = kernel_ms_per_step / slabs                   # one launch = one slab
+    launches = 1 if dom == "unpack" else slabs             # the unpack runs once per call
+    kernel_ms_per_step = stage_ms[dom] / max(calls, 1)
+    launch_ms = kernel_ms_per_step / launches
     peak, peak_kind = _peaks()
-    # algorithmic bytes of one launch (its slab's samples) / its mean duration
-    achieved = bytes_per_sample[dom] * (spl / slabs) / (launch_ms / 1e3) / 1e9
+    samples_per_launch = spl / launches
+    achieved = 2.25 * samples_per_launch / (launch_ms / 1e3) / 1e9
+    achieved_kernel = kernel_bytes[dom] * samples_per_launch / (launch_ms / 1e3) / 1e9
     N2 = plan.info.fft_n2
-    half = 1 if args.precision == "fp16" else 0
     R_tc = N1 // 8
-    kname = {"phase1": (f"k_phase1<{wl.n_taps},{N1},{min(512 // N1, N2)},0>" if args.precision == "fp32"
+    kname = {"phase1": (f"k_phase1<{wl.n_taps},{N1},{min(512 // N1, N2)},0>" if not tc
                         else f"k_phase1_tc<{R_tc},{wl.n_taps},{1 if args.precision == 'fp16' else 2}>"),
              "phase2": ("k_phase2w" if N2 == 1024 else f"k_phase2<{N2}>")
-             + ("" if args.precision != "fp16" else "<half>")}[dom]
+             + ("" if args.precision != "fp16" else "<half>"),
+             "unpack": "k_unpack_cols"}[dom]
     tr = NCU_TRAFFIC.get(kname)
     # scaled from the captured launch to this launch by its input samples
     # (the kernels' DRAM traffic grows in proportion to the samples processed)
-    traffic = (tr["bytes_per_sample"] * spl / slabs if tr and tr.get("src") == _src_hash(kname.split("<")[0])
-               else None)
+    traffic = (tr["bytes_per_sample"] * samples_per_launch
+               if tr and tr.get("src") == _src_hash(kname.split("<")[0]) else None)
     step_ms = ms_max / args.steps
     path_alg = 2.25 * spl / (step_ms / 1e3) / 1e9
     path_all = (2.25 + 2 * inter) * spl / (step_ms / 1e3) / 1e9
@@ -678,17 +738,19 @@ def main(argv=None):
                          f"{plan.info.out_bytes >> 20} MiB out per step"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes_per_sample": bytes_per_sample[dom],
-                     "launch_ms": launch_ms, "launches_per_step": slabs,
-                     "slab_spectra": int(plan.info.slab_spectra)},
+                     "algorithmic_bytes_per_sample": 2.25, "samples_per_launch": samples_per_launch,
+                     "launch_ms": launch_ms, "launches_per_step": launches,
+                     "with_intermediates": {"bytes_per_sample": kernel_bytes[dom], "achieved": achieved_kernel,
+                                            "frac": achieved_kernel / peak}},
         "path": {"stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()},
                  "algorithmic_GBps": path_alg, "frac_algorithmic": path_alg / peak,
                  "with_intermediates_GBps": path_all, "frac_with_intermediates": path_all / peak,
                  "bytes_per_sample": {"algorithmic": 2.25, "with_intermediates": 2.25 + 2 * inter}},
         "e2e": e2e,
-        "gpu_launches": (2 + 2 * slabs) * args.steps,
+        "gpu_launches": (2 + 2 * slabs + (1 if tc else 0)) * args.steps,
         "forms": forms,
         "clocks": clocks.summary(w0, w1),
+        **extra,
     }
     if not args.no_cpu and ws == 1:
         line["cpu_baseline"] = cpu_baseline(wl)

@@ -52,7 +52,8 @@ typedef enum {
     FENGINE_EBUSY = 5,        /* no free slot / over the memory budget */
     FENGINE_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
     FENGINE_EUNSUPPORTED = 7, /* valid request this build does not implement */
-    FENGINE_EDELAY = 8        /* a coarse delay of this call leaves [min_delay, max_delay] */
+    FENGINE_EDELAY = 8,       /* a coarse delay of this call leaves [min_delay, max_delay] */
+    FENGINE_EIO = 9           /* a host file could not be written */
 } fengine_status;
 
 /* Precision forms. The reduced-precision forms run the unpack, the coarse
@@ -244,6 +245,20 @@ fengine_status fengine_autotune(const fengine_config *cfg, void *cuda_stream, in
                                 fengine_config *tuned, fengine_tune_entry *entries, int32_t max_entries,
                                 int32_t *n_entries);
 
+/* fengine_autotune with its pick kept in a JSON Lines file (one object per
+ * line: device name, SM count, ABI version, the shape fields of cfg,
+ * precision, and the chosen fft_n1, slab_spectra, ms_per_call). A line whose
+ * key fields all match cfg on the current device, and whose split still makes
+ * a valid plan, is returned without timing anything (*from_cache = 1);
+ * otherwise the split is tuned as fengine_autotune does and the file is
+ * rewritten with that line replaced or added (written beside the file and
+ * renamed over it). cache_path: host path, created if missing; lines of other
+ * configurations are kept. Returns fengine_autotune's errors, FENGINE_EINVAL
+ * for a NULL or empty path, FENGINE_EIO if the file cannot be written (the
+ * tuned split is still returned in *tuned). */
+fengine_status fengine_autotune_cached(const fengine_config *cfg, void *cuda_stream, int32_t calls,
+                                       const char *cache_path, fengine_config *tuned, int32_t *from_cache);
+
 /* ---- batching: many independent plans per call (uneven streams with
  * different channel counts, tap counts and chunk lengths; engines are
  * independent, Sec. 2.1 last paragraph) ---- */
@@ -289,7 +304,9 @@ typedef struct {
 typedef struct {
     int64_t admitted, completed, deferred, failed, queued;
     int64_t bytes_in_use, peak_bytes;
-    double latency_p50_us, latency_p99_us, latency_max_us;   /* submit -> output on host */
+    double latency_p50_us, latency_p99_us, latency_max_us;   /* submit -> output on host; the
+                                                               percentiles from a histogram of
+                                                               1.1 %-wide bins, the maximum exact */
 } fengine_service_stats;
 
 /* Start the service on the current device: a dispatcher thread admits queued
@@ -328,6 +345,73 @@ fengine_status fengine_service_get_stats(fengine_service_t svc, fengine_service_
 
 /* Finish every queued request, then stop. */
 fengine_status fengine_service_destroy(fengine_service_t svc);
+
+/* ---- host ingest: digitiser heaps -> chunks on the device (Sec. 3.1-3.2) ----
+ * A digitiser sends each polarisation as heaps of FENGINE_HEAP_SAMPLES
+ * samples (FENGINE_HEAP_BYTES packed bytes) with a timestamp; heaps arrive
+ * per polarisation, possibly out of order, some not at all. An ingest object
+ * takes such heaps in arrival order into a ring of pinned host memory (one
+ * host write per byte: the copy a NIC's DMA would make), moves the ring to
+ * the device in arrival order on its own CUDA stream as the heaps come
+ * (overlapping the processing of earlier chunks), and assembles them there:
+ * a kernel places each heap at its position in the chunk of its timestamp
+ * ([antenna][pol][5L/4] bytes) and sets the chunk's received-heap flag.
+ * A chunk of every stream (both polarisations of every antenna, paired by
+ * timestamp) is emitted, in timestamp order, once all its heaps are in or
+ * once heaps of a chunk reorder_chunks later have arrived (or on a flush);
+ * its missing heaps are zero-filled and flagged, and it goes through
+ * fengine_process_chunk with those flags (Sec. 3.7: spectra whose window
+ * touches a missing heap are unusable, their output heaps flagged). */
+#define FENGINE_HEAP_BYTES (FENGINE_HEAP_SAMPLES * 10 / 8)
+
+typedef struct fengine_ingest_s *fengine_ingest_t;
+
+typedef struct {
+    int32_t antenna, pol;
+    int64_t timestamp;          /* first sample of the heap, a multiple of FENGINE_HEAP_SAMPLES */
+    const uint8_t *payload;     /* host, FENGINE_HEAP_BYTES packed samples (10-bit MSB first) */
+} fengine_heap;
+
+typedef struct {
+    int64_t heaps_accepted;     /* placed in the ring */
+    int64_t heaps_late;         /* timestamp of a chunk already emitted (dropped) */
+    int64_t heaps_duplicate;    /* a second copy of a heap already in its chunk (dropped) */
+    int64_t heaps_outside;      /* timestamp before the first chunk (dropped) */
+    int64_t heaps_missing;      /* heaps absent from emitted chunks (zero-filled, flagged) */
+    int64_t chunks_emitted;
+    int64_t bytes_to_device;    /* ring bytes copied host -> device */
+} fengine_ingest_stats;
+
+/* plan: the chunks' plan (chunk_samples and first_sample multiples of
+ * FENGINE_HEAP_SAMPLES); the ingest does not own it and must be destroyed
+ * first. first_sample: timestamp of the first chunk (the plan's next
+ * first_sample). ring_heaps: heap slots of the host and device rings
+ * (>= 1); reorder_chunks (0..3): how many chunks past the oldest pending one
+ * may receive heaps before the oldest is emitted with what it has. The
+ * device holds reorder_chunks + 1 assembly chunks. */
+fengine_status fengine_ingest_create(fengine_plan_t plan, int64_t first_sample, int32_t ring_heaps,
+                                     int32_t reorder_chunks, fengine_ingest_t *out);
+fengine_status fengine_ingest_destroy(fengine_ingest_t ing);
+
+/* Take heaps[0 .. n) in order into the ring; *accepted (host out) = how many
+ * were consumed (placed or dropped and counted). It stops early, with
+ * FENGINE_EBUSY, at a heap for a chunk beyond the reorder window or when the
+ * ring is full: call fengine_ingest_poll, then push the rest. FENGINE_EINVAL
+ * for a bad antenna, pol, unaligned timestamp or NULL payload (that heap is
+ * not consumed). */
+fengine_status fengine_ingest_push(fengine_ingest_t ing, const fengine_heap *heaps, int32_t n, int32_t *accepted);
+
+/* Move the heaps pushed so far to the device and assemble them; then, if the
+ * oldest pending chunk is due (complete, past the reorder window, or flush !=
+ * 0), emit it: zero-fill and flag its missing heaps and run
+ * fengine_process_chunk on cuda_stream into d_out / d_heap_flags (as
+ * fengine_process_chunk; d_heap_flags may be NULL). *emitted = 1 and
+ * *first_sample (its timestamp) / *first_spectrum set when a chunk was
+ * emitted, *emitted = 0 otherwise (d_out untouched). One chunk per call. */
+fengine_status fengine_ingest_poll(fengine_ingest_t ing, void *cuda_stream, int32_t flush, int8_t *d_out,
+                                   uint8_t *d_heap_flags, int32_t *emitted, int64_t *first_sample,
+                                   int64_t *first_spectrum);
+fengine_status fengine_ingest_get_stats(fengine_ingest_t ing, fengine_ingest_stats *out);
 
 /* ---- no-allocation variant (the paper has no counterpart) ----
  * For callers that cannot allocate device memory: a process whose device
@@ -382,10 +466,12 @@ fengine_status fengine_process_chunk_noalloc(const fengine_noalloc_args *args, c
 /* Per-stage device timing, a profiling aid. While enabled, every
  * fengine_process_chunk records CUDA events on its stream between its
  * kernels. fengine_stage_times waits for those events, writes the summed
- * milliseconds per stage to ms[0..3] = {delay table, phase 1 (unpack + FIR +
- * first FFT stage), phase 2 (second FFT stage + delay/gain + requantise +
- * corner turn), history tail update}, the number of timed calls to *calls,
- * and starts a new accumulation. Disabled by default. */
+ * milliseconds per stage to ms[0..4] = {delay table, phase 1 (FIR + first
+ * FFT stage; in the FP32 form also the unpack), phase 2 (second FFT stage +
+ * delay/gain + requantise + corner turn), history tail update, column unpack
+ * (tensor-core forms; 0 in the FP32 form)}, the number of timed calls to
+ * *calls, and starts a new accumulation. ms holds 5 floats. Disabled by
+ * default. */
 fengine_status fengine_set_profiling(fengine_plan_t plan, int32_t enable);
 fengine_status fengine_stage_times(fengine_plan_t plan, float *ms, int32_t *calls);
 

@@ -6,6 +6,9 @@
 // input through the public entry points.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
+#include <string>
 #include <vector>
 
 #include "../../include/fengine.h"
@@ -115,4 +118,141 @@ extern "C" fengine_status fengine_autotune(const fengine_config *cfg, void *cuda
     if (best < 0.0f) return last != FENGINE_OK ? last : FENGINE_EUNSUPPORTED;
     *tuned = best_cfg;
     return result;
+}
+
+// ---- the tuner's pick cached in a JSON Lines file --------------------------
+// One JSON object per line; a line applies to a configuration when every key
+// field matches (device name and SM count, ABI version, the shape fields of
+// fengine_config and the precision). Lines this code does not recognise are
+// kept as they are when the file is rewritten.
+namespace {
+
+const char *kCacheInts[] = {"sms", "abi", "n_antennas", "n_channels", "n_taps", "chunk_samples",
+                            "spectra_per_heap", "max_delay_samples", "min_delay_samples", "precision"};
+constexpr int kCacheNInts = 10;
+
+struct CacheKey {
+    std::string device;
+    long long v[kCacheNInts];
+};
+
+bool json_int(const std::string &line, const char *name, long long *out) {
+    const std::string pat = std::string("\"") + name + "\":";
+    const size_t at = line.find(pat);
+    if (at == std::string::npos) return false;
+    const char *p = line.c_str() + at + pat.size();
+    char *end = nullptr;
+    const long long v = std::strtoll(p, &end, 10);
+    if (end == p) return false;
+    *out = v;
+    return true;
+}
+
+bool json_str(const std::string &line, const char *name, std::string *out) {
+    const std::string pat = std::string("\"") + name + "\": \"";
+    const size_t at = line.find(pat);
+    if (at == std::string::npos) return false;
+    const size_t b = at + pat.size(), e = line.find('"', b);
+    if (e == std::string::npos) return false;
+    *out = line.substr(b, e - b);
+    return true;
+}
+
+bool cache_key(const fengine_config *cfg, CacheKey *k) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+    k->device = prop.name;
+    for (char &ch : k->device)
+        if (ch == '"' || ch == '\\' || (unsigned char)ch < 0x20) ch = '_';
+    const long long vals[kCacheNInts] = {prop.multiProcessorCount, fengine_abi_version(), cfg->n_antennas,
+                                         cfg->n_channels, cfg->n_taps, (long long)cfg->chunk_samples,
+                                         cfg->spectra_per_heap, (long long)cfg->max_delay_samples,
+                                         (long long)cfg->min_delay_samples, (long long)cfg->precision};
+    for (int i = 0; i < kCacheNInts; ++i) k->v[i] = vals[i];
+    return true;
+}
+
+bool line_matches(const std::string &line, const CacheKey &k) {
+    std::string dev;
+    if (!json_str(line, "device", &dev) || dev != k.device) return false;
+    for (int i = 0; i < kCacheNInts; ++i) {
+        long long v;
+        if (!json_int(line, kCacheInts[i], &v) || v != k.v[i]) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" fengine_status fengine_autotune_cached(const fengine_config *cfg, void *cuda_stream, int32_t calls,
+                                                  const char *cache_path, fengine_config *tuned,
+                                                  int32_t *from_cache) {
+    if (!cfg || !tuned || !cache_path || !*cache_path || calls < 1) return FENGINE_EINVAL;
+    if (from_cache) *from_cache = 0;
+    CacheKey key;
+    if (!cache_key(cfg, &key)) return FENGINE_ECUDA;
+    std::vector<std::string> lines;
+    if (FILE *f = std::fopen(cache_path, "r")) {
+        char buf[1024];
+        std::string cur;
+        while (std::fgets(buf, sizeof buf, f)) {
+            cur += buf;
+            if (!cur.empty() && cur.back() == '\n') {
+                cur.pop_back();
+                lines.push_back(cur);
+                cur.clear();
+            }
+        }
+        if (!cur.empty()) lines.push_back(cur);
+        std::fclose(f);
+    }
+    for (const std::string &line : lines) {
+        long long n1, sl;
+        if (!line_matches(line, key) || !json_int(line, "fft_n1", &n1) || !json_int(line, "slab_spectra", &sl))
+            continue;
+        fengine_config c = *cfg;
+        c.fft_n1 = (int32_t)n1;
+        c.slab_spectra = (int32_t)sl;
+        // a cached split must still make a valid plan (the library may have
+        // changed the set of splits it supports)
+        fengine_plan_t plan = nullptr;
+        if (fengine_plan_create(&c, &plan) != FENGINE_OK) continue;
+        fengine_plan_destroy(plan);
+        *tuned = c;
+        if (from_cache) *from_cache = 1;
+        return FENGINE_OK;
+    }
+    fengine_tune_entry entries[64];
+    int32_t n = 0;
+    const fengine_status s = fengine_autotune(cfg, cuda_stream, calls, tuned, entries, 64, &n);
+    if (s != FENGINE_OK) return s;
+    float ms = 0.0f;
+    for (int i = 0; i < n; ++i)
+        if (entries[i].fft_n1 == tuned->fft_n1 && entries[i].slab_spectra == tuned->slab_spectra) ms = entries[i].ms_per_call;
+    char rec[1024];
+    int len = std::snprintf(rec, sizeof rec, "{\"device\": \"%s\"", key.device.c_str());
+    for (int i = 0; i < kCacheNInts && len > 0 && len < (int)sizeof rec; ++i)
+        len += std::snprintf(rec + len, sizeof rec - len, ", \"%s\": %lld", kCacheInts[i], key.v[i]);
+    if (len > 0 && len < (int)sizeof rec)
+        len += std::snprintf(rec + len, sizeof rec - len, ", \"fft_n1\": %d, \"slab_spectra\": %d, \"ms_per_call\": %.4f}",
+                             tuned->fft_n1, tuned->slab_spectra, (double)ms);
+    if (len <= 0 || len >= (int)sizeof rec) return FENGINE_OK;   // the pick stands; nothing cached
+    std::vector<std::string> keep;
+    for (const std::string &line : lines)
+        if (!line_matches(line, key)) keep.push_back(line);
+    keep.push_back(rec);
+    // write beside the file and rename over it, so a reader sees the old or
+    // the new file, never a partial one
+    const std::string tmp = std::string(cache_path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) return FENGINE_EIO;
+    bool ok = true;
+    for (const std::string &line : keep) ok = ok && std::fprintf(f, "%s\n", line.c_str()) > 0;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), cache_path) != 0) {
+        std::remove(tmp.c_str());
+        return FENGINE_EIO;
+    }
+    return FENGINE_OK;
 }

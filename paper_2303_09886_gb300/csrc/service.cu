@@ -14,6 +14,7 @@
 // waits are bounded; nothing here waits on the device from device code.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdint>
 #include <cstring>
@@ -58,6 +59,15 @@ struct Request {
     bool deferred = false;
 };
 
+constexpr int kLatBinsPerOctave = 64;
+constexpr int kLatBins = 40 * kLatBinsPerOctave;   // 1 us .. 2^40 us
+
+int latency_bin(double us) {
+    if (!(us >= 1.0)) return 0;
+    const int b = (int)std::floor(std::log2(us) * kLatBinsPerOctave);
+    return std::min(b, kLatBins - 1);
+}
+
 }  // namespace
 
 struct fengine_service_s {
@@ -67,7 +77,11 @@ struct fengine_service_s {
     std::map<fengine_plan_t, int> plan_stream;
     std::deque<std::shared_ptr<Request>> queue;
     std::map<int64_t, std::shared_ptr<Request>> all;
-    std::vector<double> latencies_us;
+    // completed-request latencies as a histogram of fixed size: bin b holds
+    // latencies in [2^(b/kLatBinsPerOctave), 2^((b+1)/kLatBinsPerOctave)) us
+    // (1.1 % wide), so a long-lived service keeps constant memory
+    std::vector<int64_t> lat_hist = std::vector<int64_t>(kLatBins, 0);
+    double lat_max_us = 0.0;
     int64_t next_ticket = 1;
     int64_t admitted = 0, completed = 0, deferred = 0, failed = 0;
     std::mutex mu;
@@ -139,8 +153,9 @@ void dispatcher(fengine_service_s *s) {
                 s->in_use -= (int64_t)(r.in_bytes + r.out_bytes);
                 s->stream_busy[r.stream]--;
                 s->completed++;
-                s->latencies_us.push_back(
-                    std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count());
+                const double us = std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count();
+                s->lat_hist[latency_bin(us)]++;
+                s->lat_max_us = std::max(s->lat_max_us, us);
                 retired = true;
             }
         }
@@ -377,12 +392,19 @@ fengine_status fengine_service_wait(fengine_service_t s, int64_t ticket, int32_t
 fengine_status fengine_service_get_stats(fengine_service_t s, fengine_service_stats *out) {
     if (!s || !out) return FENGINE_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
-    std::vector<double> lat = s->latencies_us;
-    std::sort(lat.begin(), lat.end());
+    int64_t n_lat = 0;
+    for (int64_t c : s->lat_hist) n_lat += c;
+    // q-quantile: the geometric centre of the bin holding the ceil(q n)-th
+    // smallest latency (relative resolution 1.1 %), capped at the maximum
     auto pct = [&](double q) {
-        if (lat.empty()) return 0.0;
-        const size_t i = (size_t)std::min<double>((double)lat.size() - 1, q * (double)(lat.size() - 1) + 0.5);
-        return lat[i];
+        if (n_lat == 0) return 0.0;
+        const int64_t rank = std::max<int64_t>(1, (int64_t)std::ceil(q * (double)n_lat));
+        int64_t acc = 0;
+        for (int b = 0; b < kLatBins; ++b) {
+            acc += s->lat_hist[b];
+            if (acc >= rank) return std::min(s->lat_max_us, std::exp2(((double)b + 0.5) / kLatBinsPerOctave));
+        }
+        return s->lat_max_us;
     };
     out->admitted = s->admitted;
     out->completed = s->completed;
@@ -393,7 +415,7 @@ fengine_status fengine_service_get_stats(fengine_service_t s, fengine_service_st
     out->peak_bytes = s->peak;
     out->latency_p50_us = pct(0.50);
     out->latency_p99_us = pct(0.99);
-    out->latency_max_us = lat.empty() ? 0.0 : lat.back();
+    out->latency_max_us = s->lat_max_us;
     return FENGINE_OK;
 }
 

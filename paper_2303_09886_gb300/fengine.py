@@ -22,7 +22,7 @@ HEAP_SAMPLES = 4096        # samples per digitiser heap (lost-data flags)
 FAR_PAST = -(2 ** 62)      # t_apply of a model or gain set that applies at once
 STATUS = {0: "FENGINE_OK", 1: "FENGINE_EINVAL", 2: "FENGINE_ENOMEM", 3: "FENGINE_ECUDA",
           4: "FENGINE_ESEQ", 5: "FENGINE_EBUSY", 6: "FENGINE_ETIMEOUT",
-          7: "FENGINE_EUNSUPPORTED", 8: "FENGINE_EDELAY"}
+          7: "FENGINE_EUNSUPPORTED", 8: "FENGINE_EDELAY", 9: "FENGINE_EIO"}
 
 # every symbol include/fengine.h declares
 EXPORTS = ("fengine_strerror", "fengine_last_error", "fengine_abi_version", "fengine_quantise",
@@ -33,7 +33,8 @@ EXPORTS = ("fengine_strerror", "fengine_last_error", "fengine_abi_version", "fen
            "fengine_service_create", "fengine_service_submit", "fengine_service_set_delay",
            "fengine_service_set_gains", "fengine_service_wait", "fengine_service_get_stats",
            "fengine_service_destroy", "fengine_process_chunk_noalloc", "fengine_autotune",
-           "fengine_device_status")
+           "fengine_autotune_cached", "fengine_device_status", "fengine_ingest_create",
+           "fengine_ingest_destroy", "fengine_ingest_push", "fengine_ingest_poll", "fengine_ingest_get_stats")
 
 
 class FEngineError(RuntimeError):
@@ -115,7 +116,9 @@ def load(path: str = LIB_PATH):
     lib.fengine_batch_process.argtypes = [vp, vp, ctypes.POINTER(ChunkDesc), i32, ctypes.POINTER(i64)]
     lib.fengine_autotune.argtypes = [ctypes.POINTER(Config), vp, i32, ctypes.POINTER(Config),
                                      ctypes.POINTER(TuneEntry), i32, ctypes.POINTER(i32)]
-    for name in ("fengine_autotune", "fengine_default_weights", "fengine_plan_create", "fengine_plan_destroy",
+    lib.fengine_autotune_cached.argtypes = [ctypes.POINTER(Config), vp, i32, ctypes.c_char_p,
+                                            ctypes.POINTER(Config), ctypes.POINTER(i32)]
+    for name in ("fengine_autotune", "fengine_autotune_cached", "fengine_default_weights", "fengine_plan_create", "fengine_plan_destroy",
                  "fengine_get_info", "fengine_set_delay", "fengine_set_gains", "fengine_reset",
                  "fengine_process_chunk", "fengine_set_profiling", "fengine_stage_times",
                  "fengine_batch_create", "fengine_batch_destroy", "fengine_batch_process",
@@ -211,14 +214,14 @@ class Plan:
     def reset(self):
         _check(load().fengine_reset(self._h))
 
-    STAGES = ("delay_table", "phase1", "phase2", "tail")
+    STAGES = ("delay_table", "phase1", "phase2", "tail", "unpack")
 
     def set_profiling(self, enable: bool = True):
         _check(load().fengine_set_profiling(self._h, 1 if enable else 0))
 
     def stage_times(self):
         """Summed device milliseconds per stage since the last call, and the call count."""
-        ms = (ctypes.c_float * 4)()
+        ms = (ctypes.c_float * 5)()
         calls = ctypes.c_int32()
         _check(load().fengine_stage_times(self._h, ms, ctypes.byref(calls)))
         return dict(zip(self.STAGES, list(ms))), calls.value
@@ -269,6 +272,23 @@ def autotune(n_antennas: int, n_channels: int, n_taps: int, chunk_samples: int, 
                                    entries, 32, ctypes.byref(n)))
     table = [(entries[i].fft_n1, entries[i].slab_spectra, float(entries[i].ms_per_call)) for i in range(n.value)]
     return {"fft_n1": tuned.fft_n1, "slab_spectra": tuned.slab_spectra}, table
+
+
+def autotune_cached(cache_path: str, n_antennas: int, n_channels: int, n_taps: int, chunk_samples: int,
+                    spectra_per_heap: int = 0, max_delay_samples: int = 0, precision: int = FP32,
+                    calls: int = 5, stream=None):
+    """fengine_autotune_cached: the split stored in the JSON Lines file
+    `cache_path` for this configuration and device, else a fresh tuning that
+    is then stored. Returns ({"fft_n1": .., "slab_spectra": ..}, from_cache)."""
+    import torch
+    cfg = Config(n_antennas, 2, n_channels, n_taps, chunk_samples, spectra_per_heap, precision,
+                 max_delay_samples, None, 0, 0, 0)
+    tuned = Config()
+    hit = ctypes.c_int32()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(load().fengine_autotune_cached(ctypes.byref(cfg), ctypes.c_void_p(s.cuda_stream), calls,
+                                          os.fsencode(cache_path), ctypes.byref(tuned), ctypes.byref(hit)))
+    return {"fft_n1": tuned.fft_n1, "slab_spectra": tuned.slab_spectra}, bool(hit.value)
 
 
 class Batch:
@@ -404,6 +424,88 @@ class Service:
             _check(load().fengine_service_destroy(self._h))
             self._h = None
             self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+HEAP_BYTES = HEAP_SAMPLES * 10 // 8
+
+
+class Heap(ctypes.Structure):
+    _fields_ = [("antenna", ctypes.c_int32), ("pol", ctypes.c_int32), ("timestamp", ctypes.c_int64),
+                ("payload", ctypes.c_void_p)]
+
+
+class IngestStats(ctypes.Structure):
+    _fields_ = [("heaps_accepted", ctypes.c_int64), ("heaps_late", ctypes.c_int64),
+                ("heaps_duplicate", ctypes.c_int64), ("heaps_outside", ctypes.c_int64),
+                ("heaps_missing", ctypes.c_int64), ("chunks_emitted", ctypes.c_int64),
+                ("bytes_to_device", ctypes.c_int64)]
+
+
+def _ingest_signatures(lib):
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.fengine_ingest_create.argtypes = [vp, i64, i32, i32, ctypes.POINTER(vp)]
+    lib.fengine_ingest_destroy.argtypes = [vp]
+    lib.fengine_ingest_push.argtypes = [vp, ctypes.POINTER(Heap), i32, ctypes.POINTER(i32)]
+    lib.fengine_ingest_poll.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                        ctypes.POINTER(i64)]
+    lib.fengine_ingest_get_stats.argtypes = [vp, ctypes.POINTER(IngestStats)]
+    for name in ("fengine_ingest_create", "fengine_ingest_destroy", "fengine_ingest_push", "fengine_ingest_poll",
+                 "fengine_ingest_get_stats"):
+        getattr(lib, name).restype = ctypes.c_int
+
+
+class Ingest:
+    """Digitiser heaps in arrival order -> chunks on the device (fengine_ingest_*)."""
+
+    def __init__(self, plan: Plan, first_sample: int = 0, ring_heaps: int = 4096, reorder_chunks: int = 1):
+        lib = load()
+        _ingest_signatures(lib)
+        h = ctypes.c_void_p()
+        _check(lib.fengine_ingest_create(plan._h, first_sample, ring_heaps, reorder_chunks, ctypes.byref(h)))
+        self._h = h
+        self.plan = plan
+
+    def push(self, heaps) -> int:
+        """heaps: sequence of (antenna, pol, timestamp, payload uint8 array of HEAP_BYTES).
+        Returns how many were consumed; fewer than given means the ring or the
+        reorder window is full (poll, then push the rest)."""
+        arr = (Heap * max(len(heaps), 1))()
+        for i, (a, p, ts, payload) in enumerate(heaps):
+            if payload.dtype != np.uint8 or payload.nbytes != HEAP_BYTES or not payload.flags["C_CONTIGUOUS"]:
+                raise ValueError("payload must be a contiguous uint8 array of HEAP_BYTES")
+            arr[i] = Heap(a, p, ts, payload.ctypes.data)
+        acc = ctypes.c_int32()
+        st = load().fengine_ingest_push(self._h, arr, len(heaps), ctypes.byref(acc))
+        if st not in (0, 5):          # FENGINE_EBUSY: stopped early, not an error here
+            _check(st)
+        return acc.value
+
+    def poll(self, out, heap_flags=None, stream=None, flush: bool = False):
+        """Send pushed heaps to the device; emit the oldest chunk if due.
+        Returns (emitted, first_sample, first_spectrum)."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        em, t0, m0 = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().fengine_ingest_poll(self._h, ctypes.c_void_p(s.cuda_stream), int(flush), out.data_ptr(),
+                                          heap_flags.data_ptr() if heap_flags is not None else None,
+                                          ctypes.byref(em), ctypes.byref(t0), ctypes.byref(m0)))
+        return bool(em.value), t0.value, m0.value
+
+    def stats(self) -> dict:
+        s = IngestStats()
+        _check(load().fengine_ingest_get_stats(self._h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in IngestStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().fengine_ingest_destroy(self._h))
+            self._h = None
 
     def __del__(self):
         try:

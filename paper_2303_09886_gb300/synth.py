@@ -47,6 +47,19 @@ def digitiser_samples(seed: int, n: int, sigma: float, tones=(), chirp=None, sta
     return out
 
 
+def dithered_tone(seed: int, n: int, freq: float, amplitude: float, phase: float = 0.0,
+                  start: int = 0) -> np.ndarray:
+    """int16 samples [start, start + n) of one tone quantised to 10 bits with
+    a uniform dither of one LSB (round(x + u), u ~ U(-1/2, 1/2)): the
+    quantisation error then has zero mean whatever the tone, as in the
+    paper's FFT-precision experiment (Sec. 3.5) and its channel-response
+    measurement (Sec. 5.2)."""
+    g = rng(seed)
+    i = np.arange(start, start + n, dtype=np.float64)
+    x = amplitude * np.cos(2.0 * np.pi * np.mod(freq * i, 1.0) + phase) + g.uniform(-0.5, 0.5, n)
+    return np.clip(np.rint(x), SAMPLE_MIN, SAMPLE_MAX).astype(np.int16)
+
+
 def pack10(samples: np.ndarray) -> np.ndarray:
     """Pack int samples in [-512, 511] into the 10-bit MSB-first byte stream.
 

@@ -135,3 +135,35 @@ def test_batch_and_service_refuse_bad_arguments_before_any_device_call(lib):
     assert lib.fengine_service_wait(None, 0, 10, ctypes.byref(lat)) == EINVAL
     assert lib.fengine_service_get_stats(None, None) == EINVAL
     assert lib.fengine_service_destroy(None) == EINVAL
+
+
+def test_ingest_and_tune_cache_refuse_bad_arguments_before_any_device_call(lib, tmp_path):
+    EINVAL = 1
+    vp = ctypes.c_void_p
+    h = vp()
+    fengine._ingest_signatures(lib)
+    # no plan, bad ring size or reorder depth, no out pointer
+    assert lib.fengine_ingest_create(None, 0, 64, 1, ctypes.byref(h)) == EINVAL
+    for ring, reorder in ((0, 1), (64, -1), (64, 4)):
+        assert lib.fengine_ingest_create(vp(1), 0, ring, reorder, ctypes.byref(h)) == EINVAL
+    assert lib.fengine_ingest_destroy(None) == EINVAL
+    acc = ctypes.c_int32()
+    assert lib.fengine_ingest_push(None, None, 0, ctypes.byref(acc)) == EINVAL
+    em, t0, m0 = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    assert lib.fengine_ingest_poll(None, None, 0, None, None, ctypes.byref(em), ctypes.byref(t0),
+                                   ctypes.byref(m0)) == EINVAL
+    assert lib.fengine_ingest_get_stats(None, None) == EINVAL
+    # the autotune cache: a configuration, a path and an out pointer
+    c = fengine.Config(n_antennas=1, n_pols=2, n_channels=1024, n_taps=16, chunk_samples=2048 * 8,
+                       spectra_per_heap=0, precision=0, max_delay_samples=0, weights=None, fft_n1=0,
+                       slab_spectra=0, min_delay_samples=0)
+    tuned, hit = fengine.Config(), ctypes.c_int32()
+    path = str(tmp_path / "tune.jsonl").encode()
+    assert lib.fengine_autotune_cached(None, None, 3, path, ctypes.byref(tuned), ctypes.byref(hit)) == EINVAL
+    assert lib.fengine_autotune_cached(ctypes.byref(c), None, 3, None, ctypes.byref(tuned),
+                                       ctypes.byref(hit)) == EINVAL
+    assert lib.fengine_autotune_cached(ctypes.byref(c), None, 3, b"", ctypes.byref(tuned),
+                                       ctypes.byref(hit)) == EINVAL
+    assert lib.fengine_autotune_cached(ctypes.byref(c), None, 0, path, ctypes.byref(tuned),
+                                       ctypes.byref(hit)) == EINVAL
+    assert not (tmp_path / "tune.jsonl").exists()
