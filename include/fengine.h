@@ -358,7 +358,8 @@ fengine_status fengine_service_destroy(fengine_service_t svc);
  * ([antenna][pol][5L/4] bytes) and sets the chunk's received-heap flag.
  * A chunk of every stream (both polarisations of every antenna, paired by
  * timestamp) is emitted, in timestamp order, once all its heaps are in or
- * once heaps of a chunk reorder_chunks later have arrived (or on a flush);
+ * once a heap of a chunk more than reorder_chunks past it arrives (or on a
+ * flush);
  * its missing heaps are zero-filled and flagged, and it goes through
  * fengine_process_chunk with those flags (Sec. 3.7: spectra whose window
  * touches a missing heap are unusable, their output heaps flagged). */
@@ -387,8 +388,9 @@ typedef struct {
  * first. first_sample: timestamp of the first chunk (the plan's next
  * first_sample). ring_heaps: heap slots of the host and device rings
  * (>= 1); reorder_chunks (0..3): how many chunks past the oldest pending one
- * may receive heaps before the oldest is emitted with what it has. The
- * device holds reorder_chunks + 1 assembly chunks. */
+ * may receive heaps while it waits; a heap of a later chunk makes the oldest
+ * due (emitted with what it has). The device holds reorder_chunks + 1
+ * assembly chunks. */
 fengine_status fengine_ingest_create(fengine_plan_t plan, int64_t first_sample, int32_t ring_heaps,
                                      int32_t reorder_chunks, fengine_ingest_t *out);
 fengine_status fengine_ingest_destroy(fengine_ingest_t ing);
@@ -402,8 +404,8 @@ fengine_status fengine_ingest_destroy(fengine_ingest_t ing);
 fengine_status fengine_ingest_push(fengine_ingest_t ing, const fengine_heap *heaps, int32_t n, int32_t *accepted);
 
 /* Move the heaps pushed so far to the device and assemble them; then, if the
- * oldest pending chunk is due (complete, past the reorder window, or flush !=
- * 0), emit it: zero-fill and flag its missing heaps and run
+ * oldest pending chunk is due (complete, a push stopped at a heap past the
+ * reorder window, or flush != 0), emit it: zero-fill and flag its missing heaps and run
  * fengine_process_chunk on cuda_stream into d_out / d_heap_flags (as
  * fengine_process_chunk; d_heap_flags may be NULL). *emitted = 1 and
  * *first_sample (its timestamp) / *first_spectrum set when a chunk was

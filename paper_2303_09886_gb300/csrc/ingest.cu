@@ -76,7 +76,7 @@ struct fengine_ingest_s {
     uint8_t *d_chunks = nullptr, *d_valid = nullptr;
     std::vector<std::vector<uint8_t>> got;   // per slot: received flags (host copy)
     std::vector<long long> count;            // per slot: heaps received
-    long long next_emit = 0, max_seen = -1;
+    long long next_emit = 0;
     bool blocked = false;                    // a push stopped at a heap past the reorder window
     cudaStream_t cs = nullptr;
     cudaEvent_t ev_scat = nullptr, ev_done = nullptr;
@@ -252,7 +252,6 @@ extern "C" fengine_status fengine_ingest_push(fengine_ingest_t g, const fengine_
         g->head++;
         flag = 1;
         g->count[slot]++;
-        g->max_seen = w > g->max_seen ? w : g->max_seen;
         g->st.heaps_accepted++;
         ++*accepted;
     }
@@ -269,7 +268,7 @@ extern "C" fengine_status fengine_ingest_poll(fengine_ingest_t g, void *cuda_str
     reclaim(g, false);
     const int slot = (int)(g->next_emit % g->n_slots);
     const bool complete = g->count[slot] == (long long)g->n_streams * g->hpc;
-    const bool due = complete || flush || g->blocked || (g->reorder > 0 && g->max_seen >= g->next_emit + g->reorder);
+    const bool due = complete || flush || g->blocked;
     if (!due) return FENGINE_OK;
     if (!d_out) return FENGINE_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
