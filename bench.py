@@ -43,7 +43,7 @@ UNIT = "Gsample/s"
 # its own launch by the input samples the launch processes. Valid only for the
 # sources they were taken from (src = hash of the kernel's source files).
 KERNEL_SOURCES = {
-    "k_phase1": ['k_phase1.cuh', 'k_phase1_t1.cu', 'k_phase1_t2.cu', 'k_phase1_t4.cu', 'k_phase1_t8.cu', 'k_phase1_t16.cu', 'k_phase1_t32.cu', 'fe_device.cuh', 'fe_internal.cuh'],
+    "k_phase1": ['k_phase1.cuh', 'k_phase1_tile.inc', 'k_phase1_t1.cu', 'k_phase1_t2.cu', 'k_phase1_t4.cu', 'k_phase1_t8.cu', 'k_phase1_t16.cu', 'k_phase1_t32.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase2": ['k_phase2.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase2w": ['k_phase2w.cu', 'fe_device.cuh', 'fe_internal.cuh'],
     "k_phase1_tc": ['k_phase1_tc.cu', 'fe_device.cuh', 'fe_internal.cuh'],
@@ -244,6 +244,22 @@ def _base_streams(seed: int, n: int, sigma: float = 32.0):
     return synth.pack10(synth.digitiser_samples(seed, n, sigma, [(0.123, 50.0, 0.0)]))
 
 
+def _batched_launches(plans):
+    """Kernel launches of one fengine_batch_process over FP32 plans: a delay
+    table and a history-tail update per member, then per group of members
+    with the same (taps, N1, N2), one phase-1 and one phase-2 grid per slab
+    round (at most 64 members per grid)."""
+    groups = {}
+    for p in plans:
+        groups.setdefault((p.n_taps, p.info.fft_n1, p.info.fft_n2), []).append(int(p.info.slabs_per_chunk))
+    grids = 0
+    for slabs in groups.values():
+        for r in range(max(slabs)):
+            k = sum(1 for s in slabs if s > r)
+            grids += 2 * ((k + 63) // 64)
+    return 2 * len(plans) + grids
+
+
 def run_batched(args):
     """Workload 4 as its own JSON line."""
     import torch
@@ -340,7 +356,7 @@ def batched_result(args, fengine, torch):
            "samples_per_step": total,
            "sequential_single_stream": {"value": total * k2 / (ms_seq / 1e3) / 1e9, "unit": UNIT,
                                         "ms_per_step": ms_seq / k2},
-           "gpu_launches": args.steps * sum(2 + 2 * m[0].info.slabs_per_chunk for m in members)}
+           "gpu_launches": args.steps * _batched_launches([m[0] for m in members])}
     batch.close()
     for p in plans:
         p.close()

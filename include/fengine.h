@@ -280,9 +280,14 @@ fengine_status fengine_batch_destroy(fengine_batch_t batch);
 
 /* Process one chunk of each of n distinct plans as one call on cuda_stream:
  * every member computes exactly what fengine_process_chunk computes for it
- * (Sec. 2.1 steps 1-6), with the members spread over the pool's streams,
- * largest work first onto the least-loaded stream, forked from and joined
- * back into cuda_stream (so the call can be captured into a CUDA graph).
+ * (Sec. 2.1 steps 1-6). Members in the FP32 form are grouped: their small
+ * per-call kernels run spread over the pool's streams, then their phase-1
+ * and phase-2 work goes out as one grid per kernel instantiation (members
+ * with the same taps and FFT split; up to 64 members per grid), slab by
+ * slab, on cuda_stream. Members of the other forms run whole on the pool's
+ * streams meanwhile, largest work first onto the least-loaded stream.
+ * Everything forks from and joins back into cuda_stream (so the call can be
+ * captured into a CUDA graph).
  * first_spectra (host, n entries, may be NULL) receives each member's first
  * spectrum. FENGINE_EINVAL for a repeated or invalid plan; a member that
  * fails validation stops the call with its status, members enqueued before

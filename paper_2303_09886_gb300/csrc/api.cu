@@ -533,10 +533,16 @@ fengine_status fengine_reset(fengine_plan_t pl) {
     return FENGINE_OK;
 }
 
-fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const uint8_t *d_packed,
-                                     int64_t first_sample, const uint8_t *d_valid, int8_t *d_out,
-                                     uint8_t *d_heap_flags, float *d_prequant, int32_t *d_window_tap,
-                                     int64_t *first_spectrum) {
+}  // extern "C"
+
+namespace {
+
+// fengine_process_chunk; with def (FP32 form), the phase-1 / phase-2 launches
+// are returned in def instead of enqueued (the history tail is then updated
+// first: it writes the history buffer this call does not read)
+fengine_status process_impl(fengine_plan_t pl, void *cuda_stream, const uint8_t *d_packed, int64_t first_sample,
+                            const uint8_t *d_valid, int8_t *d_out, uint8_t *d_heap_flags, float *d_prequant,
+                            int32_t *d_window_tap, int64_t *first_spectrum, fe::DeferredCall *def) {
     if (!pl || !d_packed || !d_out) return fail(FENGINE_EINVAL, "null argument");
     if (((uintptr_t)d_packed & 3) || ((uintptr_t)d_out & 3))
         return fail(FENGINE_EINVAL, "d_packed and d_out must be 4-byte aligned");
@@ -754,6 +760,39 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     pt.window_tap = d_window_tap;
     pt.err = pl->d_err;
 
+    if (def) {
+        const size_t slab_elems = (size_t)pl->n_streams * pl->SL * (pl->N1 / 2 + 1) * pl->N2;
+        if ((e = fe::launch_tail_update(pl->d_hist[pl->cur], d_packed, pl->d_hist[1 - pl->cur], pl->hist_bytes,
+                                        pl->chunk_bytes, pl->n_streams, st)) != cudaSuccess)
+            return cuda_fail(e, "tail launch");
+        def->T = pl->T;
+        def->N1 = pl->N1;
+        def->N2 = pl->N2;
+        def->n_streams = pl->n_streams;
+        def->n_ant = pl->n_ant;
+        def->p1.clear();
+        def->p2.clear();
+        for (int s = 0; s < pl->n_slabs; s++) {
+            float2 *A = reinterpret_cast<float2 *>(reinterpret_cast<char *>(pl->d_A) +
+                                                   (size_t)(s & 1) * slab_elems * pl->a_elem);
+            const int qb = s * pl->SL;
+            const int qc = (pl->M - qb) < pl->SL ? (pl->M - qb) : pl->SL;
+            p1.A = A;
+            p1.q_begin = qb;
+            p1.q_count = qc;
+            p2.A = A;
+            p2.q_begin = qb;
+            p2.q_count = qc;
+            def->p1.push_back(p1);
+            def->p2.push_back(p2);
+        }
+        pl->cur = 1 - pl->cur;
+        pl->started = true;
+        pl->next_sample = first_sample + pl->L;
+        if (first_spectrum) *first_spectrum = m0;
+        return FENGINE_OK;
+    }
+
     // Slab pipeline: slab s uses intermediate buffer s % 2; phase 1 runs on
     // internal stream 0, phase 2 on internal stream 1, so phase 1 of slab
     // s + 1 overlaps phase 2 of slab s. Buffer reuse waits for phase 2 of
@@ -809,6 +848,34 @@ fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const
     pl->next_sample = first_sample + pl->L;
     if (first_spectrum) *first_spectrum = m0;
     return FENGINE_OK;
+}
+
+}  // namespace
+
+namespace fe {
+
+bool plan_defers(fengine_plan_t pl) { return pl && !pl->tc1 && pl->precision == FENGINE_FP32; }
+
+fengine_status process_chunk_deferred(fengine_plan_t pl, cudaStream_t st, const uint8_t *d_packed,
+                                      int64_t first_sample, const uint8_t *d_valid, int8_t *d_out,
+                                      uint8_t *d_heap_flags, int64_t *first_spectrum, DeferredCall *def,
+                                      bool *deferred) {
+    const bool fp32 = plan_defers(pl);
+    *deferred = fp32;
+    return process_impl(pl, (void *)st, d_packed, first_sample, d_valid, d_out, d_heap_flags, nullptr, nullptr,
+                        first_spectrum, fp32 ? def : nullptr);
+}
+
+}  // namespace fe
+
+extern "C" {
+
+fengine_status fengine_process_chunk(fengine_plan_t pl, void *cuda_stream, const uint8_t *d_packed,
+                                     int64_t first_sample, const uint8_t *d_valid, int8_t *d_out,
+                                     uint8_t *d_heap_flags, float *d_prequant, int32_t *d_window_tap,
+                                     int64_t *first_spectrum) {
+    return process_impl(pl, cuda_stream, d_packed, first_sample, d_valid, d_out, d_heap_flags, d_prequant,
+                        d_window_tap, first_spectrum, nullptr);
 }
 
 fengine_status fengine_device_status(fengine_plan_t pl) {

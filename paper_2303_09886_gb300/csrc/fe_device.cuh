@@ -150,4 +150,17 @@ __device__ __forceinline__ void fft_regc(float2 (&z)[NN]) {
     }
 }
 
+// The member of a grouped launch (GroupArgs) that owns block b: the last m
+// with start[m] <= b (binary search over the n members' first blocks).
+template <class G>
+__device__ __forceinline__ int group_member(const G &g, int b) {
+    int lo = 0, hi = g.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 }  // namespace fe

@@ -22,6 +22,8 @@
 
 #include <vector>
 
+#include "../../include/fengine.h"
+
 namespace fe {
 
 constexpr int kMaxSeg = 16;   // FENGINE_MAX_DELAY_SEGMENTS
@@ -119,6 +121,50 @@ cudaError_t launch_phase2(int N2, const Phase2Params &p, int n_ant, cudaStream_t
 // per sequence, two in-register 32-point DFTs around one shared-memory transpose
 cudaError_t launch_phase2w(const Phase2Params &p, int n_ant, cudaStream_t s);
 size_t phase2w_smem_bytes();
+
+// ---- grouped launches (batching): the launches of several plans that use
+// one kernel instantiation, as one grid. Member m owns the blocks
+// [start[m], start[m + 1]) and runs with parameters p[m]. The whole group is
+// passed by value as the kernel's parameter (at most kMaxGroup members, a
+// few KB), so a grouped launch is captured into a CUDA graph like any other.
+constexpr int kMaxGroup = 64;
+template <class P>
+struct GroupArgs {
+    P p[kMaxGroup];
+    int start[kMaxGroup + 1];   // start[n] = blocks of the launch
+    int aux[kMaxGroup];         // the member's blocks along y (grid kernels) or antennas (k_phase2w)
+    int gx;                     // blocks along x, the same for every member (grid kernels)
+    int n;
+};
+using Phase1Group = GroupArgs<Phase1Params>;
+using Phase2Group = GroupArgs<Phase2Params>;
+// one member's blocks and their (gx, gy) in its own launch
+int phase1_blocks(int N1, const Phase1Params &p, int n_streams, int *gx, int *gy);
+int phase2_blocks(int N2, const Phase2Params &p, int n_ant, int *gx, int *gy);   // N2 < 1024
+long long phase2w_items(const Phase2Params &p, int n_ant);                        // work items of k_phase2w
+int phase2w_wave();                                                                 // CTAs of one k_phase2w wave
+cudaError_t launch_phase1_group(int T, int N1, const Phase1Group &g, cudaStream_t s);
+cudaError_t launch_phase2_group(int N2, bool half_in, const Phase2Group &g, cudaStream_t s);
+cudaError_t launch_phase2w_group(bool half_in, const Phase2Group &g, cudaStream_t s);
+
+// A call of a plan with its phase launches handed back instead of enqueued
+// (batching): the per-slab parameters fengine_process_chunk would launch.
+// The FP32 form only; its other kernels (delay table, lost data, history
+// tail) are enqueued on the call's stream as usual.
+struct DeferredCall {
+    int T = 0, N1 = 0, N2 = 0, n_streams = 0, n_ant = 0;
+    std::vector<Phase1Params> p1;   // per slab, in order
+    std::vector<Phase2Params> p2;
+};
+// whether process_chunk_deferred hands back this plan's phase launches
+bool plan_defers(fengine_plan_t pl);
+// fengine_process_chunk with the FP32 form's phase launches returned in def
+// (*deferred = true); other forms run as fengine_process_chunk (*deferred =
+// false). No debug outputs.
+fengine_status process_chunk_deferred(fengine_plan_t pl, cudaStream_t st, const uint8_t *d_packed,
+                                      int64_t first_sample, const uint8_t *d_valid, int8_t *d_out,
+                                      uint8_t *d_heap_flags, int64_t *first_spectrum, DeferredCall *def,
+                                      bool *deferred);
 
 // Tile shapes (host and device agree through these).
 constexpr int kP1Rows = 32;   // spectra per phase-1 CTA

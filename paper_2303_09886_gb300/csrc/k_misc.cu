@@ -7,6 +7,28 @@ namespace fe {
 
 template <int T>
 cudaError_t launch_phase1_n1(int N1, const Phase1Params &p, int n_streams, cudaStream_t s);
+template <int T>
+cudaError_t launch_phase1_group_n1(int N1, const Phase1Group &g, cudaStream_t s);
+
+cudaError_t launch_phase1_group(int T, int N1, const Phase1Group &g, cudaStream_t s) {
+    switch (T) {
+        case 1: return launch_phase1_group_n1<1>(N1, g, s);
+        case 2: return launch_phase1_group_n1<2>(N1, g, s);
+        case 4: return launch_phase1_group_n1<4>(N1, g, s);
+        case 8: return launch_phase1_group_n1<8>(N1, g, s);
+        case 16: return launch_phase1_group_n1<16>(N1, g, s);
+        case 32: return launch_phase1_group_n1<32>(N1, g, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// the grid launch_phase1 uses: (N2 / W, tiles of kP1Rows spectra, streams)
+int phase1_blocks(int N1, const Phase1Params &p, int n_streams, int *gx, int *gy) {
+    (void)N1;
+    *gx = p.N2 / p.W;
+    *gy = (p.q_count + kP1Rows - 1) / kP1Rows;
+    return *gx * *gy * n_streams;
+}
 
 
 cudaError_t launch_phase1(int T, int N1, const Phase1Params &p, int n_streams, cudaStream_t s) {

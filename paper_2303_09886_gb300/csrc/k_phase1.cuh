@@ -121,134 +121,48 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) 
     const int stream = blockIdx.z;
     const int t2_0 = blockIdx.x * W;
     const int q0 = p.q_begin + blockIdx.y * R;
-    const int Rv = min(R, p.q_begin + p.q_count - q0);
-    const uint8_t *chunk = p.chunk + (long long)stream * p.chunk_bytes;
-    const uint8_t *hist = p.hist + (long long)stream * p.hist_bytes;
-    const unsigned H = (unsigned)p.H, HL = (unsigned)(p.H + p.L);
-    const unsigned RB = (unsigned)N / 4u * 5u;   // packed bytes per row (a multiple of 4: same alignment every row)
-    // rel index (from the first history sample) of input row 0, column t = 0, before the delay
-    const long long rel_base = (long long)N * (p.m0 + q0) - (p.t_in - p.H) + t2_0;
+#include "k_phase1_tile.inc"
+}
 
-    for (int i = threadIdx.x; i < Rv; i += kP1Threads) c_sm[i] = p.ctab[(long long)stream * p.M + q0 + i];
-    for (int i = threadIdx.x; i < (H1 + 1) * W; i += kP1Threads) {
-        const int k = i / W, w = i % W;
-        tw1_sm[i] = __ldg(p.tw1 + (long long)k * N2 + t2_0 + w);
-    }
-
-    // this thread's FIR column pair (c, c + C/2) and its weights
-    const int ca = threadIdx.x, cb = threadIdx.x + S::C / 2;
-    const bool has_pair = ca < S::C / 2;
-    const int ta = N2 * (ca / W) + (ca % W), tb = N2 * (cb / W) + (cb % W);   // column offsets in a row
-    float2 w2[T];
-#pragma unroll
-    for (int j = 0; j < T; j++)
-        w2[j] = has_pair ? make_float2(__ldg(p.w + t2_0 + ta + (long long)N * j), __ldg(p.w + t2_0 + tb + (long long)N * j))
-                         : make_float2(0.0f, 0.0f);
-    float *ga = gs + (ca / W) * S::GW + (ca % W), *gb = gs + (cb / W) * S::GW + (cb % W);
-    __syncthreads();
-
-    int ra = 0;
-    while (ra < Rv) {
-        const int cd = c_sm[ra];
-        int rb = ra + 1;
-        while (rb < Rv && c_sm[rb] == cd) rb++;
-        const long long rel0 = rel_base - cd;   // rel of (input row 0, column 0) at this delay
-        // the whole tile at one delay and inside the chunk: fixed byte pointers per column
-        const long long lo = rel0, hi = rel0 + (long long)N * (R + T - 2) + (long long)N2 * (N1 - 1) + W;
-        if (has_pair && ra == 0 && rb == R && lo >= (long long)H && hi <= (long long)HL && !p.window_tap) {
-            const unsigned sa = (unsigned)(rel0 + ta) - H, sb = (unsigned)(rel0 + tb) - H;
-            const uint8_t *pa = chunk + (sa >> 2) * 5u + ((sa & 3u) * 5u >> 2);
-            const uint8_t *pb = chunk + (sb >> 2) * 5u + ((sb & 3u) * 5u >> 2);
-            const unsigned sha = 6u - 2u * (sa & 3u), shb = 6u - 2u * (sb & 3u);
-            // the packed bytes of rows row + 1 .. row + PF are in flight while row
-            // is filtered; the loads of a row take an (always zero) offset that
-            // the compiler must treat as produced by the previous row's decode,
-            // which keeps it from hoisting every row's loads (and registers) up front
-            constexpr int PF = 6, NR = R + T - 1;
-            unsigned dep = 0u;
-            unsigned ba[PF][2], bb[PF][2];
-#pragma unroll
-            for (int i = 0; i < PF; i++) {
-                ba[i][0] = __ldg(pa + i * RB);
-                ba[i][1] = __ldg(pa + i * RB + 1);
-                bb[i][0] = __ldg(pb + i * RB);
-                bb[i][1] = __ldg(pb + i * RB + 1);
-            }
-            // outputs in pairs (r, r + 1), two independent FMA chains, from a
-            // ring of T + 1 input rows
-            float2 win[T + 1];
-#pragma unroll
-            for (int row = 0; row < NR; row++) {
-                const int u = row % PF;
-                const float xa = field10_to_float(__byte_perm(ba[u][0], ba[u][1], 0x0004u) >> sha);
-                const float xb = field10_to_float(__byte_perm(bb[u][0], bb[u][1], 0x0004u) >> shb);
-                win[row % (T + 1)] = make_float2(xa, xb);
-                asm volatile("" : "+r"(dep) : "f"(xa), "f"(xb));
-                if (row + PF < NR) {
-                    const unsigned off = (row + PF) * RB + dep;
-                    ba[u][0] = __ldg(pa + off);
-                    ba[u][1] = __ldg(pa + off + 1);
-                    bb[u][0] = __ldg(pb + off);
-                    bb[u][1] = __ldg(pb + off + 1);
-                }
-                const int r = row - T;   // pair (r, r + 1) is complete once row r + T is in
-                if (r >= 0 && (r & 1) == 0) {
-                    float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
-#pragma unroll
-                    for (int j = 0; j < T; j++) {
-                        acc0 = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc0);
-                        acc1 = __ffma2_rn(w2[j], win[(r + 1 + j) % (T + 1)], acc1);
-                    }
-                    ga[r * S::ROW] = acc0.x;
-                    gb[r * S::ROW] = acc0.y;
-                    ga[(r + 1) * S::ROW] = acc1.x;
-                    gb[(r + 1) * S::ROW] = acc1.y;
-                }
-            }
-            if constexpr ((R & 1) != 0) {
-                constexpr int r = R - 1;
-                float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-                for (int j = 0; j < T; j++) acc = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc);
-                ga[r * S::ROW] = acc.x;
-                gb[r * S::ROW] = acc.y;
-            }
-        } else if (has_pair) {
-            p1_fir_general<T, S>(p, hist, chunk, H, HL, (unsigned)(rel0 + ta), (unsigned)(rel0 + tb), ra, rb, ga, gb,
-                                 stream, q0, t2_0, ta, tb);
-        }
-        ra = rb;
+// The tiles of several plans' launches (same T, N1, W) in one grid: the
+// member's parameters are staged in shared memory, its block decomposed into
+// the (t2 block, spectrum block, stream) of its own launch.
+template <int T, int N1, int W, bool HALF>
+__global__ void __launch_bounds__(kP1Threads, 2) k_phase1_group(const Phase1Group g) {
+    using S = P1Shape<T, N1, W>;
+    constexpr int R = S::R, H1 = N1 / 2;
+    extern __shared__ float gs[];              // [R][N1][GW] FIR output g
+    __shared__ int c_sm[R];
+    __shared__ float2 tw1_sm[(H1 + 1) * W];    // exp(-2 pi i k1 t2 / N) for this tile's t2
+    __shared__ Phase1Params sp;
+    __shared__ int sxyz[3];
+    if (threadIdx.x == 0) {
+        const int m = group_member(g, (int)blockIdx.x);
+        const int b = (int)blockIdx.x - g.start[m], gy = g.aux[m];
+        sxyz[0] = b % g.gx;
+        sxyz[1] = (b / g.gx) % gy;
+        sxyz[2] = b / (g.gx * gy);
+        sp = g.p[m];
     }
     __syncthreads();
+    const Phase1Params &p = sp;
+    const int N = p.N, N2 = p.N2;
+    const int stream = sxyz[2];
+    const int t2_0 = sxyz[0] * W;
+    const int q0 = p.q_begin + sxyz[1] * R;
+#include "k_phase1_tile.inc"
+}
 
-    // real N1-point DFT over t1, twiddle, store B[k1][t2]
-    for (int e = threadIdx.x; e < Rv * W; e += kP1Threads) {
-        const int r = e / W, w = e % W;
-        const float *g = gs + r * S::ROW + w;
-        float x[N1];
-#pragma unroll
-        for (int t1 = 0; t1 < N1; t1++) x[t1] = g[t1 * S::GW];
-        float2 X[H1 + 1];
-        rdft_reg<N1>(x, X);
-        const long long o = ((long long)stream * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) * N2 + t2_0 + w;
-        const float2 t0 = tw1_sm[w];   // exp(0), times the plan's scale
-        const float2 th = tw1_sm[H1 * W + w];
-        float2 b[H1 + 1];
-        b[0] = make_float2(X[0].x * t0.x, X[0].x * t0.y);
-#pragma unroll
-        for (int k = 1; k < H1; k++) b[k] = cmul(X[k], tw1_sm[k * W + w]);
-        b[H1] = make_float2(X[H1].x * th.x, X[H1].x * th.y);
-        if constexpr (HALF) {
-            // FP16 (re, im) pairs: the rounding the FP16 second stage applies to its operands anyway
-            __half2 *out = reinterpret_cast<__half2 *>(p.A) + o;
-#pragma unroll
-            for (int k = 0; k <= H1; k++) out[(long long)k * N2] = __floats2half2_rn(b[k].x, b[k].y);
-        } else {
-            float2 *out = p.A + o;
-#pragma unroll
-            for (int k = 0; k <= H1; k++) out[(long long)k * N2] = b[k];
-        }
-    }
+template <int T, int N1, int W>
+cudaError_t launch_phase1_tw_group(const Phase1Group &g, cudaStream_t s) {
+    using S = P1Shape<T, N1, W>;
+    const size_t smem = (size_t)S::R * S::ROW * sizeof(float);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_phase1_group<T, N1, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (g.n < 1 || g.start[g.n] < 1) return cudaSuccess;
+    k_phase1_group<T, N1, W, false><<<g.start[g.n], kP1Threads, smem, s>>>(g);
+    return cudaGetLastError();
 }
 
 template <int T, int N1, int W, bool HALF = false>
@@ -262,6 +176,21 @@ cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t 
     dim3 grid(p.N2 / W, (p.q_count + kP1Rows - 1) / kP1Rows, n_streams);
     k_phase1<T, N1, W, HALF><<<grid, kP1Threads, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int T>
+cudaError_t launch_phase1_group_n1(int N1, const Phase1Group &g, cudaStream_t s) {
+    switch (N1 * 1000 + g.p[0].W) {
+        case 8064: return launch_phase1_tw_group<T, 8, 64>(g, s);
+        case 16032: return launch_phase1_tw_group<T, 16, 32>(g, s);
+        case 32016: return launch_phase1_tw_group<T, 32, 16>(g, s);
+        case 64008: return launch_phase1_tw_group<T, 64, 8>(g, s);
+        case 8032: return launch_phase1_tw_group<T, 8, 32>(g, s);
+        case 8016: return launch_phase1_tw_group<T, 8, 16>(g, s);
+        case 8008: return launch_phase1_tw_group<T, 8, 8>(g, s);
+        case 8004: return launch_phase1_tw_group<T, 8, 4>(g, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int T>

@@ -4,4 +4,5 @@
 
 namespace fe {
 template cudaError_t launch_phase1_n1<4>(int, const Phase1Params &, int, cudaStream_t);
+template cudaError_t launch_phase1_group_n1<4>(int, const Phase1Group &, cudaStream_t);
 }  // namespace fe

@@ -171,121 +171,38 @@ __global__ void __launch_bounds__(kP2Threads, 3) k_phase2(const Phase2Params p) 
 
     const int k1 = blockIdx.x, ant = blockIdx.z;
     const int q0 = p.q_begin + blockIdx.y * R2;
-    const int M = p.M, Rv = min(R2, p.q_begin + p.q_count - q0);
-    const int N1 = p.N1, H1 = N1 / 2, N = p.N, n = N / 2, S_ = p.S;
+#include "k_phase2_tile.inc"
+}
 
-    // stage B[k1][.] rows in (sequence = pol * R2 + r), padded
-    {
-        // two complex values per 16-byte load, all of a thread's loads in
-        // flight before the first store; pad() keeps even pairs adjacent
-        constexpr int PER = (R2 * N2 + kP2Threads - 1) / kP2Threads;
-        float4 v[PER];
-#pragma unroll
-        for (int u = 0; u < PER; u++) {
-            const int e = u * kP2Threads + threadIdx.x;
-            const int sq = e / (N2 / 2), t2 = 2 * (e % (N2 / 2));
-            const int pol = sq / R2, r = sq % R2;
-            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const long long o =
-                (((long long)(ant * 2 + pol) * p.a_spectra + (q0 - p.q_begin) + r) * (H1 + 1) + k1) * N2 + t2;
-            if (e < R2 * N2 && r < Rv) {
-                if constexpr (HALF_IN) {
-                    const uint2 h = __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const uint32_t *>(p.A) + o));
-                    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&h.x));
-                    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&h.y));
-                    v[u] = make_float4(a.x, a.y, b.x, b.y);
-                } else {
-                    v[u] = __ldg(reinterpret_cast<const float4 *>(p.A + o));
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < PER; u++) {
-            const int e = u * kP2Threads + threadIdx.x;
-            const int sq = e / (N2 / 2), t2 = 2 * (e % (N2 / 2));
-            if (e < R2 * N2) {
-                buf[sq * LD + pad(t2)] = make_float2(v[u].x, v[u].y);
-                buf[sq * LD + pad(t2 + 1)] = make_float2(v[u].z, v[u].w);
-            }
-        }
-    }
-    // rotation tables: angle/pi = phi/pi - 2 delta k / N, k = k1 + N1 (LO a + b)
-    const float inv = 2.0f / (float)N;
-    for (int e = threadIdx.x; e < 2 * R2 * (S::HI + S::LO + 1); e += kP2Threads) {
-        const int sq = e % (2 * R2), which = e / (2 * R2);
-        const int pol = sq / R2, r = sq % R2;
-        if (r >= Rv) continue;
-        const float2 f = p.ftab[(long long)(ant * 2 + pol) * M + q0 + r];   // (delta, phi / pi)
-        float sn, cs;
-        if (which < S::HI) {
-            const float kk = (float)(k1 + N1 * S::LO * which);
-            sincospif(f.y - f.x * kk * inv, &sn, &cs);
-            // with the inverse of the FP16 intermediate's scale (a power of two)
-            const float us = HALF_IN ? p.tc_unscale : 1.0f;
-            thi[sq * HP + which] = make_float2(cs * us, sn * us);
-        } else if (which < S::HI + S::LO) {
-            const int b = which - S::HI;
-            sincospif(-f.x * (float)(N1 * b) * inv, &sn, &cs);
-            tlo[sq * LP + b] = make_float2(cs, sn);
-        } else {
-            // upper class: Y = G exp(2 i phi - 2 pi i delta) conj(Z)
-            sincospif(2.0f * f.y - 2.0f * f.x, &sn, &cs);
-            qup[sq] = make_float2(cs, sn);
-        }
-    }
-    if ((int)threadIdx.x < Rv) {
-        const int q = q0 + threadIdx.x;
-        const int h = q / S_, s = q - h * S_;
-        const int Sh = min(S_, M - h * S_);
-        rowoff[threadIdx.x] = (long long)h * S_ * n * 4 + s * 4;
-        rowstride[threadIdx.x] = Sh * 4;
+// The tiles of several plans' second stages (same N2) in one grid.
+template <int N2, bool HALF_IN>
+__global__ void __launch_bounds__(kP2Threads, 3) k_phase2_group(const Phase2Group g) {
+    __shared__ Phase2Params sp;
+    __shared__ int sxyz[3];
+    if (threadIdx.x == 0) {
+        const int m = group_member(g, (int)blockIdx.x);
+        const int b = (int)blockIdx.x - g.start[m], gy = g.aux[m];
+        sxyz[0] = b % g.gx;
+        sxyz[1] = (b / g.gx) % gy;
+        sxyz[2] = b / (g.gx * gy);
+        sp = g.p[m];
     }
     __syncthreads();
+    const Phase2Params &p = sp;
+    using S = P2Shape<N2>;
+    constexpr int R2 = S::R2, LD = S::LD;
+    extern __shared__ float2 sm[];
+    float2 *buf = sm;                                  // [2 R2][LD]
+    constexpr int HP = S::HI + 1, LP = S::LO + 1;      // padded table rows (no bank conflicts)
+    float2 *thi = buf + 2 * R2 * LD;                   // [2 R2][HP]
+    float2 *tlo = thi + 2 * R2 * HP;                   // [2 R2][LP]
+    float2 *qup = tlo + 2 * R2 * LP;                   // [2 R2] upper-class factor
+    long long *rowoff = reinterpret_cast<long long *>(qup + 2 * R2);   // [R2] heap row byte offset
+    int *rowstride = reinterpret_cast<int *>(rowoff + R2);             // [R2] bytes per channel row
 
-    // in-place DIF FFT over the 2 Rv sequences
-    dif_all<N2, N2>(buf, 2 * R2, p.tw2);   // twiddles read through the L1 cache
-
-    // epilogue: rotate, gain, quantise, corner turn
-    const bool upper = (k1 != 0 && k1 != H1);
-    const int nslot = upper ? N2 : N2 / 2;
-    // each thread keeps one spectrum r (kP2Threads is a multiple of R2) and
-    // walks the slots k2; lanes with consecutive r write consecutive 4-byte
-    // cells of one channel row
-    const int r = threadIdx.x % R2;
-    if (r >= Rv) return;
-    int8_t *out_r = p.out + (long long)ant * M * n * 4 + rowoff[r];
-    const int rs = rowstride[r];
-    const float2 *F0 = buf + r * LD, *F1 = buf + (R2 + r) * LD;
-    const float2 *th0 = thi + r * HP, *th1 = thi + (R2 + r) * HP;
-    const float2 *tl0 = tlo + r * LP, *tl1 = tlo + (R2 + r) * LP;
-    const float2 qu0 = qup[r], qu1 = qup[R2 + r];
-    // the gain set of this spectrum in each polarisation
-    const int gs0 = p.gsel ? p.gsel[(long long)(ant * 2) * M + q0 + r] : 0;
-    const int gs1 = p.gsel ? p.gsel[(long long)(ant * 2 + 1) * M + q0 + r] : 0;
-    const float2 *gain0 = p.gains + ((long long)(ant * 2) * p.n_gsets_max + gs0) * n;
-    const float2 *gain1 = p.gains + ((long long)(ant * 2 + 1) * p.n_gsets_max + gs1) * n;
-    float2 *pre0 = p.prequant ? p.prequant + ((long long)(ant * 2) * M + q0 + r) * n : nullptr;
-    float2 *pre1 = p.prequant ? p.prequant + ((long long)(ant * 2 + 1) * M + q0 + r) * n : nullptr;
-#pragma unroll 4
-    for (int k2 = threadIdx.x / R2; k2 < nslot; k2 += kP2Threads / R2) {
-        const bool up = k2 >= N2 / 2;
-        const int kc = k1 + N1 * k2;                    // this slot's DFT index
-        const int k = up ? N - kc : kc;                 // channel written
-        const int a = k2 / S::LO, b = k2 % S::LO;
-        const int pos = pad(dif_pos<N2>(k2));
-        const float2 z0 = cmul(cmul(th0[a], tl0[b]), F0[pos]);
-        const float2 z1 = cmul(cmul(th1[a], tl1[b]), F1[pos]);
-        const float2 g0 = __ldg(gain0 + k), g1 = __ldg(gain1 + k);
-        const float2 y0 = up ? cmul(cmul(g0, qu0), cconj(z0)) : cmul(g0, z0);
-        const float2 y1 = up ? cmul(cmul(g1, qu1), cconj(z1)) : cmul(g1, z1);
-        if (pre0) {
-            pre0[k] = y0;
-            pre1[k] = y1;
-        }
-        const unsigned packed = ((unsigned)quant8(y0.x) & 0xFFu) | (((unsigned)quant8(y0.y) & 0xFFu) << 8) |
-                                (((unsigned)quant8(y1.x) & 0xFFu) << 16) | ((unsigned)quant8(y1.y) << 24);
-        *reinterpret_cast<unsigned *>(out_r + (long long)k * rs) = packed;
-    }
+    const int k1 = sxyz[0], ant = sxyz[2];
+    const int q0 = p.q_begin + sxyz[1] * R2;
+#include "k_phase2_tile.inc"
 }
 
 size_t phase2_smem_bytes(int N2, int R2) {
@@ -311,6 +228,49 @@ static cudaError_t launch_p2h(const Phase2Params &p, int n_ant, cudaStream_t s) 
 template <int N2>
 static cudaError_t launch_p2(const Phase2Params &p, int n_ant, cudaStream_t s) {
     return p.half_in ? launch_p2h<N2, true>(p, n_ant, s) : launch_p2h<N2, false>(p, n_ant, s);
+}
+
+// the grid launch_phase2 uses for N2 < 1024: (classes k1, tiles of R2 spectra, antennas)
+int phase2_blocks(int N2, const Phase2Params &p, int n_ant, int *gx, int *gy) {
+    (void)N2;
+    *gx = p.N1 / 2 + 1;
+    *gy = (p.q_count + p.R2 - 1) / p.R2;
+    return *gx * *gy * n_ant;
+}
+
+template <int N2, bool HALF_IN>
+static cudaError_t launch_p2h_group(const Phase2Group &g, cudaStream_t s) {
+    const int R2 = P2Shape<N2>::R2;
+    const size_t smem = phase2_smem_bytes(N2, R2);
+    cudaError_t e = cudaFuncSetAttribute(k_phase2_group<N2, HALF_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    for (int m = 0; m < g.n; m++)
+        if (g.p[m].R2 != R2) return cudaErrorInvalidValue;
+    if (g.n < 1 || g.start[g.n] < 1) return cudaSuccess;
+    k_phase2_group<N2, HALF_IN><<<g.start[g.n], kP2Threads, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+template <int N2>
+static cudaError_t launch_p2_group(bool half_in, const Phase2Group &g, cudaStream_t s) {
+    return half_in ? launch_p2h_group<N2, true>(g, s) : launch_p2h_group<N2, false>(g, s);
+}
+
+cudaError_t launch_phase2_group(int N2, bool half_in, const Phase2Group &g, cudaStream_t s) {
+    switch (N2) {
+        case 2: return launch_p2_group<2>(half_in, g, s);
+        case 4: return launch_p2_group<4>(half_in, g, s);
+        case 8: return launch_p2_group<8>(half_in, g, s);
+        case 16: return launch_p2_group<16>(half_in, g, s);
+        case 32: return launch_p2_group<32>(half_in, g, s);
+        case 64: return launch_p2_group<64>(half_in, g, s);
+        case 128: return launch_p2_group<128>(half_in, g, s);
+        case 256: return launch_p2_group<256>(half_in, g, s);
+        case 512: return launch_p2_group<512>(half_in, g, s);
+        case 1024: return launch_phase2w_group(half_in, g, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_phase2(int N2, const Phase2Params &p, int n_ant, cudaStream_t s) {

@@ -102,3 +102,59 @@ def test_batch_rejects_repeated_plan():
     assert e.value.status == 1
     batch.close()
     plan.close()
+
+
+def test_grouped_launches_with_shared_shapes_slabs_and_other_forms():
+    """Members that share a kernel instantiation go out as one grid per
+    phase: five 1024-channel plans (16 taps, one of them in several slabs), three
+    8192-channel plans (the persistent 1024-point second stage, one with two
+    antennas), a 256-channel plan, and two tensor-core plans that run whole
+    beside the grids. Every member's bytes equal its plan alone, in three
+    consecutive chunks (history carried through the grouped path)."""
+    import torch
+    specs = [  # (n_antennas, n_channels, n_taps, spectra per chunk, delay, precision, slab_spectra)
+        (1, 1024, 16, 40, 7.3, fengine.FP32, 0), (1, 1024, 16, 70, 30.0, fengine.FP32, 0),
+        (2, 1024, 16, 33, 100.2, fengine.FP32, 0), (1, 1024, 16, 100, 2.5, fengine.FP32, 32),
+        (1, 1024, 16, 64, 0.0, fengine.FP32, 0),
+        (1, 8192, 16, 36, 1999.2, fengine.FP32, 0), (2, 8192, 16, 20, 50.7, fengine.FP32, 0),
+        (1, 8192, 16, 50, 5.5, fengine.FP32, 0),
+        (1, 256, 4, 300, 3.0, fengine.FP32, 0),
+        (1, 8192, 16, 40, 60.1, fengine.TC_FP16, 0), (1, 1024, 8, 45, 9.9, fengine.TC_BF16, 0),
+    ]
+    made = []
+    for i, (n_ant, n, T, m, d, prec, sl) in enumerate(specs):
+        L = 2 * n * m
+        s = streams(synth.SEED_BASE + 60 + i, n_ant, 3 * L, 25.0, tones=[(0.07 + 0.03 * i, 40.0, 0.2)])
+        plans = []
+        for _ in range(2):   # one to run alone, one in the batch
+            p = fengine.Plan(n_ant, n, T, L, spectra_per_heap=min(16, m), max_delay_samples=int(d) + 8,
+                             precision=prec, slab_spectra=sl)
+            g = synth.random_gains(700 + i, 2 * n_ant, n).reshape(n_ant, 2, n)
+            for a in range(n_ant):
+                for pol in range(2):
+                    p.set_delay(a, pol, d + 0.2 * pol, rate=1e-7, phase=0.1 * i)
+                    p.set_gains(a, pol, g[a, pol])
+            plans.append(p)
+        made.append((plans, s))
+    assert made[3][0][0].info.slabs_per_chunk > 1
+    batch = fengine.Batch(4)
+    for c in range(3):
+        members, alone = [], []
+        for plans, s in made:
+            L = plans[0].chunk_samples
+            pk = _packed(s, c * L, L)
+            d_a = torch.empty(plans[0].info.out_bytes, dtype=torch.int8, device="cuda")
+            m0 = plans[0].process(pk, c * L, d_a)
+            alone.append((m0, d_a))
+            members.append((plans[1], pk, c * L, torch.empty_like(d_a)))
+        firsts = batch.process(members)
+        torch.cuda.synchronize()
+        for k, (mem, (m0, d_a)) in enumerate(zip(members, alone)):
+            assert firsts[k] == m0
+            np.testing.assert_array_equal(mem[3].cpu().numpy(), d_a.cpu().numpy(),
+                                          err_msg=f"member {k} chunk {c}")
+    batch.close()
+    for plans, _ in made:
+        for p in plans:
+            p.device_status()
+            p.close()
