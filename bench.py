@@ -33,9 +33,6 @@ if ROOT not in sys.path:
 METRIC = "input Gsample/s per GB300 (8K-ch, 16-tap), TC/batched vs FP32 plain; % HBM roofline"
 UNIT = "Gsample/s"
 
-# DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by the hash of the kernel sources it was
-# taken on; reported as null once the sources change.
 # DRAM bytes (read + write) per input sample of each slab kernel, from ncu
 # captures (profiles/) of 1 antenna x 2 pol x 2^24 samples/pol with the whole
 # chunk in one slab (one launch of 2 x 1024 spectra = 33.5 M samples). ncu
@@ -51,11 +48,11 @@ KERNEL_SOURCES = {
 }
 _CAPTURED = 33554432   # input samples of the captured launch
 NCU_TRAFFIC = {
-    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44408832 + 95248128) / _CAPTURED, "src": "11552148f7285605"},
-    "k_phase1<16,16,32,1>": {"bytes_per_sample": (43936768 + 27555840) / _CAPTURED, "src": "11552148f7285605"},
-    "k_phase1<16,64,8,0>": {"bytes_per_sample": (44158464 + 89049344) / _CAPTURED, "src": "11552148f7285605"},
-    "k_phase2w": {"bytes_per_sample": (166702080 + 19888640) / _CAPTURED, "src": "25eaca44b1835be4"},
-    "k_phase2<256>": {"bytes_per_sample": (138605824 + 13872896) / _CAPTURED, "src": "4b85a31bd47bd8c3"},
+    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44546560 + 95343104) / _CAPTURED, "src": "10d80fecd620bff8"},
+    "k_phase2w": {"bytes_per_sample": (170740736 + 23683072) / _CAPTURED, "src": "c197de9ef1616e3b"},
+    "k_phase2w<half>": {"bytes_per_sample": (94492672 + 22903552) / _CAPTURED, "src": "c197de9ef1616e3b"},
+    "k_phase1_tc<2,16,1>": {"bytes_per_sample": (96444416 + 48808448) / _CAPTURED, "src": "55093c47be75dfea"},
+    "k_unpack_cols": {"bytes_per_sample": (42582528 + 19857664) / _CAPTURED, "src": "55093c47be75dfea"},
 }
 
 
