@@ -243,9 +243,10 @@ def _base_streams(seed: int, n: int, sigma: float = 32.0):
 
 def _batched_launches(plans):
     """Kernel launches of one fengine_batch_process over FP32 plans: a delay
-    table and a history-tail update per member, then per group of members
-    with the same (taps, N1, N2), one phase-1 and one phase-2 grid per slab
-    round (at most 64 members per grid)."""
+    table and a history-tail update per member (and the lost-data flags when
+    its chunks are heap-aligned), then per group of members with the same
+    (taps, N1, N2), one phase-1 and one phase-2 grid per slab round (at most
+    64 members per grid)."""
     groups = {}
     for p in plans:
         groups.setdefault((p.n_taps, p.info.fft_n1, p.info.fft_n2), []).append(int(p.info.slabs_per_chunk))
@@ -254,7 +255,8 @@ def _batched_launches(plans):
         for r in range(max(slabs)):
             k = sum(1 for s in slabs if s > r)
             grids += 2 * ((k + 63) // 64)
-    return 2 * len(plans) + grids
+    small = sum(2 + (1 if p.chunk_samples % 4096 == 0 else 0) for p in plans)
+    return small + grids
 
 
 def run_batched(args):
@@ -760,7 +762,10 @@ def main(argv=None):
                  "with_intermediates_GBps": path_all, "frac_with_intermediates": path_all / peak,
                  "bytes_per_sample": {"algorithmic": 2.25, "with_intermediates": 2.25 + 2 * inter}},
         "e2e": e2e,
-        "gpu_launches": (2 + 2 * slabs + (1 if tc else 0)) * args.steps,
+        # delay table, history tail, lost-data flags (heap-aligned chunks),
+        # the column unpack (tensor-core forms), a phase-1 / phase-2 pair per slab
+        "gpu_launches": (2 + (1 if wl.chunk_samples % 4096 == 0 else 0) + (1 if tc else 0) + 2 * slabs)
+        * args.steps,
         "forms": forms,
         "clocks": clocks.summary(w0, w1),
         **extra,
