@@ -45,9 +45,11 @@
  *   R13 lost data (Sec. 3.7): a digitiser heap is 4096 samples (Sec. 2.2)
  *      starting at a multiple of 4096; heaps no chunk delivered (before a
  *      stream's first chunk, or flagged missing) are missing.
+ *   R15 narrow-band mode (Sec. 6 names it only): a down-converter in front
+ *      of the channelizer, described at orc_ddc below.
  * Steps 7-8 (lost data, Sec. 3.7): orc_window_usable / orc_spectrum_flags /
  * orc_heap_flags; gain sets that change at spectrum timestamps:
- * orc_segment_select.
+ * orc_segment_select; the narrow-band front end: orc_ddc_weights / orc_ddc.
  */
 #include <math.h>
 #include <stdint.h>
@@ -410,4 +412,86 @@ int32_t orc_segment_select(int32_t n_seg, const int64_t *t_apply, int64_t t0)
         if (t_apply[k] <= t0)
             s = k;
     return s;
+}
+
+/* ------------------------------------------------------ narrow-band mode */
+
+/* Narrow-band front end. The paper names a narrow-band mode (Sec. 6: a
+ * low-pass filter before the PFB) without specifying it; this is the
+ * library's reading R15 of it, a digital down-converter that turns the
+ * wide-band stream into a real stream at a lower rate which the same
+ * channelizer then takes:
+ *   band        [fc - 1/(2D), fc + 1/(2D)] of the input (D a power of two),
+ *   mix         m[i] = x[i] exp(-2 pi i fc i),
+ *   low-pass    z[i] = sum_{u < Lh} h[u] m[i - u]  (real h, cutoff 1/(2D)),
+ *   shift       the band's lower edge to 0: z[i] exp(+2 pi i i / (2D)),
+ *   real part   y = 2 g Re(.), which keeps the band's amplitudes,
+ *   decimate    keep every (D/2)-th sample: y[j] at input sample j D / 2.
+ * Output j therefore holds 2 g Re(exp(2 pi i j / 4) sum_u h[u] x[j D/2 - u]
+ * exp(-2 pi i fc (j D/2 - u))); the band appears at output frequencies
+ * [0, 1/2) cycles per output sample, input frequency f at (f - fc) D / 2 +
+ * 1/4. The output is requantised to 10 bits (round half away from zero,
+ * saturate to [-511, 511]) so that the channelizer reads it like a
+ * digitiser stream.
+ *
+ * Default low-pass (R15): Lh = D Th taps, h[u] = sin^2(pi (u + 1/2) / Lh) *
+ * sinc((u + 1/2 - Lh/2) / D), scaled to unit DC gain (sum h = 1). */
+void orc_ddc_weights(int D, int Th, double *h)
+{
+    int64_t L = (int64_t)D * Th;
+    double s = 0.0;
+    for (int64_t u = 0; u < L; u++) {
+        double x = ((double)u + 0.5 - (double)L / 2.0) / (double)D;
+        double sinc = (x == 0.0) ? 1.0 : sin(M_PI * x) / (M_PI * x);
+        double w = sin(M_PI * ((double)u + 0.5) / (double)L);
+        h[u] = w * w * sinc;
+        s += h[u];
+    }
+    for (int64_t u = 0; u < L; u++)
+        h[u] /= s;
+}
+
+/* R15 requantiser: round half away from zero, saturate to [-511, 511]. */
+int32_t orc_quantise10(double x)
+{
+    double r = round(x);
+    if (r > 511.0)
+        r = 511.0;
+    if (r < -511.0)
+        r = -511.0;
+    return (int32_t)r;
+}
+
+/* Outputs j = j0 .. j0 + n_out - 1 of the down-converter for one stream.
+ *   x, first, count : input samples (zero outside, R8).
+ *   D, Lh, h        : decimation (even) and low-pass taps.
+ *   fc, g           : centre frequency (cycles per input sample) and gain.
+ *   y               : out, n_out doubles before requantisation.
+ *   q               : out, n_out 10-bit values, may be NULL. */
+void orc_ddc(const int32_t *x, int64_t first, int64_t count, int D, int Lh, const double *h,
+             double fc, double g, int64_t j0, int64_t n_out, double *y, int32_t *q)
+{
+    int64_t k;
+#pragma omp parallel for schedule(static)
+    for (k = 0; k < n_out; k++) {
+        int64_t j = j0 + k;
+        int64_t i0 = j * (D / 2);
+        double re = 0.0, im = 0.0;
+        for (int u = 0; u < Lh; u++) {
+            int64_t i = i0 - u;
+            double v = (i >= first && i < first + count) ? (double)x[i - first] : 0.0;
+            /* the mixing phase fc i, reduced to one cycle before the
+             * trigonometry (fc i can be large) */
+            double ph = fc * (double)i;
+            ph -= floor(ph);
+            re += h[u] * v * cos(2.0 * M_PI * ph);
+            im -= h[u] * v * sin(2.0 * M_PI * ph);
+        }
+        /* exp(2 pi i j / 4) = i^j: a quarter turn per output sample */
+        int64_t r = ((j % 4) + 4) % 4;
+        double out_re = r == 0 ? re : r == 1 ? -im : r == 2 ? -re : im;
+        y[k] = 2.0 * g * out_re;
+        if (q)
+            q[k] = orc_quantise10(y[k]);
+    }
 }

@@ -83,6 +83,14 @@ def _load():
             lib.orc_heap_flags.restype = None
             lib.orc_segment_select.argtypes = [ctypes.c_int32, _I64P, ctypes.c_int64]
             lib.orc_segment_select.restype = ctypes.c_int32
+            lib.orc_ddc_weights.argtypes = [ctypes.c_int, ctypes.c_int, _F64P]
+            lib.orc_ddc_weights.restype = None
+            lib.orc_quantise10.argtypes = [ctypes.c_double]
+            lib.orc_quantise10.restype = ctypes.c_int32
+            lib.orc_ddc.argtypes = [_I32P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _F64P,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _F64P,
+                                    _I32P]
+            lib.orc_ddc.restype = None
             _lib = lib
     return _lib
 
@@ -272,3 +280,29 @@ def heap_flags(usable_pol0: np.ndarray, usable_pol1: np.ndarray, S: int) -> np.n
     out = np.empty((M + S - 1) // S, np.uint8)
     _load().orc_heap_flags(_p(u0, _U8P), _p(u1, _U8P), M, S, _p(out, _U8P))
     return out
+
+
+# ------------------------------------------------------- narrow-band mode
+
+def ddc_weights(D: int, Th: int) -> np.ndarray:
+    """R15: default low-pass of the narrow-band front end, D Th taps, unit DC gain."""
+    h = np.empty(D * Th, np.float64)
+    _load().orc_ddc_weights(D, Th, _p(h, _F64P))
+    return h
+
+
+def quantise10(x: float) -> int:
+    """R15: round half away from zero, saturate to [-511, 511]."""
+    return int(_load().orc_quantise10(float(x)))
+
+
+def ddc(samples: np.ndarray, first: int, D: int, h: np.ndarray, fc: float, g: float, j0: int, n_out: int):
+    """R15 down-converter: outputs j0 .. j0 + n_out - 1 of one stream as
+    (y FP64 before requantisation, q 10-bit int32)."""
+    s = np.ascontiguousarray(samples, np.int32)
+    hh = np.ascontiguousarray(h, np.float64)
+    y = np.empty(n_out, np.float64)
+    q = np.empty(n_out, np.int32)
+    _load().orc_ddc(_p(s, _I32P), int(first), s.size, int(D), hh.size, _p(hh, _F64P), float(fc), float(g),
+                    int(j0), int(n_out), _p(y, _F64P), _p(q, _I32P))
+    return y, q

@@ -390,3 +390,85 @@ def test_negative_integer_delay_is_a_shift_the_other_way(c):
     assert np.all(cn == -c)
     np.testing.assert_array_equal(neg, adv)
     np.testing.assert_array_equal(qn, qa)
+
+
+# ------------------------------------------------ narrow-band front end (R15)
+
+def test_ddc_weights_lowpass_shape():
+    """Unit DC gain, symmetric, -6 dB at the cutoff 1/(2D), flat passband and
+    a stopband below -40 dB one transition width past the cutoff."""
+    for D, Th in ((4, 16), (8, 16), (16, 8)):
+        h = O.ddc_weights(D, Th)
+        assert h.size == D * Th
+        assert abs(h.sum() - 1.0) < 1e-12
+        np.testing.assert_allclose(h, h[::-1], atol=1e-15)
+        F = 1 << 16
+        H = np.abs(np.fft.fft(h, F))
+        f = np.arange(F) / F
+        edge = 20 * np.log10(H[int(round(F / (2 * D)))])
+        assert abs(edge + 6.02) < 0.2
+        if Th >= 16:   # the transition narrows with the taps: Th = 16 is the default
+            pb = H[f < 0.8 / (2 * D)]
+            assert 20 * np.log10(pb.max() / pb.min()) < 0.15
+            assert 20 * np.log10(H[(f > 1.25 / (2 * D)) & (f < 0.5)].max()) < -40.0
+
+
+def _ddc_stepwise(x, first, D, h, fc, g, j0, n_out):
+    """The down-converter's steps one after another at the full rate (mix,
+    low-pass by np.convolve, shift the band edge to 0, real part, keep every
+    (D/2)-th sample): an independent formulation of the fused sum."""
+    lo = j0 * (D // 2) - h.size + 1
+    hi = (j0 + n_out - 1) * (D // 2) + 1
+    i = np.arange(lo, hi)
+    v = np.zeros(i.size)
+    inside = (i >= first) & (i < first + x.size)
+    v[inside] = x[i[inside] - first]
+    m = v * np.exp(-2j * np.pi * fc * i.astype(np.float64))
+    z = np.convolve(m, h)[h.size - 1:h.size - 1 + i.size - h.size + 1]   # z at i = lo + Lh - 1 ...
+    iz = i[h.size - 1:]
+    s = z * np.exp(2j * np.pi * iz / (2 * D))
+    y_full = 2 * g * s.real
+    keep = (iz % (D // 2) == 0)
+    return y_full[keep][:n_out]
+
+
+def test_ddc_matches_stepwise_pipeline():
+    g = np.random.default_rng(5)
+    for D, Th, fc in ((8, 8, 0.2), (4, 16, 0.37), (16, 4, 0.05)):
+        x = g.integers(-512, 512, 6000).astype(np.int32)
+        h = O.ddc_weights(D, Th)
+        first, j0, n_out = 1000, 0, 900     # outputs from before the stream: zeros there
+        y, q = O.ddc(x, first, D, h, fc, 1.7, j0, n_out)
+        ref = _ddc_stepwise(x, first, D, h, fc, 1.7, j0, n_out)
+        np.testing.assert_allclose(y, ref, rtol=1e-9, atol=1e-9)
+        np.testing.assert_array_equal(q, [O.quantise10(v) for v in y])
+
+
+def test_ddc_tone_closed_form():
+    """A tone A cos(2 pi f i + psi) comes out as 2 g Re(i^j (A/2) [e^{i psi}
+    e^{2 pi i (f - fc) i} H(f - fc) + e^{-i psi} e^{-2 pi i (f + fc) i} H(-f - fc)])
+    at i = j D / 2, H the transform of the low-pass; only the input's
+    rounding to integers is left (|error| <= g sum |h|)."""
+    D, Th, fc, g = 8, 16, 0.21, 0.8
+    h = O.ddc_weights(D, Th)
+    u = np.arange(h.size)
+    Hf = lambda nu: np.sum(h * np.exp(-2j * np.pi * nu * u))
+    for f, A, psi in ((0.21 + 0.02, 400.0, 0.4), (0.21 - 0.045, 300.0, 2.0), (0.21, 450.0, -1.0)):
+        n = 1 << 14
+        i = np.arange(n)
+        x = np.rint(A * np.cos(2 * np.pi * f * i + psi)).astype(np.int32)
+        j0 = h.size          # windows inside the stream
+        n_out = 2000
+        y, _ = O.ddc(x, 0, D, h, fc, g, j0, n_out)
+        j = np.arange(j0, j0 + n_out)
+        t = j * (D // 2)
+        zz = (A / 2) * (np.exp(1j * psi) * np.exp(2j * np.pi * (f - fc) * t) * Hf(f - fc)
+                        + np.exp(-1j * psi) * np.exp(-2j * np.pi * (f + fc) * t) * Hf(-f - fc))
+        pred = 2 * g * (1j ** (j % 4) * zz).real
+        assert np.max(np.abs(y - pred)) <= g * np.sum(np.abs(h)) + 1e-9
+
+
+def test_quantise10_ties_and_saturation():
+    for x, q in ((10.5, 11), (-10.5, -11), (10.49, 10), (0.5, 1), (-0.5, -1), (510.5, 511),
+                 (511.5, 511), (-600.0, -511), (1e9, 511)):
+        assert O.quantise10(x) == q
