@@ -459,6 +459,53 @@ def service_result(args, fengine, torch):
     return res
 
 
+def narrowband_result(args, fengine, torch, wl, d_in):
+    """Narrow-band mode on the headline workload's input: the down-converter
+    (D = 8, 16 taps per phase, band centred at 0.2 cycles/sample) and an
+    8192-channel, 16-tap plan over its 10-bit output, one call each per
+    step, timed with CUDA events on the same stream; Gsample/s of wide-band
+    input."""
+    D, Th, fc = 8, 16, 0.2
+    L = wl.chunk_samples
+    ddc = fengine.DDC(wl.n_antennas, D, Th, L, fc, 1.0)
+    Lo = ddc.out_samples
+    plan = fengine.Plan(wl.n_antennas, 8192, 16, Lo, max_delay_samples=0)
+    d_nb = torch.empty((wl.n_antennas, 2, Lo * 5 // 4), dtype=torch.uint8, device="cuda")
+    d_out = torch.empty(plan.info.out_bytes, dtype=torch.int8, device="cuda")
+    stream = torch.cuda.current_stream()
+    t = [0]
+
+    def step(with_plan):
+        ddc.process(d_in, t[0], d_nb, stream=stream)
+        if with_plan:
+            plan.process(d_nb, t[0] * 2 // D, d_out, stream=stream)
+        t[0] += L
+
+    res = {}
+    k = max(3, min(args.steps, 20))
+    for name, with_plan in (("ddc_only", False), ("ddc_and_plan", True)):
+        ddc.reset()
+        plan.reset()
+        t[0] = 0
+        for _ in range(3):
+            step(with_plan)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            step(with_plan)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        res[name] = {"ms_per_step": ms, "value": wl.samples_per_step / (ms / 1e3) / 1e9}
+    ddc.close()
+    plan.close()
+    return {"value": res["ddc_and_plan"]["value"], "unit": UNIT,
+            "config": {"decimation": D, "taps_per_phase": Th, "center_frequency": fc,
+                       "narrow_band_channels": 8192, "narrow_band_taps": 16},
+            "ddc_only": res["ddc_only"], "ddc_and_plan": res["ddc_and_plan"]}
+
+
 def _tuned_split(fengine, wl, prec, args):
     """The work split of the plan: the autotuner's pick (fengine_autotune) unless --no-autotune."""
     if args.split:
@@ -699,6 +746,7 @@ def main(argv=None):
         ab.steps, ab.warmup = min(args.steps, 10), 3
         extra["batched"] = batched_result(ab, fengine, torch)
         extra["service"] = service_result(args, fengine, torch)
+        extra["narrowband"] = narrowband_result(args, fengine, torch, wl, d_in)
 
     if rank != 0:
         if ws > 1:

@@ -420,6 +420,59 @@ fengine_status fengine_ingest_poll(fengine_ingest_t ing, void *cuda_stream, int3
                                    int64_t *first_spectrum);
 fengine_status fengine_ingest_get_stats(fengine_ingest_t ing, fengine_ingest_stats *out);
 
+/* ---- narrow-band mode (Sec. 6 names a narrow-band mode with a low-pass
+ * filter before the PFB; this is the library's reading of it) ----
+ * A down-converter turns the wide-band stream into a real stream at 2/D of
+ * its rate whose positive frequencies are the band [fc - 1/(2D),
+ * fc + 1/(2D)] (cycles per input sample): per stream,
+ *   y[j] = 2 g Re( i^j sum_{u < Lh} h[u] x[j D/2 - u] exp(-2 pi i fc (j D/2 - u)) )
+ * (mix the band's centre to 0, low-pass with the real h, move the band's
+ * lower edge to 0, real part, keep every (D/2)-th sample), requantised to
+ * 10 bits (round half away from zero, saturate to [-511, 511]) and packed
+ * like the digitiser's stream (10 bits per sample, MSB first). Input
+ * frequency f appears at (f - fc) D/2 + 1/4 cycles per output sample, so an
+ * ordinary plan over the output channelizes the band into finer channels;
+ * the wide-band plan can run on the same input chunks. */
+typedef struct fengine_ddc_s *fengine_ddc_t;
+
+typedef struct {
+    int32_t n_antennas;        /* streams = 2 n_antennas */
+    int32_t decimation;        /* D: 2, 4, 8, 16 or 32; the band is 1/D of the input rate */
+    int32_t taps_per_phase;    /* Th: the low-pass has Lh = D Th taps, 1 <= Th, Lh <= 2048 */
+    int32_t reserved;          /* 0 */
+    int64_t chunk_samples;     /* L input samples per pol per call: a multiple of 2D, >= Lh */
+    double center_frequency;   /* fc, cycles per input sample, in [0, 0.5) */
+    float gain;                /* g, applied before the 10-bit requantisation */
+    const float *filter;       /* host, Lh taps h[u]; NULL = built-in Hann-windowed sinc with
+                                  cutoff 1/(2D) and unit DC gain (fengine_ddc_default_filter) */
+} fengine_ddc_config;
+
+/* The built-in low-pass: h[u] = sin^2(pi (u + 1/2) / Lh) sinc((u + 1/2 - Lh/2) / D),
+ * scaled to sum h = 1; out: host, D Th floats. FENGINE_EINVAL for a bad shape. */
+fengine_status fengine_ddc_default_filter(int32_t decimation, int32_t taps_per_phase, float *out);
+
+/* The down-converter owns its history (the last Lh samples of every stream,
+ * zero before a stream's first chunk) and its filter table on the current
+ * device. */
+fengine_status fengine_ddc_create(const fengine_ddc_config *cfg, fengine_ddc_t *out);
+fengine_status fengine_ddc_destroy(fengine_ddc_t ddc);
+/* Forget the history: the next call may start at any first_sample. */
+fengine_status fengine_ddc_reset(fengine_ddc_t ddc);
+
+/* One chunk of every stream.
+ *   d_packed     device, 4-byte aligned, [antenna][pol][5L/4] bytes: input
+ *                samples [first_sample, first_sample + L).
+ *   first_sample a multiple of 2D; after the first call (or a reset) the
+ *                previous first_sample + L, else FENGINE_ESEQ.
+ *   d_out        device, 4-byte aligned, [antenna][pol][5 L' / 4] bytes,
+ *                L' = 2L/D: output samples j = 2 first_sample / D + k,
+ *                k in [0, L'), packed 10 bits per sample.
+ *   d_out_float  optional device FP32 [antenna][pol][L']: y before
+ *                requantisation (NULL to skip).
+ * Asynchronous on cuda_stream. */
+fengine_status fengine_ddc_process(fengine_ddc_t ddc, void *cuda_stream, const uint8_t *d_packed,
+                                   int64_t first_sample, uint8_t *d_out, float *d_out_float);
+
 /* ---- no-allocation variant (the paper has no counterpart) ----
  * For callers that cannot allocate device memory: a process whose device
  * memory is handed out in full by another allocator (a framework's caching

@@ -34,7 +34,9 @@ EXPORTS = ("fengine_strerror", "fengine_last_error", "fengine_abi_version", "fen
            "fengine_service_set_gains", "fengine_service_wait", "fengine_service_get_stats",
            "fengine_service_destroy", "fengine_process_chunk_noalloc", "fengine_autotune",
            "fengine_autotune_cached", "fengine_device_status", "fengine_ingest_create",
-           "fengine_ingest_destroy", "fengine_ingest_push", "fengine_ingest_poll", "fengine_ingest_get_stats")
+           "fengine_ingest_destroy", "fengine_ingest_push", "fengine_ingest_poll", "fengine_ingest_get_stats",
+           "fengine_ddc_default_filter", "fengine_ddc_create", "fengine_ddc_destroy", "fengine_ddc_reset",
+           "fengine_ddc_process")
 
 
 class FEngineError(RuntimeError):
@@ -505,6 +507,82 @@ class Ingest:
     def close(self):
         if getattr(self, "_h", None):
             _check(load().fengine_ingest_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DdcConfig(ctypes.Structure):
+    _fields_ = [("n_antennas", ctypes.c_int32), ("decimation", ctypes.c_int32),
+                ("taps_per_phase", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("chunk_samples", ctypes.c_int64), ("center_frequency", ctypes.c_double),
+                ("gain", ctypes.c_float), ("filter", ctypes.POINTER(ctypes.c_float))]
+
+
+def _ddc_signatures(lib):
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.fengine_ddc_default_filter.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_float)]
+    lib.fengine_ddc_create.argtypes = [ctypes.POINTER(DdcConfig), ctypes.POINTER(vp)]
+    lib.fengine_ddc_destroy.argtypes = [vp]
+    lib.fengine_ddc_reset.argtypes = [vp]
+    lib.fengine_ddc_process.argtypes = [vp, vp, vp, i64, vp, vp]
+    for name in ("fengine_ddc_default_filter", "fengine_ddc_create", "fengine_ddc_destroy", "fengine_ddc_reset",
+                 "fengine_ddc_process"):
+        getattr(lib, name).restype = ctypes.c_int
+
+
+def ddc_default_filter(decimation: int, taps_per_phase: int) -> np.ndarray:
+    """fengine_ddc_default_filter: the narrow-band mode's built-in low-pass."""
+    lib = load()
+    _ddc_signatures(lib)
+    out = np.empty(decimation * taps_per_phase, np.float32)
+    _check(lib.fengine_ddc_default_filter(decimation, taps_per_phase,
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+class DDC:
+    """Narrow-band front end (fengine_ddc_*): the wide-band stream down-converted
+    to a real 10-bit stream at 2/D of its rate holding the band around fc."""
+
+    def __init__(self, n_antennas: int, decimation: int, taps_per_phase: int, chunk_samples: int,
+                 center_frequency: float, gain: float = 1.0, filter=None):
+        lib = load()
+        _ddc_signatures(lib)
+        self._filt = None if filter is None else np.ascontiguousarray(filter, np.float32)
+        cfg = DdcConfig(n_antennas, decimation, taps_per_phase, 0, chunk_samples, center_frequency, gain,
+                        None if self._filt is None else self._filt.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        h = ctypes.c_void_p()
+        _check(lib.fengine_ddc_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.n_antennas, self.decimation, self.chunk_samples = n_antennas, decimation, chunk_samples
+        self.out_samples = 2 * chunk_samples // decimation
+
+    def process(self, packed, first_sample: int, out, out_float=None, stream=None):
+        """packed: uint8 CUDA tensor [ant, pol, 5L/4]; out: uint8 CUDA tensor
+        [ant, pol, 5L'/4], L' = 2L/D; out_float: optional float32 CUDA tensor [ant, pol, L']."""
+        import torch
+        if packed.numel() != self.n_antennas * 2 * self.chunk_samples * 5 // 4:
+            raise ValueError("packed size mismatch")
+        if out.numel() != self.n_antennas * 2 * self.out_samples * 5 // 4:
+            raise ValueError("out size mismatch")
+        if out_float is not None and out_float.numel() != self.n_antennas * 2 * self.out_samples:
+            raise ValueError("out_float size mismatch")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(load().fengine_ddc_process(self._h, ctypes.c_void_p(s.cuda_stream), packed.data_ptr(), first_sample,
+                                          out.data_ptr(),
+                                          out_float.data_ptr() if out_float is not None else None))
+
+    def reset(self):
+        _check(load().fengine_ddc_reset(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().fengine_ddc_destroy(self._h))
             self._h = None
 
     def __del__(self):

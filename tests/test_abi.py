@@ -167,3 +167,30 @@ def test_ingest_and_tune_cache_refuse_bad_arguments_before_any_device_call(lib, 
     assert lib.fengine_autotune_cached(ctypes.byref(c), None, 0, path, ctypes.byref(tuned),
                                        ctypes.byref(hit)) == EINVAL
     assert not (tmp_path / "tune.jsonl").exists()
+
+
+@pytest.mark.parametrize("D,Th", [(2, 16), (8, 16), (32, 4), (16, 128)])
+def test_ddc_default_filter_matches_oracle(lib, D, Th):
+    h = fengine.ddc_default_filter(D, Th)
+    np.testing.assert_allclose(h, O.ddc_weights(D, Th), rtol=2e-7, atol=1e-9)
+
+
+def test_ddc_refuses_bad_configuration_before_any_device_call(lib):
+    EINVAL = 1
+    fengine._ddc_signatures(lib)
+    h = ctypes.c_void_p()
+    ok = dict(n_antennas=1, decimation=8, taps_per_phase=16, reserved=0, chunk_samples=8 * 1024,
+              center_frequency=0.2, gain=1.0, filter=None)
+    for bad in (dict(n_antennas=0), dict(decimation=6), dict(decimation=64), dict(taps_per_phase=0),
+                dict(taps_per_phase=300), dict(reserved=1), dict(chunk_samples=8 * 1024 + 8),
+                dict(chunk_samples=64), dict(center_frequency=0.5), dict(center_frequency=-0.1),
+                dict(center_frequency=float("nan")), dict(gain=float("inf"))):
+        cfg = fengine.DdcConfig(**{**ok, **bad})
+        assert lib.fengine_ddc_create(ctypes.byref(cfg), ctypes.byref(h)) == EINVAL, bad
+    assert lib.fengine_ddc_create(None, ctypes.byref(h)) == EINVAL
+    assert lib.fengine_ddc_destroy(None) == EINVAL
+    assert lib.fengine_ddc_reset(None) == EINVAL
+    assert lib.fengine_ddc_process(None, None, None, 0, None, None) == EINVAL
+    out = (ctypes.c_float * 8)()
+    assert lib.fengine_ddc_default_filter(6, 4, out) == EINVAL
+    assert lib.fengine_ddc_default_filter(8, 0, out) == EINVAL

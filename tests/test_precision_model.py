@@ -1,75 +1,106 @@
-"""Why the tensor-core second stage splits its operands (no GPU needed).
+"""Where the FP16 tensor-core form's error comes from (no GPU needed).
 
-The reduced-precision forms compute the 1024-point DFT of a class sequence
-as two 32-point DFT contractions (t2 = 32 a + b, k2 = c + 32 d):
-Y = W32 . B, Y' = twiddle * Y, F = Y' . W32^T. This model replays that order
-in numpy with FP16 rounding at the points the kernel rounds (the FP16
-intermediate B, the DFT matrices, the data between the contractions) and
-measures the largest error of F relative to the largest channel of the
-sequence, for sequences that hold two strong tones over weak noise (a strong
-tone dominates its class sequence in the workloads). With single FP16
-operands the error reaches ~1e-4 of the tone: an 8-bit output next to a
-tone of amplitude 1e4 is then off by more than 1 LSB. Carrying the DFT
-matrices and the mid data as hi + lo pairs (2 products in contraction 1,
-3 in contraction 2) leaves the FP16 intermediate's own rounding, a few 1e-5.
+The FP16 form computes the FIR and the first DFT stage as one contraction
+per output column t2, B[k1][t2] = sum_k x[t2 + P k] W_t2[k][k1], with the
+data exact in FP16 (10-bit integers), the operand block W_t2 (weights x DFT
+x twiddle) rounded to FP16 after a power-of-two scale of its own, FP32
+accumulation, and B stored as FP16 after one global power-of-two scale;
+the second stage is FP32. This model replays those roundings in numpy on a
+1024-channel, 16-tap PFB (N1 = 8, N2 = 256) and checks that
+
+  * the relative RMS error of the spectra sits far inside the 2e-3 bar,
+    at the level the GPU measures for the FP16 form (a few 1e-4);
+  * the two FP16 roundings contribute errors of the same order, and
+    neither scale leaves the FP16 range;
+  * the BF16 form's hi + lo split of data and operands (three products)
+    brings the contraction's error down by more than an order of magnitude.
 """
 import numpy as np
 
-n = np.arange(32)
-W = np.exp(-2j * np.pi * np.outer(n, n) / 32)
-TW = np.exp(-2j * np.pi * np.outer(n, n) / 1024) / 32
+from oracle import oracle as O
+
+N, T, N1 = 2048, 16, 8
+P, N2 = N // 8, N // N1
+n = N // 2
 
 
-def h16(x):
-    return x.real.astype(np.float16).astype(np.float64) + 1j * x.imag.astype(np.float16).astype(np.float64)
+def _f16(a):
+    return a.astype(np.float16).astype(np.float64)
 
 
-def split(x):
-    hi = h16(x)
-    return hi, h16(x - hi)
+def _bf16(a):
+    """Round to BF16 (8 significant bits), nearest even, via the FP32 bit pattern."""
+    f = np.asarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def single(x):
-    X = h16(x).reshape(32, 32)            # [a][b]
-    Y = h16(h16(W) @ X * TW)
-    F = Y @ h16(W).T
-    return (32 * F).T.reshape(-1)        # k2 = c + 32 d
+def _operands():
+    w = O.pfb_weights(N, T)
+    k = np.arange(8 * T)
+    Wt = np.empty((P, 8 * T, N1), np.complex128)
+    for t in range(P):
+        ph = np.outer(P * (k % 8) + t, np.arange(N1)) / N
+        Wt[t] = w[t + P * k][:, None] * np.exp(-2j * np.pi * ph)
+    return w, Wt
 
 
-def split_form(x):
-    X = h16(x).reshape(32, 32)
-    Wh, Wl = split(W)
-    Yh, Yl = split((Wh @ X + Wl @ X) * TW)
-    F = Yh @ Wh.T + Yh @ Wl.T + Yl @ Wh.T
-    return (32 * F).T.reshape(-1)
+def _spectra(x, Wt, mode):
+    """Spectra k < n of windows x[m] (rows: spectra) in one of the forms."""
+    M = x.shape[0]
+    k = np.arange(8 * T)
+    A = np.stack([x[:, t + P * k] for t in range(P)], axis=1)       # [m][t][k]
+    if mode == "exact":
+        B = np.einsum("mtk,tkc->mct", A, Wt)
+    else:
+        # per-column power of two: the block's largest entry just below 2^15
+        bmax = np.max(np.abs(np.concatenate([Wt.real, Wt.imag], axis=1)), axis=(1, 2))
+        sB = 2.0 ** np.floor(np.log2(32768.0 / bmax))
+        Ws = Wt * sB[:, None, None]
+        if mode == "fp16":
+            Wq = _f16(Ws.real) + 1j * _f16(Ws.imag)
+            B = np.einsum("mtk,tkc->mct", A, Wq) / sB[None, None, :]
+            # the FP16 intermediate, one global power of two from |B| <= 512 sum |w|
+            bound = 512.0 * np.max(np.sum(np.abs(Wt), axis=1))
+            s_int = 2.0 ** np.floor(np.log2(32768.0 / bound))
+            assert np.max(np.abs(Ws)) < 65504 and np.max(np.abs(B)) * s_int < 65504
+            B = (_f16(B.real * s_int) + 1j * _f16(B.imag * s_int)) / s_int
+        elif mode == "fp16_operands_only":
+            Wq = _f16(Ws.real) + 1j * _f16(Ws.imag)
+            B = np.einsum("mtk,tkc->mct", A, Wq) / sB[None, None, :]
+        else:   # bf16: x = x_hi + x_lo, W = W_hi + W_lo, three products
+            xh = _bf16(A)
+            xl = A - xh
+            Wh = _bf16(Ws.real) + 1j * _bf16(Ws.imag)
+            Wl = (_bf16(Ws.real - Wh.real) + 1j * _bf16(Ws.imag - Wh.imag))
+            B = (np.einsum("mtk,tkc->mct", xh, Wh) + np.einsum("mtk,tkc->mct", xl, Wh)
+                 + np.einsum("mtk,tkc->mct", xh, Wl)) / sB[None, None, :]
+    # second stage (exact here): X[k1 + N1 k2] = sum_t2 exp(-2 pi i k2 t2 / N2) B[k1][t2]
+    X = np.fft.fft(B, axis=2)                                       # [m][k1][k2]
+    X = X.transpose(0, 2, 1).reshape(M, N)                          # index k1 + N1 k2
+    return X[:, :n]
 
 
-def _errors(seeds):
-    t = np.arange(1024)
-    out = []
-    for seed in seeds:
-        g = np.random.default_rng(seed)
-        x = g.normal(size=1024) + 1j * g.normal(size=1024)
-        for k, A in zip(g.uniform(0, 1024, 2), (58.0, 96.0)):
-            x = x + A * np.exp(2j * np.pi * k * t / 1024 + 1j * g.uniform(0, 2 * np.pi))
-        ref = np.fft.fft(x)
-        top = np.abs(ref).max()
-        out.append((np.abs(single(x) - ref).max() / top, np.abs(split_form(x) - ref).max() / top))
-    return np.array(out)
+def test_fp16_form_error_budget():
+    g = np.random.default_rng(3)
+    M = 24
+    i = np.arange(M * N + N * T)
+    sig = 40 * g.standard_normal(i.size) + 90 * np.cos(2 * np.pi * 0.1234 * i)
+    s = np.clip(np.rint(sig), -512, 511)
+    x = np.stack([s[m * N:m * N + N * T] for m in range(M)])
+    w, Wt = _operands()
+    ref = _spectra(x, Wt, "exact")
+    # the exact contraction is the PFB + DFT itself (closed form of Eq. 1 + DFT)
+    g_fir = np.stack([np.sum((w * x[m]).reshape(T, N), axis=0) for m in range(M)])
+    np.testing.assert_allclose(ref, np.fft.fft(g_fir, axis=1)[:, :n], rtol=0, atol=1e-8 * np.abs(ref).max())
 
+    def rel(a):
+        return np.sqrt(np.sum(np.abs(a - ref) ** 2) / np.sum(np.abs(ref) ** 2))
 
-def test_contraction_order_reproduces_the_fft():
-    x = np.random.default_rng(0).normal(size=1024) + 0j
-    Y = (W @ x.reshape(32, 32)) * TW
-    F = (32 * (Y @ W.T)).T.reshape(-1)
-    np.testing.assert_allclose(F, np.fft.fft(x), rtol=0, atol=1e-9)
-
-
-def test_single_fp16_operands_miss_the_8bit_bar_next_to_tones_and_split_operands_meet_it():
-    e = _errors(range(40))
-    # single FP16 operands: errors of the order of 1e-4 of the strongest channel
-    assert e[:, 0].max() > 1e-4
-    assert np.median(e[:, 0]) > 5e-5
-    # split operands: only the FP16 intermediate's rounding is left
-    assert e[:, 1].max() < 5e-5
-    assert np.all(e[:, 1] < e[:, 0] / 2)
+    e16, e_op, ebf = rel(_spectra(x, Wt, "fp16")), rel(_spectra(x, Wt, "fp16_operands_only")), \
+        rel(_spectra(x, Wt, "bf16"))
+    print(f"[precision model] FP16 form {e16:.3g} (operand rounding alone {e_op:.3g}), BF16 form {ebf:.3g}")
+    assert 3e-5 < e16 < 5e-4                     # the GPU measures 2e-4 .. 3e-4; the bar is 2e-3
+    assert 0.2 < e_op / e16 < 0.95               # both roundings matter, neither alone explains it
+    assert ebf < e16 / 10
