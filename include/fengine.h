@@ -246,8 +246,9 @@ fengine_status fengine_autotune(const fengine_config *cfg, void *cuda_stream, in
                                 int32_t *n_entries);
 
 /* fengine_autotune with its pick kept in a JSON Lines file (one object per
- * line: device name, SM count, ABI version, the shape fields of cfg,
- * precision, and the chosen fft_n1, slab_spectra, ms_per_call). A line whose
+ * line: device name, SM count, a hash of the library's sources, ABI version,
+ * the shape fields of cfg, precision, and the chosen fft_n1, slab_spectra,
+ * ms_per_call). A line whose
  * key fields all match cfg on the current device, and whose split still makes
  * a valid plan, is returned without timing anything (*from_cache = 1);
  * otherwise the split is tuned as fengine_autotune does and the file is

@@ -39,6 +39,18 @@ def _deps():
             glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
+def source_hash() -> str:
+    """Hash of every source and header the library is built from (it keys the
+    autotuner's cache, so that a pick made on other sources is not reused)."""
+    import hashlib
+    h = hashlib.sha256()
+    for d in sorted(_deps(), key=os.path.basename):
+        h.update(os.path.basename(d).encode())
+        with open(d, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
@@ -52,10 +64,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     srcs = _sources()
+    src_hash = source_hash()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, f"-DFENGINE_SRC_HASH=\"{src_hash}\"", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -94,8 +94,9 @@ struct fengine_plan_s {
     // slab pipeline: phase 1 of slab s+1 overlaps phase 2 of slab s on two
     // internal streams; the intermediate of a slab stays in L2
     int SL = 0, n_slabs = 0;
-    cudaStream_t sp[2] = {nullptr, nullptr};
+    cudaStream_t sp[3] = {nullptr, nullptr, nullptr};   // phase 1, phase 2, column unpack
     cudaEvent_t ev_fork = nullptr, ev_p1[2] = {nullptr, nullptr}, ev_p2[2] = {nullptr, nullptr};
+    cudaEvent_t ev_u[2] = {nullptr, nullptr};            // column unpack of a slab done
     // optional per-stage timing: (stage, start, end) event records
     bool profiling = false;
     std::vector<cudaEvent_t> prof_events;
@@ -147,8 +148,10 @@ void release(fengine_plan_s *pl) {
         if (pl->ev_p1[i]) cudaEventDestroy(pl->ev_p1[i]);
         if (pl->ev_p2[i]) cudaEventDestroy(pl->ev_p2[i]);
         if (pl->sp[i]) cudaStreamDestroy(pl->sp[i]);
+        if (pl->ev_u[i]) cudaEventDestroy(pl->ev_u[i]);
     }
     if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+    if (pl->sp[2]) cudaStreamDestroy(pl->sp[2]);
     delete pl;
 }
 
@@ -368,10 +371,12 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
     for (int i = 0; i < 2 && e == cudaSuccess; i++) {
         if ((e = cudaStreamCreateWithFlags(&pl->sp[i], cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&pl->ev_p1[i], cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&pl->ev_p2[i], cudaEventDisableTiming)) != cudaSuccess)
+            (e = cudaEventCreateWithFlags(&pl->ev_p2[i], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&pl->ev_u[i], cudaEventDisableTiming)) != cudaSuccess)
             break;
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->sp[2], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         release(pl);
         return cuda_fail(e, "stream/event creation");
@@ -717,12 +722,17 @@ fengine_status process_impl(fengine_plan_t pl, void *cuda_stream, const uint8_t 
     p2.tc_unscale = pl->tc_unscale;
 
     fe::Phase1TcParams pt{};
+    // with several slabs the column unpack goes slab by slab on its own
+    // internal stream, ahead of the phase 1 that needs it: the unpack of slab
+    // s + 1 runs on the SMs beside the tensor-core phase 1 of slab s (one
+    // unpack CTA fits next to it in shared memory and registers)
+    const bool split_unpack = pl->tc1 && pl->n_slabs > 1 && (pl->N / 8) % 64 == 0 && !def;
+    fe::UnpackColsParams up{};
     if (pl->tc1) {
         // unpack history + chunk into FP16 column sequences (row origin a
         // multiple of 8, so that 16-byte copies of a column stay aligned)
         const long long P = pl->N / 8;
         auto fdiv = [](long long a, long long b) { return a / b - ((a % b != 0 && a < 0) ? 1 : 0); };
-        fe::UnpackColsParams up{};
         up.chunk = d_packed;
         up.hist = pl->d_hist[pl->cur];
         up.chunk_bytes = pl->chunk_bytes;
@@ -739,9 +749,13 @@ fengine_status process_impl(fengine_plan_t pl, void *cuda_stream, const uint8_t 
         up.RTP = pl->cols_rtp;
         up.cols = pl->d_cols;
         up.n_streams = pl->n_streams;
-        prof_begin(pl, 4, st);
-        if ((e = fe::launch_unpack_cols(up, st)) != cudaSuccess) return cuda_fail(e, "unpack launch");
-        prof_end(pl, st);
+        up.row_begin = 0;
+        up.row_end = pl->cols_rtp;
+        if (!split_unpack) {
+            prof_begin(pl, 4, st);
+            if ((e = fe::launch_unpack_cols(up, st)) != cudaSuccess) return cuda_fail(e, "unpack launch");
+            prof_end(pl, st);
+        }
         pt.cols = pl->d_cols;
         pt.rb = up.rb;
         pt.RTP = pl->cols_rtp;
@@ -800,8 +814,10 @@ fengine_status process_impl(fengine_plan_t pl, void *cuda_stream, const uint8_t 
     const size_t slab_elems = (size_t)pl->n_streams * pl->SL * (pl->N1 / 2 + 1) * pl->N2;
     if ((e = cudaEventRecord(pl->ev_fork, st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(pl->sp[0], pl->ev_fork, 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(pl->sp[1], pl->ev_fork, 0)) != cudaSuccess)
+        (e = cudaStreamWaitEvent(pl->sp[1], pl->ev_fork, 0)) != cudaSuccess ||
+        (split_unpack && (e = cudaStreamWaitEvent(pl->sp[2], pl->ev_fork, 0)) != cudaSuccess))
         return cuda_fail(e, "slab fork");
+    int unpacked = 0;   // column rows [0, unpacked) enqueued so far
     for (int s = 0; s < pl->n_slabs; s++) {
         const int b = s & 1;
         float2 *A = reinterpret_cast<float2 *>(reinterpret_cast<char *>(pl->d_A) + (size_t)b * slab_elems * pl->a_elem);
@@ -809,6 +825,31 @@ fengine_status process_impl(fengine_plan_t pl, void *cuda_stream, const uint8_t 
         const int qc = (pl->M - qb) < pl->SL ? (pl->M - qb) : pl->SL;
         if (s >= 2 && (e = cudaStreamWaitEvent(pl->sp[0], pl->ev_p2[b], 0)) != cudaSuccess)
             return cuda_fail(e, "slab wait");
+        if (split_unpack) {
+            // the rows this slab's passes can read: the last tile's column
+            // sequences (8 (127 + T') rows from row 8 (m0 + q0) - rb), moved by
+            // at most (D - Dmin) / P + 1 rows for a pass whose delay differs from
+            // the unpack's, plus the realigned copy's extra 16-byte chunk
+            int hi = pl->cols_rtp;
+            if (s + 1 < pl->n_slabs) {
+                const long long q_last = qb + (long long)((qc - 1) / 128) * 128;
+                const long long shift = (pl->D - pl->Dmin) / (pl->N / 8) + 2;
+                const long long rows = 8 * (m0 + q_last) - up.rb + shift + 8LL * (127 + (pl->T < 2 ? 2 : pl->T)) + 16;
+                const long long r64 = (rows + 63) / 64 * 64;
+                hi = (int)(r64 < pl->cols_rtp ? r64 : pl->cols_rtp);
+            }
+            if (hi > unpacked) {
+                up.row_begin = unpacked;
+                up.row_end = hi;
+                prof_begin(pl, 4, pl->sp[2]);
+                if ((e = fe::launch_unpack_cols(up, pl->sp[2])) != cudaSuccess) return cuda_fail(e, "unpack launch");
+                prof_end(pl, pl->sp[2]);
+                unpacked = hi;
+            }
+            if ((e = cudaEventRecord(pl->ev_u[b], pl->sp[2])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(pl->sp[0], pl->ev_u[b], 0)) != cudaSuccess)
+                return cuda_fail(e, "unpack handoff");
+        }
         p1.A = A;
         p1.q_begin = qb;
         p1.q_count = qc;

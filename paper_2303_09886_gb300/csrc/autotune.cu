@@ -122,8 +122,8 @@ extern "C" fengine_status fengine_autotune(const fengine_config *cfg, void *cuda
 
 // ---- the tuner's pick cached in a JSON Lines file --------------------------
 // One JSON object per line; a line applies to a configuration when every key
-// field matches (device name and SM count, ABI version, the shape fields of
-// fengine_config and the precision). Lines this code does not recognise are
+// field matches (device name and SM count, the hash of the library's sources,
+// ABI version, the shape fields of fengine_config and the precision). Lines this code does not recognise are
 // kept as they are when the file is rewritten.
 namespace {
 
@@ -131,8 +131,12 @@ const char *kCacheInts[] = {"sms", "abi", "n_antennas", "n_channels", "n_taps", 
                             "spectra_per_heap", "max_delay_samples", "min_delay_samples", "precision"};
 constexpr int kCacheNInts = 10;
 
+#ifndef FENGINE_SRC_HASH
+#define FENGINE_SRC_HASH "unknown"
+#endif
+
 struct CacheKey {
-    std::string device;
+    std::string device, src;
     long long v[kCacheNInts];
 };
 
@@ -163,6 +167,7 @@ bool cache_key(const fengine_config *cfg, CacheKey *k) {
     cudaDeviceProp prop;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
     k->device = prop.name;
+    k->src = FENGINE_SRC_HASH;
     for (char &ch : k->device)
         if (ch == '"' || ch == '\\' || (unsigned char)ch < 0x20) ch = '_';
     const long long vals[kCacheNInts] = {prop.multiProcessorCount, fengine_abi_version(), cfg->n_antennas,
@@ -174,8 +179,9 @@ bool cache_key(const fengine_config *cfg, CacheKey *k) {
 }
 
 bool line_matches(const std::string &line, const CacheKey &k) {
-    std::string dev;
+    std::string dev, src;
     if (!json_str(line, "device", &dev) || dev != k.device) return false;
+    if (!json_str(line, "src", &src) || src != k.src) return false;
     for (int i = 0; i < kCacheNInts; ++i) {
         long long v;
         if (!json_int(line, kCacheInts[i], &v) || v != k.v[i]) return false;
@@ -231,7 +237,8 @@ extern "C" fengine_status fengine_autotune_cached(const fengine_config *cfg, voi
     for (int i = 0; i < n; ++i)
         if (entries[i].fft_n1 == tuned->fft_n1 && entries[i].slab_spectra == tuned->slab_spectra) ms = entries[i].ms_per_call;
     char rec[1024];
-    int len = std::snprintf(rec, sizeof rec, "{\"device\": \"%s\"", key.device.c_str());
+    int len = std::snprintf(rec, sizeof rec, "{\"device\": \"%s\", \"src\": \"%s\"", key.device.c_str(),
+                            key.src.c_str());
     for (int i = 0; i < kCacheNInts && len > 0 && len < (int)sizeof rec; ++i)
         len += std::snprintf(rec + len, sizeof rec - len, ", \"%s\": %lld", kCacheInts[i], key.v[i]);
     if (len > 0 && len < (int)sizeof rec)

@@ -196,6 +196,8 @@ struct UnpackColsParams {
     int P;                    // N / 8
     long long rb;             // absolute row of column row 0 (a multiple of 8)
     int RT, RTP;              // rows holding samples; rows per column (padded, a multiple of 64)
+    int row_begin, row_end;   // the launch writes rows [row_begin, row_end) (multiples of 64;
+                              // [0, RTP) for the whole buffer)
     uint16_t *cols;           // out [stream][P][RTP] FP16, pre-delayed by ctab[stream][0]
     const int *ctab;          // [stream][M] coarse delays
     int M;

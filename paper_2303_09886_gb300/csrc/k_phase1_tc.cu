@@ -277,13 +277,13 @@ __device__ __forceinline__ bool warp_next_pass(PassIter &s, Pass &ps, const Phas
 // for every pass with coarse delay c0 a FIR column's sequence x_t[u] starts
 // at a row that is a multiple of 8 (16-byte aligned) and is read as one
 // contiguous block. Tile: 64 rows x 64 columns per CTA: the packed rows are
-// read as aligned 32-bit words (24 per 64-sample segment, all segments of a
-// tile at one bit offset), a thread converts 8 samples of two rows into FP16
-// pairs, and the tile is written out column by column.
+// read as aligned 32-bit words straight from global memory (five per
+// 8-sample run of a row; neighbouring threads share words through L1), a
+// thread converts 8 samples of two rows into FP16 pairs, and the tile goes
+// through shared memory once to be written out column by column.
 __global__ void __launch_bounds__(256) k_unpack_cols(const UnpackColsParams p) {
-    __shared__ uint32_t raw[64][25];     // words 0 .. 23 of each row segment (the last ones only feed shifts)
     __shared__ uint32_t tile[64][33];    // [column][row pair] FP16 pairs
-    const int col0 = blockIdx.x * 64, r0 = blockIdx.y * 64, st = blockIdx.z;
+    const int col0 = blockIdx.x * 64, r0 = p.row_begin + blockIdx.y * 64, st = blockIdx.z;
     const int tid = threadIdx.x;
     const long long c0 = p.ctab[(long long)st * p.M];
     // relative sample (from the first history sample) of row 0, column col0;
@@ -291,39 +291,33 @@ __global__ void __launch_bounds__(256) k_unpack_cols(const UnpackColsParams p) {
     const long long rel00 = (p.rb + r0) * (long long)p.P + col0 - c0 - (p.t_in - p.H);
     const long long bit00 = 10 * rel00;
     const int off = (int)(bit00 & 31);   // the same for every row (10 P is a multiple of 32)
-    {
-        // thread: row tid / 4, words 6 part .. 6 part + 5 of the row segment
-        const int row = tid >> 2, part = tid & 3;
-        const uint32_t *hw = reinterpret_cast<const uint32_t *>(p.hist + (long long)st * p.hist_bytes);
-        const uint32_t *cw = reinterpret_cast<const uint32_t *>(p.chunk + (long long)st * p.chunk_bytes);
-        const long long hwords = 10 * p.H / 32, cwords = p.chunk_bytes / 4;
-        const long long w0 = ((bit00 + (long long)row * 10 * p.P) >> 5) + 6 * part;
-        const bool live = r0 + row < p.RT;
-        uint32_t v[6];
-#pragma unroll
-        for (int i = 0; i < 6; i++) {
-            const long long w = w0 + i;
-            v[i] = 0u;
-            if (live && w >= 0) {
-                if (w < hwords) v[i] = __ldg(hw + w);
-                else if (w - hwords < cwords) v[i] = __ldg(cw + (w - hwords));
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 6; i++) raw[row][6 * part + i] = __byte_perm(v[i], 0u, 0x0123u);   // big-endian bits
-    }
-    __syncthreads();
+    const uint32_t *hw = reinterpret_cast<const uint32_t *>(p.hist + (long long)st * p.hist_bytes);
+    const uint32_t *cw = reinterpret_cast<const uint32_t *>(p.chunk + (long long)st * p.chunk_bytes);
+    const long long hwords = 10 * p.H / 32, cwords = p.chunk_bytes / 4;
     {
         // thread: rows 2 rp, 2 rp + 1, samples 8 g .. 8 g + 7 (bits off + 80 g .. + 80)
         const int rp = tid >> 3, g = tid & 7;
-        const int b0 = off + 80 * g, w0 = b0 >> 5, sh = b0 & 31;
+        const int b0 = off + 80 * g, wi = b0 >> 5, sh = b0 & 31;
         uint32_t f[2][8];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int row = 2 * rp + h;
+            const long long wrow = ((bit00 + (long long)row * 10 * p.P) >> 5) + wi;
+            const bool live = r0 + row < p.RT;
+            uint32_t raw[5];
+#pragma unroll
+            for (int i = 0; i < 5; i++) {
+                const long long w = wrow + i;
+                uint32_t v = 0u;
+                if (live && w >= 0) {
+                    if (w < hwords) v = __ldg(hw + w);
+                    else if (w - hwords < cwords) v = __ldg(cw + (w - hwords));
+                }
+                raw[i] = __byte_perm(v, 0u, 0x0123u);   // big-endian bits
+            }
             uint32_t a[4];
 #pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = __funnelshift_l(raw[row][w0 + i + 1], raw[row][w0 + i], (unsigned)sh);
+            for (int i = 0; i < 4; i++) a[i] = __funnelshift_l(raw[i + 1], raw[i], (unsigned)sh);
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 const int bb = 10 * k;
@@ -331,7 +325,7 @@ __global__ void __launch_bounds__(256) k_unpack_cols(const UnpackColsParams p) {
             }
             // samples before the first history sample, or rows past the data, are zero
             const long long rel = rel00 + (long long)row * p.P + 8 * g;
-            if (r0 + row >= p.RT || rel + 7 < 0) {
+            if (!live || rel + 7 < 0) {
 #pragma unroll
                 for (int k = 0; k < 8; k++) f[h][k] = 0u;
             } else if (rel < 0) {
@@ -909,12 +903,16 @@ static cudaError_t launch_tc_r(int R, int T, const Phase1TcParams &p, cudaStream
 
 cudaError_t launch_unpack_cols(const UnpackColsParams &p, cudaStream_t s) {
     if (p.RTP % 64) return cudaErrorInvalidValue;
+    if (p.row_begin % 64 || p.row_end % 64 || p.row_begin < 0 || p.row_end > p.RTP || p.row_end < p.row_begin)
+        return cudaErrorInvalidValue;
+    if (p.row_end == p.row_begin) return cudaSuccess;
     if (p.P % 64) {
+        if (p.row_begin != 0 || p.row_end != p.RTP) return cudaErrorInvalidValue;   // whole buffer only
         const long long total = (long long)p.n_streams * p.P * p.RTP;
         const long long blocks = (total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192;
         k_unpack_cols_small<<<(unsigned)blocks, 256, 0, s>>>(p);
     } else {
-        dim3 grid(p.P / 64, p.RTP / 64, p.n_streams);
+        dim3 grid(p.P / 64, (p.row_end - p.row_begin) / 64, p.n_streams);
         k_unpack_cols<<<grid, 256, 0, s>>>(p);
     }
     return cudaGetLastError();
