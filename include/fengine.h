@@ -441,7 +441,7 @@ typedef struct {
     int32_t decimation;        /* D: 2, 4, 8, 16 or 32; the band is 1/D of the input rate */
     int32_t taps_per_phase;    /* Th: the low-pass has Lh = D Th taps, 1 <= Th, Lh <= 2048 */
     int32_t reserved;          /* 0 */
-    int64_t chunk_samples;     /* L input samples per pol per call: a multiple of 2D, >= Lh */
+    int64_t chunk_samples;     /* L input samples per pol per call: a multiple of 2D and of 16, >= Lh */
     double center_frequency;   /* fc, cycles per input sample, in [0, 0.5) */
     float gain;                /* g, applied before the 10-bit requantisation */
     const float *filter;       /* host, Lh taps h[u]; NULL = built-in Hann-windowed sinc with

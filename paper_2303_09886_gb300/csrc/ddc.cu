@@ -32,7 +32,7 @@ constexpr int kDdcOut = kDdcThreads * kDdcPer;      // outputs per CTA
 struct DdcParams {
     const uint8_t *chunk, *hist;   // [stream][chunk_bytes], [stream][hist_bytes]
     long long chunk_bytes, hist_bytes;
-    long long L, H;                // chunk and history samples (H a multiple of 4, >= Lh)
+    long long L, H;                // chunk and history samples (H a multiple of 16, >= Lh)
     long long t_in;                // first input sample of the chunk
     long long j0;                  // first output of the call (= 2 t_in / D)
     int D2, lgD2, Th2, Lout;       // D / 2, log2(D / 2), Lh / (D / 2), outputs per stream
@@ -42,13 +42,6 @@ struct DdcParams {
     uint8_t *out;                  // [stream][5 Lout / 4]
     float *out_float;              // optional [stream][Lout]
 };
-
-__device__ __forceinline__ float sample10_at(const uint8_t *buf, long long s) {
-    const uint8_t *b = buf + ((5 * s) >> 2);
-    const unsigned w = ((unsigned)b[0] << 8) | (unsigned)b[1];
-    const int v = (int)((w >> (6u - 2u * (unsigned)(s & 3))) & 0x3FFu);
-    return (float)(v >= 512 ? v - 1024 : v);
-}
 
 // position of plane element k: one word of padding per 16 elements, so that
 // the 32 lanes of a warp, 16 elements apart, hit 32 different banks
@@ -74,12 +67,50 @@ __global__ void __launch_bounds__(kDdcThreads) k_ddc(const DdcParams p) {
     const uint8_t *chunk = p.chunk + (long long)st * p.chunk_bytes;
     const uint8_t *hist = p.hist + (long long)st * p.hist_bytes;
     const long long h0 = p.t_in - p.H;                      // first history sample
-    for (int o = threadIdx.x; o < D2 * K; o += kDdcThreads) {
-        const long long rel = i_base + o - h0;
-        float v = 0.0f;
-        if (rel >= 0 && rel < p.H) v = sample10_at(hist, rel);
-        else if (rel >= p.H && rel - p.H < p.L) v = sample10_at(chunk, rel - p.H);
-        xp[(o & (D2 - 1)) * KP + ppos(o >> p.lgD2)] = v;
+    // decode 8 consecutive samples per task from 32-bit words of the packed
+    // stream (history and chunk are one bit stream: 10 H is a multiple of
+    // 32), zero outside it
+    {
+        const uint32_t *hw = reinterpret_cast<const uint32_t *>(hist);
+        const uint32_t *cw = reinterpret_cast<const uint32_t *>(chunk);
+        const long long hwords = 10 * p.H / 32, cwords = p.chunk_bytes / 4, n_rel = p.H + p.L;
+        for (int e = threadIdx.x; 8 * e < D2 * K; e += kDdcThreads) {
+            const long long rel = i_base + 8 * e - h0;
+            uint32_t fld[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) fld[k] = 0x200u;   // offset binary: 0x200 is zero
+            if (rel + 8 > 0 && rel < n_rel) {
+                const long long bit = 10 * rel;
+                const long long w0 = bit >> 5;   // floor, also for negative rel
+                const unsigned sh = (unsigned)(bit & 31);
+                uint32_t wd[5];
+#pragma unroll
+                for (int i = 0; i < 5; i++) {
+                    const long long w = w0 + i;
+                    uint32_t x = 0u;
+                    if (w >= 0 && w < hwords) x = __ldg(hw + w);
+                    else if (w >= hwords && w - hwords < cwords) x = __ldg(cw + (w - hwords));
+                    wd[i] = __byte_perm(x, 0u, 0x0123u);   // big-endian bits
+                }
+                uint32_t a[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) a[i] = __funnelshift_l(wd[i + 1], wd[i], sh);
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const int bb = 10 * k;
+                    const uint32_t f = __funnelshift_l(a[(bb >> 5) + 1], a[bb >> 5], (unsigned)(bb & 31)) >> 22;
+                    fld[k] = (rel + k < 0 || rel + k >= n_rel) ? 0x200u : (f ^ 0x200u);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; k++) fld[k] = 0x200u;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int o = 8 * e + k;
+                if (o < D2 * K) xp[(o & (D2 - 1)) * KP + ppos(o >> p.lgD2)] = (float)((int)fld[k] - 512);
+            }
+        }
     }
     for (int u = threadIdx.x; u < Lh; u += kDdcThreads) tp[u] = __ldg(p.taps + u);
     __syncthreads();
@@ -211,7 +242,7 @@ extern "C" fengine_status fengine_ddc_create(const fengine_ddc_config *cfg, feng
         (long long)D * Th > 2048 || cfg->reserved != 0)
         return FENGINE_EINVAL;
     const long long Lh = (long long)D * Th;
-    if (cfg->chunk_samples <= 0 || cfg->chunk_samples % (2 * D) || cfg->chunk_samples < Lh ||
+    if (cfg->chunk_samples <= 0 || cfg->chunk_samples % (2 * D) || cfg->chunk_samples % 16 || cfg->chunk_samples < Lh ||
         cfg->chunk_samples > (1LL << 34))
         return FENGINE_EINVAL;
     if (!(cfg->center_frequency >= 0.0 && cfg->center_frequency < 0.5) || !std::isfinite(cfg->gain))
@@ -233,7 +264,7 @@ extern "C" fengine_status fengine_ddc_create(const fengine_ddc_config *cfg, feng
     d->Th = Th;
     d->Lh = (int)Lh;
     d->L = cfg->chunk_samples;
-    d->H = (Lh + 3) / 4 * 4;
+    d->H = (Lh + 15) / 16 * 16;
     d->hist_bytes = d->H / 4 * 5;
     d->chunk_bytes = d->L / 4 * 5;
     d->fc = cfg->center_frequency;
