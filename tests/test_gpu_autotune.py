@@ -75,3 +75,31 @@ def test_autotune_returns_a_measured_valid_split(n, precision):
                          fft_n1=best["fft_n1"], slab_spectra=best["slab_spectra"], taps=False)
     bar = 1e-5 if precision == fengine.FP32 else REL_RMS_REDUCED
     _report(f"autotuned n={n}", compare_call(s, res[0], M2, S, n, T, delays, None, rel_rms=bar))
+
+
+def test_autotune_cache_round_trip(tmp_path):
+    """fengine_autotune_cached: the first call tunes and writes one line; the
+    same configuration then comes from the file without timing; another
+    shape adds its own line and keeps the first; a line whose split no
+    longer makes a plan is ignored and replaced."""
+    import json
+    path = str(tmp_path / "tune.jsonl")
+    kw = dict(spectra_per_heap=0, max_delay_samples=0, calls=1)
+    best, hit = fengine.autotune_cached(path, 1, 1024, 8, 2048 * 64, **kw)
+    assert not hit
+    lines = [json.loads(x) for x in open(path)]
+    assert len(lines) == 1 and lines[0]["fft_n1"] == best["fft_n1"] and lines[0]["n_channels"] == 1024
+    again, hit = fengine.autotune_cached(path, 1, 1024, 8, 2048 * 64, **kw)
+    assert hit and again == best
+    other, hit = fengine.autotune_cached(path, 1, 2048, 8, 4096 * 32, **kw)
+    assert not hit
+    assert len(open(path).readlines()) == 2
+    # a stale split (fft_n1 = 3 makes no plan) is ignored and the line replaced
+    first = json.loads(open(path).readline())
+    first["fft_n1"] = 3
+    rest = open(path).readlines()[1:]
+    with open(path, "w") as f:
+        f.write(json.dumps(first) + "\n" + "".join(rest))
+    fresh, hit = fengine.autotune_cached(path, 1, 1024, 8, 2048 * 64, **kw)
+    assert not hit and fresh["fft_n1"] != 3
+    assert len(open(path).readlines()) == 2

@@ -158,3 +158,46 @@ def test_grouped_launches_with_shared_shapes_slabs_and_other_forms():
         for p in plans:
             p.device_status()
             p.close()
+
+
+def test_grouped_batch_with_lost_data_flags():
+    """Grouped members carrying received-heap flags (Sec. 3.7): the output
+    and the output-heap flags of every member equal its plan alone."""
+    import torch
+    HS = fengine.HEAP_SAMPLES
+    specs = [(1, 2048, 16, 64), (2, 2048, 16, 128), (1, 8192, 16, 32), (1, 8192, 16, 64)]
+    g = np.random.default_rng(11)
+    made = []
+    for i, (n_ant, n, T, m) in enumerate(specs):
+        L = 2 * n * m
+        s = streams(synth.SEED_BASE + 90 + i, n_ant, 2 * L, 30.0, tones=[(0.2 + 0.01 * i, 70.0, 0.0)])
+        plans = [fengine.Plan(n_ant, n, T, L, spectra_per_heap=16, max_delay_samples=100) for _ in range(2)]
+        for p in plans:
+            for a in range(n_ant):
+                for pol in range(2):
+                    p.set_delay(a, pol, 10.0 + a + pol, rate=1e-7)
+        valid = [(g.random((n_ant, 2, L // HS)) > 0.15).astype(np.uint8) for _ in range(2)]
+        made.append((plans, s, valid))
+    batch = fengine.Batch(3)
+    for c in range(2):
+        members, alone = [], []
+        for plans, s, valid in made:
+            L = plans[0].chunk_samples
+            pk = _packed(s, c * L, L)
+            v = torch.from_numpy(valid[c]).cuda()
+            d_a = torch.empty(plans[0].info.out_bytes, dtype=torch.int8, device="cuda")
+            f_a = torch.empty((plans[0].n_antennas, plans[0].heaps), dtype=torch.uint8, device="cuda")
+            plans[0].process(pk, c * L, d_a, valid=v, heap_flags=f_a)
+            d_b, f_b = torch.empty_like(d_a), torch.empty_like(f_a)
+            alone.append((d_a, f_a))
+            members.append((plans[1], pk, c * L, d_b, v, f_b))
+        batch.process(members)
+        torch.cuda.synchronize()
+        for k, (mem, (d_a, f_a)) in enumerate(zip(members, alone)):
+            np.testing.assert_array_equal(mem[3].cpu().numpy(), d_a.cpu().numpy(), err_msg=f"member {k} chunk {c}")
+            np.testing.assert_array_equal(mem[5].cpu().numpy(), f_a.cpu().numpy(), err_msg=f"flags {k} chunk {c}")
+            assert f_a.cpu().numpy().min() == 0          # some heaps were flagged
+    batch.close()
+    for plans, _, _ in made:
+        for p in plans:
+            p.close()

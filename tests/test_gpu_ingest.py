@@ -25,16 +25,17 @@ def _cuda():
     fengine.load()
 
 
-def _plan(n_ant, n, T, L):
-    p = fengine.Plan(n_ant, n, T, L, spectra_per_heap=16, max_delay_samples=300)
+def _plan(n_ant, n, T, L, precision=fengine.FP32):
+    p = fengine.Plan(n_ant, n, T, L, spectra_per_heap=16, max_delay_samples=300, precision=precision)
     for a in range(n_ant):
         for pol in range(2):
             p.set_delay(a, pol, 17.3 + 40 * a + 9 * pol, 1e-6, 0.2 * pol)
     return p
 
 
-@pytest.mark.parametrize("reorder", [0, 1, 2])
-def test_shuffled_heaps_with_losses_equal_direct_chunks(reorder):
+@pytest.mark.parametrize("reorder,precision", [(0, fengine.FP32), (1, fengine.FP32), (2, fengine.FP32),
+                                               (1, fengine.TC_FP16)])
+def test_shuffled_heaps_with_losses_equal_direct_chunks(reorder, precision):
     import torch
     n_ant, n, T = 2, 1024, 8
     N = 2 * n
@@ -74,7 +75,7 @@ def test_shuffled_heaps_with_losses_equal_direct_chunks(reorder):
     heaps = [heap(*x) for x in order]
     late = heap(0, 1, 3)                           # chunk 0 again, after it has been emitted
 
-    plan = _plan(n_ant, n, T, L)
+    plan = _plan(n_ant, n, T, L, precision)
     ing = fengine.Ingest(plan, first_sample=0, ring_heaps=48, reorder_chunks=reorder)
     d_out = torch.empty(plan.info.out_bytes, dtype=torch.int8, device="cuda")
     d_flags = torch.empty((n_ant, plan.heaps), dtype=torch.uint8, device="cuda")
@@ -106,7 +107,7 @@ def test_shuffled_heaps_with_losses_equal_direct_chunks(reorder):
     plan.close()
 
     # the same chunks through fengine_process_chunk, missing heaps zeroed
-    ref = _plan(n_ant, n, T, L)
+    ref = _plan(n_ant, n, T, L, precision)
     r_out = torch.empty_like(d_out)
     r_flags = torch.empty_like(d_flags)
     for c in range(n_chunks):
