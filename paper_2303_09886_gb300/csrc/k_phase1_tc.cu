@@ -76,11 +76,6 @@ __host__ __device__ constexpr long long tc_smem_ph(int ph, int R, int T, int pre
 __host__ __device__ constexpr int tc_phys(int R, int T, int prec) {
     return (prec == 1 && R <= 2 && tc_smem_ph(16, R, T, prec, 1, 2) <= kTcSmemMax) ? 16 : 8;
 }
-// warps: 4 epilogue (one per 32 tensor-memory lanes), F fill, 1 MMA. Four
-// fill warps at one CTA per SM (PH = 16); two at two CTAs per SM, which
-// leaves each thread 128 registers
-__host__ __device__ constexpr int tc_fill_warps(int ph) { return ph == 16 ? 4 : 2; }
-__host__ __device__ constexpr int tc_threads(int ph) { return 32 * (5 + tc_fill_warps(ph)); }
 __host__ __device__ constexpr long long tc_smem(int ph, int R, int T, int prec, int ks, int nxb) {
     return tc_smem_ph(ph, R, T, prec, ks, nxb);
 }
@@ -103,6 +98,17 @@ __host__ __device__ constexpr int tc_nxb(int ph, int R, int T, int prec) {
 __host__ __device__ constexpr int tc_tmem_cols(int ph, int R, int T, int prec) {
     return 2 * (ph / R) * tc_nm(R, tc_ks1(ph, R, T, prec)) <= 256 ? 256 : 512;
 }
+
+// One CTA per SM when the CTA's shared memory leaves no room for a second
+// (and always at PH = 16), else two. Warps: 4 epilogue (one per 32
+// tensor-memory lanes), F fill, 1 MMA; four fill warps at one CTA per SM,
+// two at two CTAs per SM (which leaves each thread 128 registers).
+constexpr long long kTcTwoCtaSmem = 113 * 1024;
+__host__ __device__ constexpr bool tc_one_cta(int ph, int R, int T, int prec) {
+    return ph == 16 || tc_smem(ph, R, T, prec, tc_ks1(ph, R, T, prec), tc_nxb(ph, R, T, prec)) > kTcTwoCtaSmem;
+}
+__host__ __device__ constexpr int tc_fill_warps(bool one) { return one ? 4 : 2; }
+__host__ __device__ constexpr int tc_threads(bool one) { return 32 * (5 + tc_fill_warps(one)); }
 
 // ---- tcgen05 / mbarrier primitives (PTX ISA, sm_100a family) ----
 
@@ -376,7 +382,7 @@ __global__ void k_unpack_cols_small(const UnpackColsParams p) {
 //   warps 0-3    epilogue: tensor memory -> scale -> second-stage input in HBM
 //   next F warps fill: the pass's PH column sequences from cols into the ring
 //                of shared-memory data buffers (BF16: hi and lo planes); F = 4
-//                at PH = 16 (one CTA per SM), 2 at PH = 8 (two CTAs per SM)
+//                at one CTA per SM, 2 at two CTAs per SM
 //   last warp    MMA: the tcgen05 chain of a pass into one of two tensor-memory
 //                buffers, committed to the barriers that free its data buffer
 //                and hand the accumulator to the epilogue
@@ -384,7 +390,8 @@ __global__ void k_unpack_cols_small(const UnpackColsParams p) {
 // mbarriers (xfull / xempty per data buffer, tfull / tempty per tensor-memory
 // buffer), every wait bounded.
 template <int R, int T, int PREC, int PH>   // PH: physical FIR columns of the CTA
-__global__ void __launch_bounds__(tc_threads(PH), PH == 16 ? 1 : 2) k_phase1_tc(const Phase1TcParams p) {
+__global__ void __launch_bounds__(tc_threads(tc_one_cta(PH, R, T, PREC)), tc_one_cta(PH, R, T, PREC) ? 1 : 2)
+    k_phase1_tc(const Phase1TcParams p) {
     constexpr int KS = tc_ks(PH, R, T, PREC), KPS = tc_kps(R, KS);   // k1-slices, k1 values per slice
     constexpr int TMEMC = tc_tmem_cols(PH, R, T, PREC);               // tensor-memory columns allocated
     constexpr int NM = tc_nm(R, KS), TP = tc_tp(T), K = 8 * TP, XL = tc_xl(T), CW = PH / R;
@@ -395,8 +402,9 @@ __global__ void __launch_bounds__(tc_threads(PH), PH == 16 ? 1 : 2) k_phase1_tc(
     constexpr int TMC = CW * NM;              // tensor-memory columns per pass buffer
     constexpr int NG = (2 * KPS + 7) / 8;     // 8-column groups holding (Re, Im) of the slice's k1
     constexpr int NXB = tc_nxb(PH, R, T, PREC);   // data buffers
-    constexpr int NTH = tc_threads(PH), FT = 32 * tc_fill_warps(PH);   // threads, fill threads
-    constexpr int WMMA = 4 + tc_fill_warps(PH);                         // the MMA warp
+    constexpr bool ONE = tc_one_cta(PH, R, T, PREC);                   // one CTA per SM
+    constexpr int NTH = tc_threads(ONE), FT = 32 * tc_fill_warps(ONE);  // threads, fill threads
+    constexpr int WMMA = 4 + tc_fill_warps(ONE);                        // the MMA warp
     static_assert(KS > 0, "shape does not fit in shared memory");
     static_assert(2 * TMC <= TMEMC, "tensor memory");
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -671,32 +679,37 @@ __global__ void __launch_bounds__(tc_threads(PH), PH == 16 ? 1 : 2) k_phase1_tc(
             const uint32_t trow = tmem + (uint32_t)(b * TMC) + ((uint32_t)(32 * warp) << 16);
             const long long q_rel = ps.q0 + row - p.q_begin;
             // store the (Re, Im) pairs of k1 = k1_lo + 4 g + kq of this row and the CW columns
-            auto store_group = [&](int g, const float (&v)[CW][8]) {
+            // store the (Re, Im) pairs of k1 = k1_lo + 4 g + kq of this row for
+            // the NC columns c0 .. c0 + NC - 1 of the group
+            auto store_cols = [&](int g, int c0, const auto &v) {
+                constexpr int NC = sizeof(v) / sizeof(v[0]);
                 if (!valid) return;
 #pragma unroll
                 for (int kq = 0; kq < 4; kq++) {
                     const int k1 = k1_lo + 4 * g + kq;
                     if (k1 >= k1_hi) break;
-                    const long long o = (((long long)ps.st * p.a_spectra + q_rel) * (H1 + 1) + k1) * N2 + cg * CW;
+                    const long long o =
+                        (((long long)ps.st * p.a_spectra + q_rel) * (H1 + 1) + k1) * N2 + cg * CW + c0;
                     if constexpr (PREC == 2) {
                         float2 *out = reinterpret_cast<float2 *>(p.A) + o;
 #pragma unroll
-                        for (int c = 0; c < CW; c++)
-                            out[c] = make_float2(v[c][2 * kq] * osc[c], v[c][2 * kq + 1] * osc[c]);
+                        for (int c = 0; c < NC; c++)
+                            out[c] = make_float2(v[c][2 * kq] * osc[c0 + c], v[c][2 * kq + 1] * osc[c0 + c]);
                     } else {
-                        uint32_t hv[CW];
+                        uint32_t hv[NC];
 #pragma unroll
-                        for (int c = 0; c < CW; c++) {
-                            const __half2 h = __floats2half2_rn(v[c][2 * kq] * osc[c], v[c][2 * kq + 1] * osc[c]);
+                        for (int c = 0; c < NC; c++) {
+                            const __half2 h =
+                                __floats2half2_rn(v[c][2 * kq] * osc[c0 + c], v[c][2 * kq + 1] * osc[c0 + c]);
                             hv[c] = *reinterpret_cast<const uint32_t *>(&h);
                         }
                         uint32_t *out = reinterpret_cast<uint32_t *>(p.A) + o;
-                        static_assert(CW == 1 || CW == 2 || CW % 4 == 0, "column group width");
-                        if constexpr (CW % 4 == 0) {
+                        static_assert(NC == 1 || NC == 2 || NC % 4 == 0, "column group width");
+                        if constexpr (NC % 4 == 0) {
 #pragma unroll
-                            for (int c = 0; c < CW; c += 4)
+                            for (int c = 0; c < NC; c += 4)
                                 reinterpret_cast<uint4 *>(out)[c / 4] = make_uint4(hv[c], hv[c + 1], hv[c + 2], hv[c + 3]);
-                        } else if constexpr (CW == 2) {
+                        } else if constexpr (NC == 2) {
                             reinterpret_cast<uint2 *>(out)[0] = make_uint2(hv[0], hv[1]);
                         } else {
                             out[0] = hv[0];
@@ -704,7 +717,7 @@ __global__ void __launch_bounds__(tc_threads(PH), PH == 16 ? 1 : 2) k_phase1_tc(
                     }
                 }
             };
-            if constexpr (NG * CW <= (PH == 16 ? 16 : 4)) {
+            if constexpr (NG * CW <= (PH == 16 ? 16 : ONE ? 8 : 4)) {
                 // all of the pass's accumulator columns in registers, one wait,
                 // tensor memory released before the stores (within the register
                 // budget of two CTAs per SM when PH = 8)
@@ -717,19 +730,24 @@ __global__ void __launch_bounds__(tc_threads(PH), PH == 16 ? 1 : 2) k_phase1_tc(
                 tc_fence_before();
                 arrive(&tempty[b]);   // tensor memory free for the pass after next
 #pragma unroll
-                for (int g = 0; g < NG; g++) store_group(g, vall[g]);
+                for (int g = 0; g < NG; g++) store_cols(g, 0, vall[g]);
             } else {
+                // at most 8 columns at a time (64 registers of accumulator)
+                constexpr int CH = CW < 8 ? CW : 8;
 #pragma unroll 1
                 for (int g = 0; g < NG; g++) {
-                    float v[CW][8];
+#pragma unroll 1
+                    for (int c0 = 0; c0 < CW; c0 += CH) {
+                        float v[CH][8];
 #pragma unroll
-                    for (int c = 0; c < CW; c++) tmem_ld8(trow + (uint32_t)(c * NM + 8 * g), v[c]);
-                    tmem_ld_wait();
-                    if (g == NG - 1) {
-                        tc_fence_before();
-                        arrive(&tempty[b]);
+                        for (int c = 0; c < CH; c++) tmem_ld8(trow + (uint32_t)((c0 + c) * NM + 8 * g), v[c]);
+                        tmem_ld_wait();
+                        if (g == NG - 1 && c0 + CH == CW) {
+                            tc_fence_before();
+                            arrive(&tempty[b]);
+                        }
+                        store_cols(g, c0, v);
                     }
-                    store_group(g, v);
                 }
             }
         }
@@ -857,10 +875,10 @@ static cudaError_t launch_tc_ph(const Phase1TcParams &p, cudaStream_t s) {
     constexpr int KS = tc_ks1(PH, R, T, PREC);
     const long long n_units = (long long)n_cg * KS * p.n_streams * ((p.q_count + kTcRows - 1) / kTcRows);
     // one wave: two CTAs per SM when two fit in shared memory, else one
-    const long long ctas = (long long)p.splits * (smem <= 113 * 1024 ? 2 : 1);
+    const long long ctas = (long long)p.splits * (tc_one_cta(PH, R, T, PREC) ? 1 : 2);
     const int grid = (int)(n_units < ctas ? n_units : ctas);
     if (grid < 1) return cudaErrorInvalidValue;
-    k_phase1_tc<R, T, PREC, PH><<<grid, tc_threads(PH), smem, s>>>(p);
+    k_phase1_tc<R, T, PREC, PH><<<grid, tc_threads(tc_one_cta(PH, R, T, PREC)), smem, s>>>(p);
     return cudaGetLastError();
 }
 
