@@ -407,7 +407,9 @@ fengine_status fengine_plan_create(const fengine_config *cfg, fengine_plan_t *ou
         fe::build_phase1_tc_tables((int)N, T, pl->precision, w.data(), bmat, osc, s_int);
         pl->tc_unscale = 1.0f / s_int;
         pl->cols_rtp = fe::unpack_cols_rows(pl->H, pl->L, pl->D, pl->Dmin, (int)N, T);
-        const size_t cols_bytes = sizeof(uint16_t) * (size_t)pl->n_streams * (N / 8) * pl->cols_rtp;
+        // one FP16 plane; the BF16 form keeps hi and lo planes
+        const size_t cols_bytes = sizeof(uint16_t) * (size_t)pl->n_streams * (N / 8) * pl->cols_rtp *
+                                  (pl->precision == FENGINE_TC_BF16 ? 2 : 1);
         if ((e = dalloc(pl, &pl->d_cols, cols_bytes)) != cudaSuccess) {
             release(pl);
             g_last_error = std::string("device allocation: ") + cudaGetErrorString(e);
@@ -751,12 +753,15 @@ fengine_status process_impl(fengine_plan_t pl, void *cuda_stream, const uint8_t 
         up.n_streams = pl->n_streams;
         up.row_begin = 0;
         up.row_end = pl->cols_rtp;
+        up.bf16 = pl->precision == FENGINE_TC_BF16 ? 1 : 0;
+        up.plane_elems = (long long)pl->n_streams * (pl->N / 8) * pl->cols_rtp;
         if (!split_unpack) {
             prof_begin(pl, 4, st);
             if ((e = fe::launch_unpack_cols(up, st)) != cudaSuccess) return cuda_fail(e, "unpack launch");
             prof_end(pl, st);
         }
         pt.cols = pl->d_cols;
+        pt.plane_elems = up.plane_elems;
         pt.rb = up.rb;
         pt.RTP = pl->cols_rtp;
     }

@@ -198,6 +198,8 @@ struct UnpackColsParams {
     int RT, RTP;              // rows holding samples; rows per column (padded, a multiple of 64)
     int row_begin, row_end;   // the launch writes rows [row_begin, row_end) (multiples of 64;
                               // [0, RTP) for the whole buffer)
+    int bf16;                 // 1: write BF16 hi and lo planes (the lo plane plane_elems after the hi)
+    long long plane_elems;    // n_streams P RTP
     uint16_t *cols;           // out [stream][P][RTP] FP16, pre-delayed by ctab[stream][0]
     const int *ctab;          // [stream][M] coarse delays
     int M;
@@ -205,7 +207,9 @@ struct UnpackColsParams {
 };
 
 struct Phase1TcParams {
-    const uint16_t *cols;     // [stream][P][RTP] FP16 samples (UnpackColsParams)
+    const uint16_t *cols;     // [plane][stream][P][RTP] samples (UnpackColsParams): FP16, or BF16 hi
+                              // and lo planes in the BF16 form
+    long long plane_elems;    // elements per plane
     long long rb;
     int RTP;
     int N, N2;                // FFT length, second-stage size

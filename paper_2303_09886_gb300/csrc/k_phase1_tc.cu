@@ -349,8 +349,20 @@ __global__ void __launch_bounds__(256) k_unpack_cols(const UnpackColsParams p) {
         const int c = tid >> 2, part = tid & 3;
         uint4 *dst = reinterpret_cast<uint4 *>(p.cols + ((long long)st * p.P + col0 + c) * p.RTP + r0 + 16 * part);
         const uint32_t *t = &tile[c][8 * part];
-        dst[0] = make_uint4(t[0], t[1], t[2], t[3]);
-        dst[1] = make_uint4(t[4], t[5], t[6], t[7]);
+        if (p.bf16) {
+            // the BF16 form's data planes: x = hi + lo exactly
+            uint32_t h[8], l[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) half2_to_bf16x2(t[i], h[i], l[i]);
+            uint4 *dlo = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(dst) + p.plane_elems);
+            dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+            dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+            dlo[0] = make_uint4(l[0], l[1], l[2], l[3]);
+            dlo[1] = make_uint4(l[4], l[5], l[6], l[7]);
+        } else {
+            dst[0] = make_uint4(t[0], t[1], t[2], t[3]);
+            dst[1] = make_uint4(t[4], t[5], t[6], t[7]);
+        }
     }
 }
 
@@ -373,7 +385,14 @@ __global__ void k_unpack_cols_small(const UnpackColsParams p) {
             const unsigned w = ((unsigned)__ldg(b) << 8) | (unsigned)__ldg(b + 1);
             v = field_to_half((w >> (6u - 2u * (unsigned)(u & 3))) & 0x3FFu);
         }
-        p.cols[e] = v;
+        if (p.bf16) {
+            uint32_t hi, lo;
+            half2_to_bf16x2((uint32_t)v, hi, lo);
+            p.cols[e] = (uint16_t)(hi & 0xFFFFu);
+            p.cols[e + p.plane_elems] = (uint16_t)(lo & 0xFFFFu);
+        } else {
+            p.cols[e] = v;
+        }
     }
 }
 
@@ -518,18 +537,19 @@ __global__ void __launch_bounds__(tc_threads(tc_one_cta(PH, R, T, PREC)), tc_one
                          : "memory");
             if (!ok) break;
             uint16_t *xb = xsm + (size_t)s * NPL * PH * XL;
-            if (PREC == 1 && !p.window_tap && ps.c == ps.c0) {
+            if (!p.window_tap && ps.c == ps.c0) {
                 // the pass's delay is the columns' c0: every column sequence starts at
-                // row 8 (m0 + q0) - rb, 16-byte aligned, one bulk copy each
+                // row 8 (m0 + q0) - rb, 16-byte aligned, one bulk copy each (per plane)
                 if (ft == 0) {
-                    constexpr uint32_t bytes = (uint32_t)(PH * XL * 2);
+                    constexpr uint32_t bytes = (uint32_t)(NPL * PH * XL * 2);
                     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
                                  ::"r"(smem_addr(&xfull[s])), "r"(bytes) : "memory");
                     const long long row0 = 8LL * (p.m0 + ps.q0) - p.rb;
 #pragma unroll 1
-                    for (int i = 0; i < PH; i++) {
-                        const long long t = (long long)cg * CW + (i % CW) + (long long)N2 * (i / CW);
-                        const uint16_t *src = p.cols + ((long long)ps.st * P + t) * p.RTP + row0;
+                    for (int i = 0; i < NPL * PH; i++) {
+                        const int ic = i % PH, pl = i / PH;
+                        const long long t = (long long)cg * CW + (ic % CW) + (long long)N2 * (ic / CW);
+                        const uint16_t *src = p.cols + pl * p.plane_elems + ((long long)ps.st * P + t) * p.RTP + row0;
                         asm volatile(
                             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                             ::"r"(smem_addr(xb + (size_t)i * XL)), "l"(src), "r"((uint32_t)(XL * 2)),
@@ -547,14 +567,16 @@ __global__ void __launch_bounds__(tc_threads(tc_one_cta(PH, R, T, PREC)), tc_one
                 fsh[s * PH + ft] = (int)(row0 & 7);
             }
             asm volatile("bar.sync 1, %0;" ::"n"(FT) : "memory");
-            for (int e0 = ft; e0 < PH * CPC; e0 += FT * 3) {
+            // (BF16: both data planes, unpacked already split into hi and lo)
+            for (int e0 = ft; e0 < NPL * PH * CPC; e0 += FT * 3) {
                 uint4 a[3], b[3];
 #pragma unroll
                 for (int u = 0; u < 3; u++) {
                     const int e = e0 + FT * u;
-                    if (e < PH * CPC) {
-                        const int i = e / CPC, j = e - i * CPC;
-                        const uint4 *src = reinterpret_cast<const uint4 *>(p.cols + fsrc[s * PH + i]) + j;
+                    if (e < NPL * PH * CPC) {
+                        const int ip = e / CPC, j = e - ip * CPC, i = ip % PH;
+                        const uint4 *src =
+                            reinterpret_cast<const uint4 *>(p.cols + (ip / PH) * p.plane_elems + fsrc[s * PH + i]) + j;
                         a[u] = __ldg(src);
                         b[u] = __ldg(src + 1);
                     }
@@ -562,8 +584,8 @@ __global__ void __launch_bounds__(tc_threads(tc_one_cta(PH, R, T, PREC)), tc_one
 #pragma unroll
                 for (int u = 0; u < 3; u++) {
                     const int e = e0 + FT * u;
-                    if (e < PH * CPC) {
-                        const int i = e / CPC, j = e - i * CPC;
+                    if (e < NPL * PH * CPC) {
+                        const int ip = e / CPC, j = e - ip * CPC, i = ip % PH;
                         const int sh = fsh[s * PH + i];
                         const uint32_t w[8] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
                         uint32_t o[4];
@@ -586,16 +608,7 @@ __global__ void __launch_bounds__(tc_threads(tc_one_cta(PH, R, T, PREC)), tc_one
                                 for (int m = 0; m < 4; m++) o[m] = __byte_perm(w[m + 3], w[m + 4], sel);
                                 break;
                         }
-                        if constexpr (PREC == 2) {
-                            uint32_t h[4], l[4];
-#pragma unroll
-                            for (int m = 0; m < 4; m++) half2_to_bf16x2(o[m], h[m], l[m]);
-                            reinterpret_cast<uint4 *>(xb + (size_t)i * XL)[j] = make_uint4(h[0], h[1], h[2], h[3]);
-                            reinterpret_cast<uint4 *>(xb + (size_t)(PH + i) * XL)[j] =
-                                make_uint4(l[0], l[1], l[2], l[3]);
-                        } else {
-                            reinterpret_cast<uint4 *>(xb + (size_t)i * XL)[j] = make_uint4(o[0], o[1], o[2], o[3]);
-                        }
+                        reinterpret_cast<uint4 *>(xb + (size_t)ip * XL)[j] = make_uint4(o[0], o[1], o[2], o[3]);
                     }
                 }
             }
