@@ -172,12 +172,23 @@ inline int phase1_W(int N1, int N2) {
     int w = 512 / N1;           // 512 FIR columns per tile
     return w < N2 ? w : N2;
 }
-inline int phase2_R2(int N2) {
-    int r = 4096 / N2;          // 2 pols * R2 * N2 * 8 B <= 64 KiB: two CTAs per SM
+// shared memory of a k_phase2<N2> CTA of R2 spectra (the sequences of both
+// pols, padded rows, the rotation tables and the heap row info)
+constexpr long long phase2_smem_c(int N2, int R2) {
+    const int LD = N2 + N2 / 16 + 1, LO = N2 < 32 ? N2 : 32, HI = N2 / LO;
+    return 8LL * (2LL * R2 * LD + 2LL * R2 * ((HI + 1) + (LO + 1) + 1)) + 12LL * R2;
+}
+// spectra per k_phase2 CTA: up to 4096 / N2 (at most 32), halved while the
+// CTA's shared memory would keep three CTAs (the register limit) off an SM,
+// down to 8 (the corner turn writes 4 R2-byte rows: 32 bytes at R2 = 8)
+constexpr int phase2_R2_for(int N2) {
+    int r = 4096 / N2;
     if (r > 32) r = 32;
     if (r < 1) r = 1;
+    while (r > 8 && phase2_smem_c(N2, r) > 74 * 1024) r /= 2;
     return r;
 }
+inline int phase2_R2(int N2) { return phase2_R2_for(N2); }
 size_t phase2_smem_bytes(int N2, int R2);
 
 // Phase 1 of the reduced-precision forms on tcgen05 tensor cores

@@ -80,7 +80,7 @@ template <int N2>
 struct P2Shape {
     static constexpr int P = N2 < 16 ? N2 : 16;                   // points per thread per stage
     static constexpr int TPS = N2 / P;                            // threads per sequence
-    static constexpr int R2 = (4096 / N2) > 32 ? 32 : (4096 / N2); // spectra per CTA (2 CTAs per SM)
+    static constexpr int R2 = phase2_R2_for(N2);                  // spectra per CTA
     static constexpr int LD = N2 + N2 / 16 + 1;                   // padded row stride
     static constexpr int LO = N2 < 32 ? N2 : 32;                  // rotation low table size
     static constexpr int HI = N2 / LO;                            // rotation high table size
