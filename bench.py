@@ -48,11 +48,11 @@ KERNEL_SOURCES = {
 }
 _CAPTURED = 33554432   # input samples of the captured launch
 NCU_TRAFFIC = {
-    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44464128 + 94618624) / _CAPTURED, "src": "037726aa59c4de16"},
-    "k_phase2w": {"bytes_per_sample": (170670592 + 23595520) / _CAPTURED, "src": "156ae318891bd597"},
-    "k_phase2w<half>": {"bytes_per_sample": (94606848 + 22808064) / _CAPTURED, "src": "156ae318891bd597"},
-    "k_phase1_tc<2,16,1>": {"bytes_per_sample": (96512000 + 49110528) / _CAPTURED, "src": "9a929f12c5542e2a"},
-    "k_unpack_cols": {"bytes_per_sample": (42584064 + 20911616) / _CAPTURED, "src": "9a929f12c5542e2a"},
+    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44695040 + 92290816) / _CAPTURED, "src": "7d443bafdd340fea"},
+    "k_phase2w": {"bytes_per_sample": (170682112 + 23617280) / _CAPTURED, "src": "ef807b32b60da0e0"},
+    "k_phase2w<half>": {"bytes_per_sample": (94515456 + 22902528) / _CAPTURED, "src": "ef807b32b60da0e0"},
+    "k_phase1_tc<2,16,1>": {"bytes_per_sample": (96550912 + 48994816) / _CAPTURED, "src": "ff5a11d5acd16c73"},
+    "k_unpack_cols": {"bytes_per_sample": (42593280 + 20207616) / _CAPTURED, "src": "ff5a11d5acd16c73"},
 }
 
 

@@ -41,7 +41,48 @@ struct P1Shape {
     static constexpr int ROW = N1 * GW;      // floats per output row
     static constexpr int C = N1 * W;         // FIR columns per tile
     static constexpr int ROWS = R + T - 1;   // input rows of a full tile
+    // Staged input (tiles of one delay run inside the chunk, every thread
+    // owning a column pair): the packed bytes of each (input row, t1 segment
+    // of W columns) are copied into a shared-memory ring by 16-byte cp.async
+    // from the segment's first byte rounded down to 16, SEG bytes (the W
+    // samples' bytes plus up to 15 in front and the second byte of the last
+    // field), SG rows per commit group, NGRING groups in the ring.
+    static constexpr bool STAGED = (C == 2 * kP1Threads);
+    static constexpr int SEG = (15 + (5 * (W - 1) + 3) / 4 + 2 + 15) / 16 * 16;
+    static constexpr int SG = 8;
+    static constexpr int NGRING = (N1 * SEG <= 1024) ? 3 : 2;
+    static constexpr int RING = NGRING * SG;
+    static constexpr int STAGE_BYTES = STAGED ? RING * N1 * SEG : 0;
+    static constexpr size_t SMEM = (size_t)R * ROW * sizeof(float) + STAGE_BYTES;
 };
+
+__device__ __forceinline__ void p1_cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void p1_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void p1_cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Output rows (r, r + 1) of a column pair from the ring win of T + 1 input
+// rows (win[i % (T + 1)] holds input row i), as two independent packed FMA
+// chains; r even, row r + T the newest in the ring.
+template <int T, class S>
+__device__ __forceinline__ void p1_fir_pair(int r, const float2 (&win)[T + 1], const float2 (&w2)[T], float *ga,
+                                            float *gb) {
+    float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < T; j++) {
+        acc0 = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc0);
+        acc1 = __ffma2_rn(w2[j], win[(r + 1 + j) % (T + 1)], acc1);
+    }
+    ga[r * S::ROW] = acc0.x;
+    gb[r * S::ROW] = acc0.y;
+    ga[(r + 1) * S::ROW] = acc1.x;
+    gb[(r + 1) * S::ROW] = acc1.y;
+}
 
 // Exact float of the 10-bit two's-complement field in the low bits of x:
 // (field ^ 512) is the offset-binary value in [0, 1024), placed in the
@@ -113,7 +154,7 @@ template <int T, int N1, int W, bool HALF>
 __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) {
     using S = P1Shape<T, N1, W>;
     constexpr int R = S::R, H1 = N1 / 2;
-    extern __shared__ float gs[];              // [R][N1][GW] FIR output g
+    extern __shared__ __align__(16) float gs[];   // [R][N1][GW] FIR output g, then the staged-input ring
     __shared__ int c_sm[R];
     __shared__ float2 tw1_sm[(H1 + 1) * W];    // exp(-2 pi i k1 t2 / N) for this tile's t2
 
@@ -131,7 +172,7 @@ template <int T, int N1, int W, bool HALF>
 __global__ void __launch_bounds__(kP1Threads, 2) k_phase1_group(const Phase1Group g) {
     using S = P1Shape<T, N1, W>;
     constexpr int R = S::R, H1 = N1 / 2;
-    extern __shared__ float gs[];              // [R][N1][GW] FIR output g
+    extern __shared__ __align__(16) float gs[];   // [R][N1][GW] FIR output g, then the staged-input ring
     __shared__ int c_sm[R];
     __shared__ float2 tw1_sm[(H1 + 1) * W];    // exp(-2 pi i k1 t2 / N) for this tile's t2
     __shared__ Phase1Params sp;
@@ -156,7 +197,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1_group(const Phase1Grou
 template <int T, int N1, int W>
 cudaError_t launch_phase1_tw_group(const Phase1Group &g, cudaStream_t s) {
     using S = P1Shape<T, N1, W>;
-    const size_t smem = (size_t)S::R * S::ROW * sizeof(float);
+    const size_t smem = S::SMEM;
     cudaError_t e =
         cudaFuncSetAttribute(k_phase1_group<T, N1, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -169,7 +210,7 @@ template <int T, int N1, int W, bool HALF = false>
 cudaError_t launch_phase1_tw(const Phase1Params &p, int n_streams, cudaStream_t s) {
     using S = P1Shape<T, N1, W>;
     if (p.W != W || p.N2 % W) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)S::R * S::ROW * sizeof(float);
+    const size_t smem = S::SMEM;
     cudaError_t e =
         cudaFuncSetAttribute(k_phase1<T, N1, W, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -41,13 +41,14 @@ def streams(seed, n_ant, total, sigma, tones=(), chirp=None):
 
 def run_gpu(samples, n_ch, T, L, n_chunks, delays, gains, S=0, D=0, weights=None, start=0,
             taps=True, prequant=True, precision=fengine.FP32, fft_n1=0, slab_spectra=0, Dmin=0,
-            valids=None, flags=False):
+            valids=None, flags=False, in_offset=0):
     """Process consecutive chunks of `samples` (starting at absolute `start`).
     delays[a][p]: list of Seg; gains[a][p]: complex array, a list of
     (t_apply, complex array) gain sets, or None. valids: per call a uint8
     [ant, pol, L/4096] array of received-heap flags (or None); flags: read
-    back the output-heap flags. Returns list of dicts per call (numpy copies
-    of every output)."""
+    back the output-heap flags; in_offset: place the packed chunk this many
+    bytes (a multiple of 4) into a larger device buffer. Returns list of dicts
+    per call (numpy copies of every output)."""
     import torch
     n_ant = samples.shape[0]
     plan = fengine.Plan(n_ant, n_ch, T, L, spectra_per_heap=S, max_delay_samples=D, weights=weights,
@@ -69,6 +70,10 @@ def run_gpu(samples, n_ch, T, L, n_chunks, delays, gains, S=0, D=0, weights=None
         chunk = samples[:, :, lo:lo + L]
         packed = np.stack([np.stack([synth.pack10(chunk[a, p]) for p in range(2)]) for a in range(n_ant)])
         d_in = torch.from_numpy(packed).cuda()
+        if in_offset:
+            buf = torch.zeros(d_in.numel() + in_offset, dtype=torch.uint8, device="cuda")
+            buf[in_offset:].copy_(d_in.reshape(-1))
+            d_in = buf[in_offset:]
         d_out = torch.empty(plan.info.out_bytes, dtype=torch.int8, device="cuda")
         d_pre = torch.empty(n_ant * 2 * M * n_ch * 2, dtype=torch.float32, device="cuda") if prequant else None
         d_tap = torch.empty(n_ant * 2 * M * N, dtype=torch.int32, device="cuda") if taps else None
