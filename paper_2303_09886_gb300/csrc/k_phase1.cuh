@@ -66,6 +66,65 @@ __device__ __forceinline__ void p1_cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+__device__ __forceinline__ void p1_cp_async8(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// Whether a tile can take the staged form, and the chunk sample s00 of its
+// (input row 0, column 0) at its delay: a full tile of one delay run (lane i
+// of every warp holds the delay of output row i), no window tap, rows of a
+// multiple of 16 bytes in a 16-byte aligned stream, every window inside the
+// chunk, and the last 16-byte copy ending inside the stream's chunk bytes.
+template <int T, int N1, int W>
+__device__ __forceinline__ bool p1_stage_plan(const Phase1Params &p, const uint8_t *chunk, int cdl, int Rv,
+                                              long long rel_base, unsigned long long &s00) {
+    using S = P1Shape<T, N1, W>;
+    const int N = p.N, N2 = p.N2;
+    const unsigned RB = (unsigned)N / 4u * 5u;
+    const long long H = p.H, HL = p.H + p.L;
+    const int lane = threadIdx.x & 31;
+    const int cd = __shfl_sync(0xffffffffu, cdl, 0);
+    const bool one_run = __all_sync(0xffffffffu, lane >= Rv || cdl == cd);
+    const long long rel0 = rel_base - cd;
+    const long long hi = rel0 + (long long)N * (S::ROWS - 1) + (long long)N2 * (N1 - 1) + W;
+    s00 = (unsigned long long)(rel0 - H);
+    if (!(one_run && Rv == S::R && !p.window_tap && (RB & 15u) == 0u && ((uintptr_t)chunk & 15u) == 0u &&
+          rel0 >= H && hi <= HL))
+        return false;
+    const long long sl = rel0 - H + (long long)N2 * (N1 - 1) + (long long)N * (S::ROWS - 1);
+    const long long al = ((sl >> 2) * 5 + ((sl & 3) * 5 >> 2)) & ~15LL;
+    return al + S::SEG <= p.chunk_bytes;
+}
+
+// First byte of segment j (columns N2 j + t2_0 ...) in input row 0 of a staged
+// tile, rounded down to 16; row i starts RB i bytes further (RB a multiple of 16).
+__device__ __forceinline__ unsigned long long p1_seg_start(unsigned long long s00, int N2, int j) {
+    const unsigned long long s = s00 + (unsigned long long)N2 * j;
+    return ((s >> 2) * 5ull + ((s & 3ull) * 5ull >> 2)) & ~15ull;
+}
+
+// Copy group g (input rows g SG .. g SG + SG - 1) of a staged tile into its
+// ring slots and commit it (an empty group past the last row, so that the
+// group after g is always the newest when g is waited for).
+template <int T, int N1, int W>
+__device__ __forceinline__ void p1_stage_group(uint8_t *stg, const uint8_t *chunk, unsigned long long s00, int N2,
+                                               unsigned RB, int g) {
+    using S = P1Shape<T, N1, W>;
+    constexpr int SEG = S::SEG, SG = S::SG, RING = S::RING, NR = S::ROWS;
+    constexpr int CPR = N1 * (SEG / 16);                      // 16-byte copies per input row
+    constexpr int PER = (SG * CPR + kP1Threads - 1) / kP1Threads;
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+        const int e = threadIdx.x + k * kP1Threads;
+        const int row = g * SG + e / CPR, j = (e % CPR) / (SEG / 16), c16 = e % (SEG / 16);
+        if (e < SG * CPR && row < NR)
+            p1_cp_async16(stg + ((row % RING) * N1 + j) * SEG + 16 * c16,
+                          chunk + p1_seg_start(s00, N2, j) + (unsigned long long)RB * row + 16 * c16);
+    }
+    p1_cp_async_commit();
+}
+
 // Output rows (r, r + 1) of a column pair from the ring win of T + 1 input
 // rows (win[i % (T + 1)] holds input row i), as two independent packed FMA
 // chains; r even, row r + T the newest in the ring.
@@ -150,18 +209,22 @@ __device__ __noinline__ void p1_fir_general(const Phase1Params &p, const uint8_t
     }
 }
 
+// One tile per CTA: (t2 block, spectrum block, stream) = (blockIdx.x, .y, .z).
 template <int T, int N1, int W, bool HALF>
 __global__ void __launch_bounds__(kP1Threads, 2) k_phase1(const Phase1Params p) {
     using S = P1Shape<T, N1, W>;
     constexpr int R = S::R, H1 = N1 / 2;
     extern __shared__ __align__(16) float gs[];   // [R][N1][GW] FIR output g, then the staged-input ring
     __shared__ int c_sm[R];
-    __shared__ float2 tw1_sm[(H1 + 1) * W];    // exp(-2 pi i k1 t2 / N) for this tile's t2
+    __shared__ __align__(16) float2 tw1_sm[(H1 + 1) * W];   // exp(-2 pi i k1 t2 / N) for this tile's t2
 
     const int N = p.N, N2 = p.N2;
     const int stream = blockIdx.z;
     const int t2_0 = blockIdx.x * W;
     const int q0 = p.q_begin + blockIdx.y * R;
+    const int Rv = min(R, p.q_begin + p.q_count - q0);
+    const int lane = threadIdx.x & 31;
+    const int cdl = lane < Rv ? __ldg(p.ctab + (long long)stream * p.M + q0 + lane) : 0;
 #include "k_phase1_tile.inc"
 }
 
@@ -174,7 +237,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1_group(const Phase1Grou
     constexpr int R = S::R, H1 = N1 / 2;
     extern __shared__ __align__(16) float gs[];   // [R][N1][GW] FIR output g, then the staged-input ring
     __shared__ int c_sm[R];
-    __shared__ float2 tw1_sm[(H1 + 1) * W];    // exp(-2 pi i k1 t2 / N) for this tile's t2
+    __shared__ __align__(16) float2 tw1_sm[(H1 + 1) * W];   // exp(-2 pi i k1 t2 / N) for this tile's t2
     __shared__ Phase1Params sp;
     __shared__ int sxyz[3];
     if (threadIdx.x == 0) {
@@ -191,6 +254,9 @@ __global__ void __launch_bounds__(kP1Threads, 2) k_phase1_group(const Phase1Grou
     const int stream = sxyz[2];
     const int t2_0 = sxyz[0] * W;
     const int q0 = p.q_begin + sxyz[1] * R;
+    const int Rv = min(R, p.q_begin + p.q_count - q0);
+    const int lane = threadIdx.x & 31;
+    const int cdl = lane < Rv ? p.ctab[(long long)stream * p.M + q0 + lane] : 0;
 #include "k_phase1_tile.inc"
 }
 

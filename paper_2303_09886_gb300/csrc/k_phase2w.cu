@@ -77,20 +77,13 @@ size_t phase2w_smem_bytes() {
 }
 
 // Persistent: each CTA takes a contiguous range of work items of equal work.
-// Warp w owns
-// sequence (spectrum w / 2, polarisation w % 2) of every item; its 8 KB
-// sequence arrives in its shared-memory buffer by cp.async, and the copy of
-// the next item's sequence is issued as soon as the buffer has been read
-// (after the transpose), so it runs under this item's second DFT, epilogue
-// and corner turn.
-template <bool HALF_IN>
-__global__ void __launch_bounds__(kWThreads, 2) k_phase2w(const Phase2Params p, int n_ant) {
-    const long long cta_b = blockIdx.x, cta_nb = gridDim.x;
-#include "k_phase2w_cta.inc"
-}
-
-// The persistent CTAs of several plans' second stages in one grid: member m
-// owns CTAs [start[m], start[m + 1]) and aux[m] antennas.
+// Warp w owns sequence (spectrum w / 2, polarisation w % 2) of every item;
+// its 8 KB sequence arrives in its shared-memory buffer by cp.async, and the
+// copy of the next item's sequence is issued as soon as the buffer has been
+// read (after the transpose), so it runs under this item's second DFT,
+// epilogue and corner turn.
+// The CTAs of one or several plans' second stages in one grid: member m owns
+// CTAs [start[m], start[m + 1]) and aux[m] antennas.
 template <bool HALF_IN>
 __global__ void __launch_bounds__(kWThreads, 2) k_phase2w_group(const Phase2Group g) {
     __shared__ Phase2Params sp;
@@ -109,23 +102,26 @@ __global__ void __launch_bounds__(kWThreads, 2) k_phase2w_group(const Phase2Grou
 #include "k_phase2w_cta.inc"
 }
 
+// A single plan's second stage runs as a group of one member (the grouped
+// kernel reads the parameters from shared memory, which leaves it without the
+// register spills of a variant that reads them from the parameter bank).
+template <bool HALF_IN>
+static cudaError_t launch_w_group(const Phase2Group &g, cudaStream_t s);
+
 template <bool HALF_IN>
 static cudaError_t launch_w(const Phase2Params &p, int n_ant, cudaStream_t s) {
-    const size_t smem = phase2w_smem_bytes();
-    cudaError_t e =
-        cudaFuncSetAttribute(k_phase2w<HALF_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase2w<HALF_IN>, kWThreads, smem)) !=
-            cudaSuccess)
-        return e;
     const long long items = (long long)n_ant * (p.N1 / 2 + 1) * ((p.q_count + kWR - 1) / kWR);
     if (items <= 0) return cudaSuccess;
-    const int ctas = (int)std::min<long long>(items, (long long)sms * std::max(per_sm, 1));
-    k_phase2w<HALF_IN><<<ctas, kWThreads, smem, s>>>(p, n_ant);
-    return cudaGetLastError();
+    const int wave = phase2w_wave();
+    if (wave < 1) return cudaErrorUnknown;
+    Phase2Group g{};
+    g.p[0] = p;
+    g.start[0] = 0;
+    g.start[1] = (int)std::min<long long>(items, wave);
+    g.aux[0] = n_ant;
+    g.gx = 1;
+    g.n = 1;
+    return launch_w_group<HALF_IN>(g, s);
 }
 
 long long phase2w_items(const Phase2Params &p, int n_ant) {
