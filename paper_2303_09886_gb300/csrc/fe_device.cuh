@@ -12,6 +12,10 @@ __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// The same sums as packed FP32x2 instructions (two round-to-nearest adds in
+// one; the results are those of cadd and csub).
+__device__ __forceinline__ float2 cadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 
 // Sample j of a packed 10-bit stream (bits [10 j, 10 j + 10), most
 // significant bit first, two's complement; Sec. 2.2 fixes 10 bits/sample).
@@ -82,8 +86,8 @@ template <int NN, int K>
 __device__ __forceinline__ void dit_combine(float2 (&z)[NN], const float2 (&e)[NN / 2], const float2 (&o)[NN / 2]) {
     if constexpr (K < NN / 2) {
         const float2 t = cmul_w64<K * (64 / NN)>(o[K]);
-        z[K] = cadd(e[K], t);
-        z[K + NN / 2] = csub(e[K], t);
+        z[K] = cadd2(e[K], t);
+        z[K + NN / 2] = csub2(e[K], t);
         dit_combine<NN, K + 1>(z, e, o);
     }
 }
@@ -94,8 +98,9 @@ __device__ __forceinline__ void rdit_combine(float2 (&X)[NN / 2 + 1], const floa
                                              const float2 (&O)[NN / 4 + 1]) {
     if constexpr (K < NN / 4) {
         const float2 t = cmul_w64<K * (64 / NN)>(O[K]);
-        X[K] = cadd(E[K], t);
-        X[NN / 2 - K] = make_float2(E[K].x - t.x, t.y - E[K].y);
+        X[K] = cadd2(E[K], t);
+        const float2 d = csub2(E[K], t);
+        X[NN / 2 - K] = make_float2(d.x, -d.y);
         rdit_combine<NN, K + 1>(X, E, O);
     }
 }
