@@ -48,11 +48,11 @@ KERNEL_SOURCES = {
 }
 _CAPTURED = 33554432   # input samples of the captured launch
 NCU_TRAFFIC = {
-    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44695040 + 92290816) / _CAPTURED, "src": "7d443bafdd340fea"},
-    "k_phase2w": {"bytes_per_sample": (170682112 + 23617280) / _CAPTURED, "src": "ef807b32b60da0e0"},
-    "k_phase2w<half>": {"bytes_per_sample": (94515456 + 22902528) / _CAPTURED, "src": "ef807b32b60da0e0"},
-    "k_phase1_tc<2,16,1>": {"bytes_per_sample": (96550912 + 48994816) / _CAPTURED, "src": "ff5a11d5acd16c73"},
-    "k_unpack_cols": {"bytes_per_sample": (42593280 + 20207616) / _CAPTURED, "src": "ff5a11d5acd16c73"},
+    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44700160 + 92524800) / _CAPTURED, "src": "196d7968b89e10a2"},
+    "k_phase2w": {"bytes_per_sample": (170526976 + 23206656) / _CAPTURED, "src": "4bbfca13f09564d5"},
+    "k_phase2w<half>": {"bytes_per_sample": (94048768 + 22073856) / _CAPTURED, "src": "4bbfca13f09564d5"},
+    "k_phase1_tc<2,16,1>": {"bytes_per_sample": (96463616 + 49078272) / _CAPTURED, "src": "d6afa2a6124d675c"},
+    "k_unpack_cols": {"bytes_per_sample": (42589952 + 19676416) / _CAPTURED, "src": "d6afa2a6124d675c"},
 }
 
 

@@ -233,3 +233,22 @@ def test_staged_input_equals_direct_decode_and_oracle(n, T, fft_n1):
         np.testing.assert_array_equal(ca["pre"].view(np.uint32), cb["pre"].view(np.uint32))
         np.testing.assert_array_equal(ca["out"], cb["out"])
         _report(f"staged n={n} T={T} N1={fft_n1}", compare_call(s, ca, M2, S, n, T, delays, gains))
+
+
+def test_staged_input_at_the_chunk_end_and_zero_delay():
+    """Zero delay: the last window of a call ends on the chunk's last sample,
+    so the 16-byte copies of the last tile's last segment would reach past
+    the stream's bytes and that tile decodes directly while the others are
+    staged. Aligned and offset input agree bit for bit and with the oracle."""
+    n, T, M = 8192, 16, 64
+    N = 2 * n
+    L = N * M
+    s = streams(synth.SEED_BASE + 77, 1, 2 * L, 30.0, tones=[(0.37, 60.0, 0.1)])
+    delays = [[[Seg(delay=0.0)] for _ in range(2)]]
+    kw = dict(S=16, D=0, taps=False)
+    res_a, M2, S = run_gpu(s, n, T, L, 2, delays, None, **kw)
+    res_b, _, _ = run_gpu(s, n, T, L, 2, delays, None, in_offset=4, **kw)
+    for ca, cb in zip(res_a, res_b):
+        np.testing.assert_array_equal(ca["pre"].view(np.uint32), cb["pre"].view(np.uint32))
+        np.testing.assert_array_equal(ca["out"], cb["out"])
+        _report("staged, zero delay", compare_call(s, ca, M2, S, n, T, delays, None))
