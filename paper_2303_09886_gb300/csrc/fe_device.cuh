@@ -35,8 +35,18 @@ __device__ __forceinline__ int fetch10(const uint8_t *__restrict__ p, long long 
 // correctly rounded, so t + 0.49999997 reaches the next integer exactly when
 // frac(|t|) >= 1/2). Host and device evaluate it identically.
 __host__ __device__ __forceinline__ int quant8(float x) {
+#ifdef __CUDA_ARCH__
+    // The truncating conversion to an 8-bit integer saturates at +127 by
+    // itself (and at -128, which the lower clamp keeps out of reach); only
+    // the low byte of the result is used.
+    const float t = fmaxf(x, -127.0f);
+    int d;
+    asm("cvt.rzi.s8.f32 %0, %1;" : "=r"(d) : "f"(t + copysignf(0.49999997f, t)));
+    return d;
+#else
     float t = fminf(fmaxf(x, -127.0f), 127.0f);
     return (int)(t + copysignf(0.49999997f, t));
+#endif
 }
 
 template <int NN>

@@ -14,16 +14,18 @@
 // r + j); every PFB window uses one coarse delay (Sec. 3.3), so a tile is
 // processed per run of output rows with one delay.
 //
-// Each thread owns two FIR columns and decodes their 10-bit samples itself,
-// straight from the packed stream: sample s occupies bits [10 s, 10 s + 10)
-// (most significant bit first), i.e. bytes 5 s / 4 and 5 s / 4 + 1 at a bit
-// offset 2 (s mod 4) that is the same for every row of a column (a row is N
-// samples, a multiple of 4), and the row's bytes sit 5 N / 4 further on. The
-// FIR keeps T + 1 input rows in a register ring and emits output rows in
-// pairs (packed FP32x2 FMAs, two independent chains); g goes to shared
-// memory, and for each (output row, t2) the real N1-point DFT over t1 runs in
-// registers, is multiplied by the twiddle and stored (FP32 pairs, or FP16
-// pairs for the FP16 form).
+// Each thread owns two FIR columns and decodes their 10-bit samples itself:
+// sample s occupies bits [10 s, 10 s + 10) (most significant bit first),
+// i.e. bytes 5 s / 4 and 5 s / 4 + 1 at a bit offset 2 (s mod 4) that is the
+// same for every row of a column (a row is N samples, a multiple of 4), and
+// the row's bytes sit 5 N / 4 further on. A tile of one delay run inside the
+// chunk first copies its rows' packed bytes into a shared-memory ring
+// (cp.async, a few rows ahead of the FIR) and decodes from there; other tiles
+// decode straight from global memory. The FIR keeps T + 1 input rows in a
+// register ring and emits output rows in pairs (packed FP32x2 FMAs); g goes
+// to shared memory, and for each (output row, t2) the real N1-point DFT over
+// t1 runs in registers, is multiplied by the twiddle and stored (FP32 pairs,
+// or FP16 pairs for the FP16 form).
 #pragma once
 #include <cuda_fp16.h>
 
@@ -126,21 +128,33 @@ __device__ __forceinline__ void p1_stage_group(uint8_t *stg, const uint8_t *chun
 }
 
 // Output rows (r, r + 1) of a column pair from the ring win of T + 1 input
-// rows (win[i % (T + 1)] holds input row i), as two independent packed FMA
-// chains; r even, row r + T the newest in the ring.
+// rows (win[i % (T + 1)] holds input row i), r even, row r + T the newest in
+// the ring: packed FP32x2 FMAs in four independent chains (each output row's
+// taps in two halves, added at the end).
 template <int T, class S>
 __device__ __forceinline__ void p1_fir_pair(int r, const float2 (&win)[T + 1], const float2 (&w2)[T], float *ga,
                                             float *gb) {
-    float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+    constexpr int TH = T >= 4 ? T / 2 : T;
+    float2 a0 = make_float2(0.0f, 0.0f), a1 = make_float2(0.0f, 0.0f);
+    float2 b0 = make_float2(0.0f, 0.0f), b1 = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int j = 0; j < T; j++) {
-        acc0 = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], acc0);
-        acc1 = __ffma2_rn(w2[j], win[(r + 1 + j) % (T + 1)], acc1);
+    for (int j = 0; j < TH; j++) {
+        a0 = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], a0);
+        a1 = __ffma2_rn(w2[j], win[(r + 1 + j) % (T + 1)], a1);
     }
-    ga[r * S::ROW] = acc0.x;
-    gb[r * S::ROW] = acc0.y;
-    ga[(r + 1) * S::ROW] = acc1.x;
-    gb[(r + 1) * S::ROW] = acc1.y;
+#pragma unroll
+    for (int j = TH; j < T; j++) {
+        b0 = __ffma2_rn(w2[j], win[(r + j) % (T + 1)], b0);
+        b1 = __ffma2_rn(w2[j], win[(r + 1 + j) % (T + 1)], b1);
+    }
+    if constexpr (TH < T) {
+        a0 = __fadd2_rn(a0, b0);
+        a1 = __fadd2_rn(a1, b1);
+    }
+    ga[r * S::ROW] = a0.x;
+    gb[r * S::ROW] = a0.y;
+    ga[(r + 1) * S::ROW] = a1.x;
+    gb[(r + 1) * S::ROW] = a1.y;
 }
 
 // Exact float of the 10-bit two's-complement field in the low bits of x:
@@ -200,11 +214,18 @@ __device__ __noinline__ void p1_fir_general(const Phase1Params &p, const uint8_t
         }
         const int r = row - (T - 1);
         if (r >= ra) {
-            float2 acc = make_float2(0.0f, 0.0f);
+            // the taps' two halves in separate chains, added at the end: the
+            // summation order of p1_fir_pair, so that a window gives the same
+            // bits whichever path filters it
+            constexpr int TH = T >= 4 ? T / 2 : T;
+            float2 a = make_float2(0.0f, 0.0f), b = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int j = 0; j < T; j++) acc = __ffma2_rn(w2[j], win[j], acc);
-            ga[r * S::ROW] = acc.x;
-            gb[r * S::ROW] = acc.y;
+            for (int j = 0; j < TH; j++) a = __ffma2_rn(w2[j], win[j], a);
+#pragma unroll
+            for (int j = TH; j < T; j++) b = __ffma2_rn(w2[j], win[j], b);
+            if constexpr (TH < T) a = __fadd2_rn(a, b);
+            ga[r * S::ROW] = a.x;
+            gb[r * S::ROW] = a.y;
         }
     }
 }
