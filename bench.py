@@ -48,11 +48,11 @@ KERNEL_SOURCES = {
 }
 _CAPTURED = 33554432   # input samples of the captured launch
 NCU_TRAFFIC = {
-    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44700160 + 92524800) / _CAPTURED, "src": "196d7968b89e10a2"},
-    "k_phase2w": {"bytes_per_sample": (170526976 + 23206656) / _CAPTURED, "src": "4bbfca13f09564d5"},
-    "k_phase2w<half>": {"bytes_per_sample": (94048768 + 22073856) / _CAPTURED, "src": "4bbfca13f09564d5"},
-    "k_phase1_tc<2,16,1>": {"bytes_per_sample": (96463616 + 49078272) / _CAPTURED, "src": "d6afa2a6124d675c"},
-    "k_unpack_cols": {"bytes_per_sample": (42589952 + 19676416) / _CAPTURED, "src": "d6afa2a6124d675c"},
+    "k_phase1<16,16,32,0>": {"bytes_per_sample": (44702720 + 92542720) / _CAPTURED, "src": "17209441f63721c1"},
+    "k_phase2w": {"bytes_per_sample": (170189312 + 22351616) / _CAPTURED, "src": "0ed9442a5b4bd850"},
+    "k_phase2w<half>": {"bytes_per_sample": (94110976 + 22121728) / _CAPTURED, "src": "0ed9442a5b4bd850"},
+    "k_phase1_tc<2,16,1>": {"bytes_per_sample": (96520704 + 48678144) / _CAPTURED, "src": "ea5cae1109eb0be7"},
+    "k_unpack_cols": {"bytes_per_sample": (42592512 + 19993088) / _CAPTURED, "src": "ea5cae1109eb0be7"},
 }
 
 
